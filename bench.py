@@ -1,0 +1,407 @@
+"""Throughput of the gb300fft hot path on GB300.
+
+Headline workload: one forward 2D complex64 FFT of 8192 x 8192 (inputs
+N(0,1) re/im, seed 2506) on the plain FP32 path -- the largest configuration
+of the square-size sweep, and the one the HBM-roofline target is stated on.
+A step is one fft_execute over the whole array (row pass + column pass, the
+twiddles and the reorders fused in).  Input and output are 512 MiB each, far
+larger than L2, so no flush is needed between steps.
+
+Metric: GFLOP/s under the 5 N log2 N convention (N = nx*ny per transform),
+whole-job over all ranks.  Beside it: the roofline of the dominant kernel
+(algorithmic bytes / CUDA-event duration, measured live on the launching
+stream), an end-to-end figure with pinned host buffers and the copies inside
+the timed region, the FP64 CPU oracle timed on a bounded sample, and the
+other forms (inverse, other sizes, split tensor-core, differentiation,
+ragged batch) in "forms".
+
+  python bench.py [--gpus N --steps K --warmup W]      # this library
+  python bench.py --impl reference [...]               # the FP64 CPU oracle
+Multi-GPU: launched by torchrun, one rank per GPU, independent replicas
+(weak scaling; the batched/2D transform needs no exchange per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2D C2C FFT GFLOP/s (5N log2N), % of HBM roofline; split-TC vs FP32 path"
+NX = NY = 8192
+SEED = 2506
+
+
+def flops_2d(nx, ny, batch=1):
+    n = nx * ny
+    return 5.0 * n * math.log2(n) * batch if n > 1 else 0.0
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", d
+    return 6800.0, "fallback", {}
+
+
+def read_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    return None if e is None else float(e["bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        t0, t1 = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (0, 1e18)
+        inside = [s for t, s in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or [s for _, s in self.samples[-3:]]
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in inside:
+            f = [x.strip() for x in s.split(",")]
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle (test infrastructure) on bounded samples
+# ---------------------------------------------------------------------------
+def oracle_sample_step(x, rows: int, threads: int):
+    """One bounded sample of the 8192^2 transform on the oracle: `rows` full
+    row transforms (length nx) and `rows` full column transforms (length ny),
+    i.e. rows/ny of the whole 2D job.  Returns the flops that represents."""
+    import oracle
+    ny, nx = x.shape
+    oracle.fft1d_batch(x[:rows], dir=-1, threads=threads)
+    cols = np.ascontiguousarray(x[:, :rows].T)
+    oracle.fft1d_batch(cols, dir=-1, threads=threads)
+    return flops_2d(nx, ny) * rows / ny
+
+
+def cpu_baseline(x, budget_s: float = 12.0):
+    import oracle
+    threads = oracle.max_threads()
+    rows = 256
+    t = time.perf_counter()
+    fl = oracle_sample_step(x, rows, threads)
+    dt = time.perf_counter() - t
+    reps = max(1, min(20, int(budget_s / max(dt, 1e-3))))
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        oracle_sample_step(x, rows, threads)
+        times.append(time.perf_counter() - t)
+    med = statistics.median(times)
+    return {"value": fl / med / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{rows} row FFTs + {rows} column FFTs (length 8192, FP64 recursive radix-2) of the "
+                      f"8192x8192 input = {rows}/8192 of one 2D transform; median of {reps}"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    x = synth.normal_complex((NY, NX), seed=SEED)
+    import oracle
+    threads = oracle.max_threads()
+    rows = 64
+    for _ in range(args.warmup):
+        oracle_sample_step(x, rows, threads)
+    times = []
+    fl = 0.0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        fl = oracle_sample_step(x, rows, threads)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = fl * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "fft2d_c2c_8192x8192_forward", "nx": NX, "ny": NY, "batch": 1,
+                       "inputs": "re/im N(0,1), seed 2506",
+                       "sample_per_step": f"{rows} rows + {rows} columns of the 2D transform"},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{rows} row + {rows} column FFTs of length 8192 per step"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# This library
+# ---------------------------------------------------------------------------
+def time_plan(torch, plan, x, out, steps, warmup, pass_events=False):
+    """Mean ms per execute (CUDA events on the current stream); optionally the
+    mean per-pass durations from events recorded between the passes."""
+    for _ in range(warmup):
+        plan.execute(x, out=out)
+    torch.cuda.synchronize()
+    evs = []
+    if pass_events:
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for trip in evs:
+            for e in trip:
+                e.record()
+        torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(steps):
+        if pass_events:
+            plan.set_pass_events(*evs[k])
+        plan.execute(x, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    if pass_events:
+        plan.set_pass_events(None, None, None)
+    ms = a.elapsed_time(b) / steps
+    passes = None
+    if pass_events:
+        r = [t[0].elapsed_time(t[1]) for t in evs]
+        c = [t[1].elapsed_time(t[2]) for t in evs]
+        passes = (sum(r) / steps, sum(c) / steps)
+    return ms, passes
+
+
+def forms(torch, g, steps, warmup, dev):
+    """Secondary measurements (rank 0, N=1 only): other sizes, inverse, the
+    split tensor-core path, the differentiation form and the ragged batch."""
+    import synth
+    out = {}
+    for n in (1024, 2048, 4096, 8192):
+        x = torch.from_numpy(synth.normal_complex((n, n), seed=SEED)).to(dev)
+        y = torch.empty_like(x)
+        for inv in (False, True):
+            plan = g.get_plan(n, n, 1, inv, "fp32", dev)
+            ms, _ = time_plan(torch, plan, x, y, max(10, steps // 4), 3)
+            out[f"fp32_{'inv' if inv else 'fwd'}_{n}"] = {
+                "ms": ms, "GFLOP/s": flops_2d(n, n) / ms / 1e6,
+                "HBM_GB/s_algorithmic": 32.0 * n * n / ms / 1e6,
+                "note": "fits L2 (hot)" if n <= 2048 else "larger than L2"}
+        del x, y
+    # batch of 16384 1D length-4096 signals (one pass)
+    x = torch.from_numpy(synth.exp_mix_1d(16384, 4096, seed=SEED)[0]).to(dev)
+    y = torch.empty_like(x)
+    plan = g.get_plan(4096, 1, 16384, False, "fp32", dev)
+    ms, _ = time_plan(torch, plan, x, y, max(10, steps // 4), 3)
+    out["fp32_1d_4096x16384"] = {"ms": ms, "GFLOP/s": flops_2d(4096, 1, 16384) / ms / 1e6,
+                                 "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
+    del x, y
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2506_15437_gb300 import build as _build
+    if rank == 0 or not _build.up_to_date():
+        _build.build()
+    if pg:
+        pg.barrier()
+    import paper_2506_15437_gb300 as g
+    import synth
+
+    x_host = torch.from_numpy(synth.normal_complex((NY, NX), seed=SEED + rank)).pin_memory()
+    x = x_host.to(dev)
+    out = torch.empty_like(x)
+    plan = g.Plan(NX, NY, 1, inverse=False, precision="fp32")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        plan.execute(x, out=out)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for trip in evs:
+        for e in trip:
+            e.record()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    clocks.mark()
+    start.record()
+    for k in range(args.steps):
+        plan.set_pass_events(*evs[k])
+        plan.execute(x, out=out)
+    end.record()
+    torch.cuda.synchronize()
+    clocks.mark()
+    if pg:
+        pg.barrier()
+    plan.set_pass_events(None, None, None)
+    ms = start.elapsed_time(end) / args.steps
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    status = plan.status()
+    rows_ms = sum(t[0].elapsed_time(t[1]) for t in evs) / args.steps
+    cols_ms = sum(t[1].elapsed_time(t[2]) for t in evs) / args.steps
+    time.sleep(0.25)
+    clocks.stop()
+    clk = clocks.summary()
+
+    value = world * flops_2d(NX, NY) / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host input -> device, transform,
+    # device -> pinned host output, all inside the timed region
+    out_host = torch.empty_like(x_host).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        x.copy_(x_host, non_blocking=True)
+        plan.execute(x, out=out)
+        out_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(e2e_steps):
+        x.copy_(x_host, non_blocking=True)
+        plan.execute(x, out=out)
+        out_host.copy_(out, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = NX * NY * 8
+
+    peak, peak_kind, _ = read_peaks()
+    dom_name, dom_ms = ("k_rows<8192,16>", rows_ms) if rows_ms >= cols_ms else ("k_cols<8192,16,2>", cols_ms)
+    achieved = 16.0 * NX * NY / (dom_ms * 1e-3) / 1e9
+    traffic = read_traffic(dom_name)
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": traffic, "algorithmic_bytes_per_launch": 16 * NX * NY,
+                "passes_ms": {"rows": rows_ms, "cols": cols_ms},
+                "whole_step_frac": (32.0 * NX * NY / (ms * 1e-3) / 1e9) / peak}
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fft2d_c2c_8192x8192_forward", "nx": NX, "ny": NY, "batch": 1,
+                       "precision": "fp32", "inputs": "re/im N(0,1), seed 2506 (+rank)",
+                       "l2": "inputs and outputs 512 MiB each, larger than L2; no flush"},
+            "roofline": roofline,
+            "e2e": {"value": world * flops_2d(NX, NY) / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk, "status": status}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x_host.numpy())
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = forms(torch, g, args.steps, args.warmup, dev)
+    if rank == 0:
+        print(json.dumps(line))
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * gb300fft -- 2D complex-to-complex Cooley-Tukey FFT for the NVIDIA GB300
+ * (sm_103a).  C ABI of libgb300fft.so.
+ *
+ * What is computed.  For each [ny][nx] slice of a row-major complex64 array
+ * (interleaved re, im float32; nx is the contiguous row length), the
+ * unnormalised 2D DFT
+ *
+ *     X[ky][kx] = sum_{y<ny} sum_{x<nx} x[y][x] * exp(dir*2*pi*i*(ky*y/ny + kx*x/nx)),
+ *
+ * evaluated as the paper's Section 5 decomposition (Fig. 6): radix-2^k
+ * Cooley-Tukey FFTs (Section 2.2, Fig. 2, Listing 1) along every row, then
+ * along every column.  The twiddle multiply (Section 2.2) and the data
+ * reordering between butterfly steps (Section 4, Figs. 4 and 5) are fused
+ * into the kernels; the output is always in natural [ky][kx] order.  The
+ * paper states neither a sign convention nor a normalisation: here
+ * dir = -1 (FFT_FORWARD) is exp(-...), dir = +1 (FFT_INVERSE) is exp(+...),
+ * and neither direction scales, so inverse(forward(x)) = nx*ny*x.
+ *
+ * Memory.  Every data pointer passed to an execute call is a caller-owned
+ * DEVICE pointer to contiguous complex64 data, 16-byte aligned.  in == out
+ * (in place) is allowed; partially overlapping buffers are not.  A plan owns
+ * its device workspace (twiddle tables, status word, ragged work queue) and
+ * allocates all of it at creation; execute calls allocate nothing and do
+ * not synchronise, so they are stream-ordered and may be captured in a CUDA
+ * graph.  A plan must not be used on two streams at the same time.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).
+ *
+ * Errors.  Calls return FFT_OK (0) or a negative FFT_ERR_* code; plan
+ * constructors return NULL and leave the reason in fft_last_error()
+ * (per calling thread).  Launch failures map to FFT_ERR_CUDA.  Device-side
+ * failures (a bounded wait that ran out) are recorded in the plan's device
+ * status word, read back by fft_plan_status().  No kernel traps.
+ */
+#ifndef GB300FFT_H
+#define GB300FFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan_s *fft_plan_t;
+
+enum { FFT_FORWARD = -1, FFT_INVERSE = 1 };
+
+/* Arithmetic of the butterflies.  FFT_PREC_FP32: every stage in float32 on
+ * the CUDA cores.  FFT_PREC_SPLIT_FP16_TC: the radix-16 stages run as
+ * 16x16 complex DFT-matrix products on the tensor cores with operands split
+ * into a high and a low float16 part (3 products, float32 accumulation);
+ * twiddles between stages stay float32. */
+enum { FFT_PREC_FP32 = 0, FFT_PREC_SPLIT_FP16_TC = 1 };
+
+enum {
+    FFT_OK = 0,
+    FFT_ERR_INVALID_SIZE = -1, /* n not a power of two in range, batch < 1, count < 1 */
+    FFT_ERR_INVALID_ARG = -2,  /* NULL / misaligned pointer, bad dir or precision, bad index */
+    FFT_ERR_ALLOC = -3,        /* device or host allocation failed at plan creation */
+    FFT_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
+    FFT_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement */
+    FFT_ERR_TIMEOUT = -6       /* a device-side bounded wait ran out (status word) */
+};
+
+/*
+ * fft_plan_create -- plan `batch` 2D transforms of size [ny][nx].
+ *   nx, ny     powers of two, 1 <= n <= 8192 each (nx = 1 or ny = 1 gives a
+ *              batch of 1D transforms along the other axis).
+ *   batch      >= 1; slices are stored back to back, nx*ny elements apart.
+ *   dir        FFT_FORWARD or FFT_INVERSE: the exponent sign of fft_execute.
+ *   precision  FFT_PREC_FP32 or FFT_PREC_SPLIT_FP16_TC.
+ * Returns NULL on failure (reason in fft_last_error()).  Must be called with
+ * the device that will run the plan current; allocates device memory.
+ */
+fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision);
+
+/*
+ * fft_execute -- out = DFT_dir(in) for the plan's batch (Section 5: row
+ * FFTs, then column FFTs, natural-order output).  `in` and `out` are device
+ * pointers to batch*ny*nx complex64 each; `in` is read only when in != out.
+ */
+int fft_execute(fft_plan_t p, const void *in, void *out, void *stream);
+
+/*
+ * fft_backward -- the adjoint (conjugate transpose) of the plan's transform:
+ * grad_in = F^H grad_out, i.e. the unnormalised transform with the opposite
+ * exponent sign.  This is the vector-Jacobian product of fft_execute for a
+ * real loss under PyTorch's conjugate-Wirtinger convention.
+ */
+int fft_backward(fft_plan_t p, const void *grad_out, void *grad_in, void *stream);
+
+/*
+ * fft_backward_weighted -- grad_in = F^H (scale * w (.) X), with the
+ * elementwise weighting fused into the first pass's load.  For the loss
+ * L = sum w*|F x|^2, passing X = F x and scale = 2 gives dL/dx.
+ *   X, grad_in  device complex64, batch*ny*nx elements (may alias).
+ *   w           device float32, batch*ny*nx elements (must not alias X).
+ */
+int fft_backward_weighted(fft_plan_t p, const void *X, const void *w, float scale,
+                          void *grad_in, void *stream);
+
+/*
+ * fft_weighted_power -- partial sums of L = sum w*|X|^2 over X, w of the
+ * plan's full size: writes `nparts` float32 partial sums to the device array
+ * `partials` (the caller adds them, preferably in double).  nparts is
+ * fft_weighted_power_parts(p).  Each partial is a compensated float sum.
+ */
+int fft_weighted_power(fft_plan_t p, const void *X, const void *w, void *partials,
+                       void *stream);
+int fft_weighted_power_parts(fft_plan_t p);
+
+/* Destroy a plan and free its device memory (synchronises the device).
+ * NULL is a no-op returning FFT_OK. */
+int fft_plan_destroy(fft_plan_t p);
+
+/* Last error set on this thread by a plan constructor (FFT_OK if none). */
+int fft_last_error(void);
+
+/* Static description of an error code (never NULL). */
+const char *fft_error_string(int code);
+
+/*
+ * Ragged batches (many independent 2D transforms of mixed sizes in one
+ * persistent launch captured in a CUDA graph).
+ *
+ * fft_plan_create_ragged -- `count` instances, instance i of size
+ * [ny[i]][nx[i]] with nx[i], ny[i] powers of two in 32..1024.  nx, ny are
+ * host arrays read only during the call.  Instances are packed back to back
+ * in the order given: instance i starts fft_ragged_offset(i) complex
+ * elements into the buffer.
+ */
+fft_plan_t fft_plan_create_ragged(int count, const int *nx, const int *ny, int dir,
+                                  int precision);
+
+/* Element offset of instance i in the packed layout (i == count gives the
+ * total number of elements). */
+int fft_ragged_offset(fft_plan_t p, int i, long long *elem_offset);
+
+/* Transform every instance of a ragged plan: one graph launch. */
+int fft_execute_ragged(fft_plan_t p, const void *in, void *out, void *stream);
+
+/* The same work as fft_execute_ragged, issued as one plain launch per
+ * instance of the row/column kernels (the comparison baseline). */
+int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *stream);
+
+/*
+ * fft_plan_status -- synchronise `stream`, return the plan's device status
+ * word (FFT_OK, or the FFT_ERR_* a kernel recorded) and clear it.
+ */
+int fft_plan_status(fft_plan_t p, void *stream);
+
+/*
+ * fft_debug_reorder_map -- the index permutation realised by the kernels'
+ * data movement alone.  Runs the row engine (axis 0) or the column engine
+ * (axis 1) for length n with every butterfly replaced by the identity and an
+ * integer payload, and writes map[i] = the output position of input i.
+ * With the arithmetic removed, the fused Stockham movement of the kernels is
+ * the mixed-radix digit reversal of the stage radices (Section 4's
+ * reordering, here folded into the stage loads and stores).  `map` is a
+ * device array of n int32.  Same n range as fft_plan_create.
+ */
+int fft_debug_reorder_map(int n, int axis, void *map, void *stream);
+
+/*
+ * fft_plan_set_pass_events -- profiling hook.  When set, every following
+ * fft_execute / fft_backward on this dense plan records ev_start before the
+ * row pass, ev_mid between the row and column passes and ev_end after the
+ * column pass, on the call's stream (cudaEvent_t handles passed as void*,
+ * created by the caller with timing enabled).  Passing three NULLs turns it
+ * off.  The events' elapsed times are the per-pass kernel durations.
+ */
+int fft_plan_set_pass_events(fft_plan_t p, void *ev_start, void *ev_mid, void *ev_end);
+
+/* Stage radices the kernels use for length n along an axis (0 rows, 1
+ * columns), first stage first; returns the number of stages written to
+ * `radices` (capacity 16) or a negative error. */
+int fft_debug_radices(int n, int axis, int *radices);
+
+/* Library version string. */
+const char *fft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300FFT_H */

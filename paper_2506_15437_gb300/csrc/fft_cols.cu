@@ -1,0 +1,286 @@
+// Column pass: batched length-N FFTs down the columns of each [N][nx] slice
+// (the second half of the paper's Section 5 decomposition).  The paper moves
+// data between the two halves with a global transpose (Fig. 6); here there is
+// none.  Each CTA stages a tile of W adjacent columns x N rows into shared
+// memory with 2D TMA copies (cp.async.bulk.tensor, completion on an mbarrier),
+// transforms the W columns with the same Stockham engine as the row pass, and
+// stores natural-order results back into the same columns.
+//
+// CTAs are persistent: each walks tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...  While tile k is being transformed, tile k+1 sits in L2 (bulk L2
+// prefetch issued one tile ahead) and its TMA load into shared memory starts
+// as soon as every thread has read its last-stage operands of tile k, so the
+// load overlaps the last butterflies and the stores of tile k.
+#include "fft_common.cuh"
+#include "fft_internal.h"
+
+namespace gb300fft {
+
+template <int N, int E, int W>
+struct ColShape {
+    static constexpr int T = N / E;
+    static constexpr int THREADS = T * W;
+    using Eng = Engine<N, E, W, PadShift<E>::value>;
+    static constexpr int ELEMS = Eng::SMEM_ELEMS > N * W ? Eng::SMEM_ELEMS : N * W;
+    static constexpr int BOXR = N < 256 ? N : 256;
+    static constexpr uint32_t TILE_BYTES = (uint32_t)N * W * sizeof(float2);
+    static constexpr size_t BAR_OFF = ((size_t)ELEMS * sizeof(float2) + 127) / 128 * 128;
+    static constexpr size_t SMEM = BAR_OFF + 16;
+};
+
+template <int N, int E, int W>
+__global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
+    k_cols(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw, int nx,
+           int batch, int conj_out, int *status) {
+    using Sh = ColShape<N, E, W>;
+    using Eng = typename Sh::Eng;
+    constexpr int R0 = Eng::R0;
+    constexpr int T = Sh::T;
+    extern __shared__ __align__(128) unsigned char raw[];
+    float2 *tile = reinterpret_cast<float2 *>(raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    __shared__ int s_ok;
+
+    const int t = threadIdx.x;
+    const int c = t % W;
+    const int tt = t / W;
+    const int groups_x = nx / W;
+    const long long ntiles = (long long)groups_x * batch;
+    const float so = conj_out ? -1.f : 1.f;
+
+    auto issue = [&](long long id) {  // thread 0: TMA loads of tile `id`
+        const int b = (int)(id / groups_x);
+        const int x = (int)(id % groups_x) * 2 * W;
+        mbar_expect_tx(bar, Sh::TILE_BYTES);
+#pragma unroll 1
+        for (int k = 0; k < N / Sh::BOXR; ++k)
+            tma_load_2d(tile + k * Sh::BOXR * W, &map, x, b * N + k * Sh::BOXR, bar);
+    };
+    auto prefetch = [&](long long id) {  // thread 0: bulk L2 prefetch of tile `id`
+        const int b = (int)(id / groups_x);
+        const int x = (int)(id % groups_x) * 2 * W;
+#pragma unroll 1
+        for (int k = 0; k < N / Sh::BOXR; ++k) tma_prefetch_2d(&map, x, b * N + k * Sh::BOXR);
+    };
+
+    if (t == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long id = blockIdx.x;
+    uint32_t phase = 0;
+    if (t == 0 && id < ntiles) {
+        issue(id);
+        if (id + gridDim.x < ntiles) prefetch(id + gridDim.x);
+    }
+    for (; id < ntiles; id += gridDim.x) {
+        if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (t == 0) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(bar, phase);  // give the copy in flight a last chance to land
+            }
+            return;
+        }
+        phase ^= 1;
+        const long long next = id + gridDim.x;
+        const int b = (int)(id / groups_x);
+        float2 *dst = out + (long long)b * N * nx + (long long)(id % groups_x) * W;
+
+        float2 v[E];
+#pragma unroll
+        for (int bb = 0; bb < E / R0; ++bb) {
+            const int j = tt + bb * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) v[bb * R0 + r] = tile[(j + r * (N / R0)) * W + c];
+        }
+        auto after_reads = [&] {
+            __syncthreads();
+            if (t == 0 && next < ntiles) {
+                fence_proxy_async_smem();
+                issue(next);
+                if (next + gridDim.x < ntiles) prefetch(next + gridDim.x);
+            }
+        };
+        auto store = [&](int i, int cc, float2 x) {
+            x.y *= so;
+            dst[(long long)i * nx + cc] = x;
+        };
+        Eng::template run<FftPolicy, true>(v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
+    }
+}
+
+// Movement-only twin: one tile of W columns whose dense staging buffer holds
+// integer tags exactly where the TMA copy would put the data.  map[i] = final
+// row of the element that started in row i of column 0.
+template <int N, int E, int W>
+__global__ void __launch_bounds__(ColShape<N, E, W>::THREADS) k_cols_movemap(int *map) {
+    using Sh = ColShape<N, E, W>;
+    using Eng = typename Sh::Eng;
+    constexpr int R0 = Eng::R0;
+    constexpr int T = Sh::T;
+    extern __shared__ __align__(128) unsigned char raw[];
+    float2 *tile = reinterpret_cast<float2 *>(raw);
+    const int t = threadIdx.x;
+    const int c = t % W;
+    const int tt = t / W;
+    for (int k = t; k < N * W; k += blockDim.x) tile[k] = make_float2(__int_as_float(k / W), __int_as_float(k % W));
+    __syncthreads();
+    float2 v[E];
+#pragma unroll
+    for (int bb = 0; bb < E / R0; ++bb) {
+        const int j = tt + bb * T;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[bb * R0 + r] = tile[(j + r * (N / R0)) * W + c];
+    }
+    auto after = [] { __syncthreads(); };
+    auto store = [&](int i, int cc, float2 x) {
+        if (cc == 0 && __float_as_int(x.y) == 0) map[__float_as_int(x.x)] = i;
+    };
+    Eng::template run<MovePolicy, true>(v, tile, nullptr, tt, c, SyncBlock{}, after, store);
+}
+
+// ---------------------------------------------------------------------------
+// Variant table: (log2 n, E, W) with W in {2, 4, 8, 16} and N*W <= 16384
+// (a tile of at most 128 KiB plus padding).
+// ---------------------------------------------------------------------------
+namespace {
+struct ColEntry {
+    ColVariant v;
+    const void *movemap = nullptr;
+};
+constexpr int kWSlots = 4;  // W = 2, 4, 8, 16
+ColEntry g_cols[kMaxLog2 + 1][2][kWSlots];  // [log2n][E slot: default, 32][W slot]
+bool g_cols_init = false;
+
+int w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : -1; }
+
+template <int N, int E, int W>
+void reg_col(int eslot) {
+    using Sh = ColShape<N, E, W>;
+    ColEntry &en = g_cols[ilog2(N)][eslot][w_slot(W)];
+    en.v.fn = (const void *)k_cols<N, E, W>;
+    en.v.n = N;
+    en.v.e = E;
+    en.v.w = W;
+    en.v.threads = Sh::THREADS;
+    en.v.smem = Sh::SMEM;
+    en.v.box_rows = Sh::BOXR;
+    en.v.tw_size = Sched<N, E>::tw_size;
+    en.movemap = (const void *)k_cols_movemap<N, E, W>;
+}
+
+template <int N, int E>
+void reg_col_ws(int eslot) {
+    reg_col<N, E, 2>(eslot);
+    if constexpr (N * 4 <= 16384) reg_col<N, E, 4>(eslot);
+    if constexpr (N * 8 <= 16384) reg_col<N, E, 8>(eslot);
+    if constexpr (N * 16 <= 16384) reg_col<N, E, 16>(eslot);
+}
+
+template <int N>
+void reg_cols_n() {
+    constexpr int E = N >= 16 ? 16 : N;
+    reg_col_ws<N, E>(0);
+    if constexpr (N >= 4096) reg_col_ws<N, 32>(1);
+}
+
+void init_cols() {
+    if (g_cols_init) return;
+    reg_cols_n<2>();
+    reg_cols_n<4>();
+    reg_cols_n<8>();
+    reg_cols_n<16>();
+    reg_cols_n<32>();
+    reg_cols_n<64>();
+    reg_cols_n<128>();
+    reg_cols_n<256>();
+    reg_cols_n<512>();
+    reg_cols_n<1024>();
+    reg_cols_n<2048>();
+    reg_cols_n<4096>();
+    reg_cols_n<8192>();
+    g_cols_init = true;
+}
+
+const ColEntry *col_entry(int log2n, int e, int w) {
+    init_cols();
+    if (log2n < 1 || log2n > kMaxLog2) return nullptr;
+    const int ws = w_slot(w);
+    if (ws < 0) return nullptr;
+    const int n = 1 << log2n;
+    const int es = (e == default_col_e(n)) ? 0 : (e == 32 ? 1 : -1);
+    if (es < 0) return nullptr;
+    const ColEntry *en = &g_cols[log2n][es][ws];
+    return en->v.fn ? en : nullptr;
+}
+}  // namespace
+
+int default_col_e(int n) { return n >= 16 ? 16 : n; }
+
+// Widest tile that keeps the staged tile near 64 KiB, within the row length.
+int default_col_w(int n, int nx) {
+    int w = 8192 / n;
+    if (w > 16) w = 16;
+    if (w < 2) w = 2;
+    while (w > nx) w >>= 1;
+    return w;
+}
+
+const ColVariant *col_variant(int log2n, int e, int w) {
+    const ColEntry *en = col_entry(log2n, e, w);
+    return en ? &en->v : nullptr;
+}
+
+int col_ctas_per_sm(const ColVariant &v) {
+    int blocks = 0;
+    if (v.smem > 48 * 1024)
+        cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, v.fn, v.threads, v.smem) != cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
+                        int nx, int batch, int conj_out, int *status, int grid, cudaStream_t s) {
+    if (v.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (e != cudaSuccess) return e;
+    }
+    CUtensorMap m = map;
+    void *args[] = {(void *)&m, (void *)&out, (void *)&tw, (void *)&nx, (void *)&batch, (void *)&conj_out,
+                    (void *)&status};
+    return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, v.smem, s);
+}
+
+cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s) {
+    const int n = 1 << log2n;
+    const ColEntry *en = col_entry(log2n, default_col_e(n), 2);
+    if (!en) return cudaErrorInvalidValue;
+    if (en->v.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(en->movemap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)en->v.smem);
+        if (e != cudaSuccess) return e;
+    }
+    void *args[] = {(void *)&map};
+    return cudaLaunchKernel(en->movemap, dim3(1), dim3(en->v.threads), args, en->v.smem, s);
+}
+
+int schedule_radices(int n, int e, int *radices) {
+    if (n < 1 || (n & (n - 1)) || e < 1 || (e & (e - 1))) return -1;
+    if (e > n) e = n;
+    const int L = ilog2(n), LE = ilog2(e);
+    if (n == 1) {
+        radices[0] = 1;
+        return 1;
+    }
+    const int S = (L + LE - 1) / LE;
+    radices[0] = n >> (LE * (S - 1));
+    for (int s = 1; s < S; ++s) radices[s] = e;
+    return S;
+}
+
+}  // namespace gb300fft

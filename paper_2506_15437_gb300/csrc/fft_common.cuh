@@ -1,0 +1,328 @@
+// Device building blocks shared by the gb300fft kernels (sm_103a).
+//
+// The transform is the radix-2^k Cooley-Tukey FFT of the paper's Section 2.2
+// (Fig. 2, Listing 1) in its self-sorting (Stockham) arrangement: every
+// butterfly stage reads its operands in the order that stage needs and writes
+// its results straight into the order the NEXT stage needs.  That is the
+// paper's "one reordering per step" idea (Section 4, Fig. 5) taken to its end
+// point: the reordering is the address arithmetic of the stage's loads and
+// stores, the intermediate orders live only in shared memory and registers,
+// and no separate bit-reversal pass or HBM round trip exists.
+//
+// Stage s of a length-N transform has radix R and span Ns = R_0 * ... * R_{s-1}.
+// Butterfly j (0 <= j < N/R), with m = j mod Ns, reads a_r = d[j + r*N/R],
+// multiplies a_r by w_{Ns*R}^{r*m} (w_K = exp(-2*pi*i/K)), takes the length-R
+// DFT b_k = sum_r a_r w_R^{r*k}, and writes b_k to d'[(j - m)*R + m + k*Ns].
+// The first stage (Ns = 1) needs no twiddles; the last one (Ns*R = N) writes
+// natural order.  The inverse direction is computed as conj(F(conj(x))), so
+// all tables and constants are for the forward sign only.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb300fft {
+
+// Device status word codes (same values as the C ABI's FFT_ERR_*).
+constexpr int kStatusOk = 0;
+constexpr int kStatusTimeout = -6;
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// ---------------------------------------------------------------------------
+// Complex arithmetic on float2 (x = re, y = im).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// sin(2*pi*q/64) for 0 <= q <= 16, rounded to float (compile-time constants).
+__host__ __device__ constexpr float qsin64(int q) {
+    return q == 0    ? 0.0f
+           : q == 1  ? 0.0980171403295606f
+           : q == 2  ? 0.19509032201612825f
+           : q == 3  ? 0.29028467725446233f
+           : q == 4  ? 0.3826834323650898f
+           : q == 5  ? 0.47139673682599764f
+           : q == 6  ? 0.5555702330196022f
+           : q == 7  ? 0.6343932841636455f
+           : q == 8  ? 0.7071067811865475f
+           : q == 9  ? 0.773010453362737f
+           : q == 10 ? 0.8314696123025452f
+           : q == 11 ? 0.8819212643483549f
+           : q == 12 ? 0.9238795325112867f
+           : q == 13 ? 0.9569403357322089f
+           : q == 14 ? 0.9807852804032304f
+           : q == 15 ? 0.9951847266721968f
+                     : 1.0f;
+}
+// sin and cos of 2*pi*q/64 for any integer q, by quadrant symmetry.
+__host__ __device__ constexpr float sin64(int q) {
+    return (q & 63) < 16   ? qsin64(q & 63)
+           : (q & 63) < 32 ? qsin64(32 - (q & 63))
+           : (q & 63) < 48 ? -qsin64((q & 63) - 32)
+                           : -qsin64(64 - (q & 63));
+}
+__host__ __device__ constexpr float cos64(int q) { return sin64(q + 16); }
+
+// z * exp(-2*pi*i*q/64).  q is a compile-time constant after unrolling, so the
+// branches fold: multiples of pi/2 become swaps and sign flips, odd multiples
+// of pi/4 cost two adds and two multiplies, the rest a complex multiply by
+// immediate constants.
+__device__ __forceinline__ float2 mul_root64(float2 z, int q) {
+    q &= 63;
+    if (q == 0) return z;
+    if (q == 16) return make_float2(z.y, -z.x);
+    if (q == 32) return make_float2(-z.x, -z.y);
+    if (q == 48) return make_float2(-z.y, z.x);
+    if ((q & 15) == 8) {
+        const float h = 0.7071067811865475f;
+        if (q == 8) return make_float2((z.x + z.y) * h, (z.y - z.x) * h);
+        if (q == 24) return make_float2((z.y - z.x) * h, (-z.x - z.y) * h);
+        if (q == 40) return make_float2((-z.x - z.y) * h, (z.x - z.y) * h);
+        return make_float2((z.x - z.y) * h, (z.x + z.y) * h);
+    }
+    const float c = cos64(q), s = sin64(q);
+    return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
+}
+
+__host__ __device__ constexpr int bitrev(int k, int bits) {
+    return bits == 0 ? 0 : ((k & 1) << (bits - 1)) | bitrev(k >> 1, bits - 1);
+}
+
+// One radix-2 decimation-in-frequency level of span H over R registers:
+// (u, v) -> (u + v, (u - v) * w_{2H}^k).  Levels recurse at compile time so
+// every register index and twiddle is a constant.
+template <int R, int H>
+__device__ __forceinline__ void dif_level(float2 *a) {
+    if constexpr (H >= 1) {
+#pragma unroll
+        for (int blk = 0; blk < R; blk += 2 * H) {
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const float2 u = a[blk + k], v = a[blk + k + H];
+                a[blk + k] = cadd(u, v);
+                a[blk + k + H] = mul_root64(csub(u, v), k * (64 / (2 * H)));
+            }
+        }
+        dif_level<R, H / 2>(a);
+    }
+}
+
+// a[K] = t[bitrev(K)] for K = 0..R-1, every index a constant expression.
+template <int R, int K>
+__device__ __forceinline__ void bitrev_gather(float2 *a, const float2 *t) {
+    if constexpr (K < R) {
+        constexpr int src = bitrev(K, ilog2(R));
+        a[K] = t[src];
+        bitrev_gather<R, K + 1>(a, t);
+    }
+}
+
+// In-register length-R DFT (forward sign), natural order in and out,
+// R a power of two <= 64: radix-2 DIF levels, then a compile-time
+// bit-reversal of register names.
+template <int R>
+__device__ __forceinline__ void dft(float2 *a) {
+    if constexpr (R > 1) {
+        dif_level<R, R / 2>(a);
+        float2 t[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) t[k] = a[k];
+        bitrev_gather<R, 0>(a, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage schedule of a length-N transform with E elements held per thread:
+// first stage radix R0 = N / E^(S-1) (absorbs the remainder), then S-1
+// stages of radix E.  Requires E <= N, both powers of two.
+// ---------------------------------------------------------------------------
+template <int N, int E>
+struct Sched {
+    static_assert(E <= N, "E must not exceed N");
+    static constexpr int L = ilog2(N);
+    static constexpr int LE = ilog2(E);
+    static constexpr int S = (L + LE - 1) / LE > 0 ? (L + LE - 1) / LE : 1;
+    static constexpr int R0 = N >> (LE * (S - 1));
+    // span Ns of stage s
+    static constexpr int ns(int s) { return s == 0 ? 1 : R0 * ipow(E, s - 1); }
+    // offset of stage s's twiddle table (stage 1 starts at 0)
+    static constexpr int tw_off(int s) { return s <= 1 ? 0 : tw_off(s - 1) + (E - 1) * ns(s - 1); }
+    static constexpr int tw_size = tw_off(S);
+};
+
+// ---------------------------------------------------------------------------
+// Payload policies.  The FFT moves float2 and runs DFTs; the reorder-map debug
+// path moves integer tags through exactly the same addresses with identity
+// butterflies, which exposes the permutation the data movement realises.
+// ---------------------------------------------------------------------------
+struct FftPolicy {
+    using T = float2;
+    template <int R>
+    __device__ static __forceinline__ void butterfly(T *a) { dft<R>(a); }
+    __device__ static __forceinline__ T twiddle(T a, float2 w) { return cmul(a, w); }
+};
+struct MovePolicy {
+    using T = float2;  // integer tags carried bit-for-bit in the .x lane
+    template <int R>
+    __device__ static __forceinline__ void butterfly(T *) {}
+    __device__ static __forceinline__ T twiddle(T a, float2) { return a; }
+};
+
+struct SyncBlock {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncWarp {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// ---------------------------------------------------------------------------
+// The Stockham engine.  A group of NT = W*N/E threads transforms W
+// interleaved length-N vectors held in shared memory at element (i, c) ->
+// padded flat index pad(i*W + c).  Thread t of the group owns column
+// c = t % W and butterfly index tt = t / W.
+//
+// Caller contract: v[] holds the stage-0 inputs, v[b*R0 + r] = x[j + r*N/R0]
+// for j = tt + b*(N/E).  `after_reads()` runs once every thread has issued its
+// last shared-memory read (it must synchronise the group if it reuses the
+// buffer); `store(i, c, value)` receives the natural-order outputs.
+// SRC_IN_SMEM: stage-0 inputs were read from `sm` itself, so the first
+// shared-memory write must wait for every thread's reads.
+// ---------------------------------------------------------------------------
+template <int N, int E, int W, int PADSH>
+struct Engine {
+    using Sc = Sched<N, E>;
+    static constexpr int T = N / E;   // threads per column
+    static constexpr int NT = T * W;  // threads per group
+    static constexpr int R0 = Sc::R0;
+    static constexpr int S = Sc::S;
+    static constexpr int RL = (S == 1) ? R0 : E;  // radix of the last stage
+    __host__ __device__ static constexpr int pad(int f) { return f + (f >> PADSH); }
+    static constexpr int SMEM_ELEMS = (S > 1) ? pad(N * W - 1) + 1 : 0;
+
+    template <class Pol, bool SRC_IN_SMEM, class Sync, class AfterReads, class Store>
+    __device__ static __forceinline__ void run(typename Pol::T (&v)[E], typename Pol::T *sm,
+                                               const float2 *__restrict__ tw, int tt, int c,
+                                               Sync sync, AfterReads after_reads, Store store) {
+        using V = typename Pol::T;
+        // stage 0: butterflies in registers, no twiddles
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) Pol::template butterfly<R0>(&v[b * R0]);
+        if constexpr (S == 1) {
+            after_reads();
+        } else {
+#pragma unroll
+            for (int s = 1; s < S; ++s) {
+                const int Rp = (s == 1) ? R0 : E;  // radix of stage s-1
+                const int Nsp = Sc::ns(s - 1);     // span of stage s-1
+                if (s > 1 || SRC_IN_SMEM) sync();
+#pragma unroll
+                for (int b = 0; b < E / Rp; ++b) {
+                    const int j = tt + b * T;
+                    const int m = j & (Nsp - 1);
+#pragma unroll
+                    for (int k = 0; k < Rp; ++k) sm[pad(((j - m) * Rp + m + k * Nsp) * W + c)] = v[b * Rp + k];
+                }
+                sync();
+                const int Ns = Sc::ns(s);
+                const int m = tt & (Ns - 1);
+#pragma unroll
+                for (int r = 0; r < E; ++r) v[r] = sm[pad((tt + r * T) * W + c)];
+                if (s == S - 1) after_reads();
+                const float2 *tws = tw + Sc::tw_off(s) + m;
+#pragma unroll
+                for (int r = 1; r < E; ++r) v[r] = Pol::twiddle(v[r], __ldg(tws + (r - 1) * Ns));
+                Pol::template butterfly<E>(v);
+            }
+        }
+        // natural-order outputs of the last stage: position j + k*N/RL
+#pragma unroll
+        for (int b = 0; b < E / RL; ++b) {
+            const int j = tt + b * T;
+#pragma unroll
+            for (int k = 0; k < RL; ++k) store(j + k * (N / RL), c, v[b * RL + k]);
+        }
+    }
+};
+
+// Shared-memory padding shift used by every kernel for a given E: chosen so
+// that the stage loads and stores of the common shapes hit each bank pair at
+// most once per half-warp (checked by a bank model on the CPU).
+template <int E>
+struct PadShift {
+    static constexpr int value = (E >= 32) ? 5 : 4;
+};
+
+// ---------------------------------------------------------------------------
+// TMA / mbarrier helpers (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on an mbarrier phase: gives up after ~`limit_ns` nanoseconds
+// (or 2^26 polls) and returns false.  Never spins forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && globaltimer_ns() - t0 > limit_ns) break;
+    }
+    return false;
+}
+// 2D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Prefetch of one box into L2 (no shared memory involved).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+
+__device__ __forceinline__ void record_status(int *status, int code) {
+    if (status) atomicCAS(status, kStatusOk, code);
+}
+
+}  // namespace gb300fft

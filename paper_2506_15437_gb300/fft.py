@@ -1,0 +1,207 @@
+"""Python API over the C ABI: plans, fft2 and the autograd Function.
+
+PyTorch only provides device memory and streams here.  Every transform runs
+in libgb300fft.so's kernels; the only thing this module does is pass tensor
+pointers and the current stream through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _native as N
+
+_PREC = {"fp32": N.FFT_PREC_FP32, "split_tc": N.FFT_PREC_SPLIT_FP16_TC,
+         "split_fp16_tc": N.FFT_PREC_SPLIT_FP16_TC}
+
+
+def _stream_handle(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _check_tensor(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """A dense plan: ``batch`` transforms of size ``[ny][nx]``."""
+
+    def __init__(self, nx: int, ny: int, batch: int = 1, inverse: bool = False,
+                 precision: str = "fp32"):
+        lib = N.load()
+        self.nx, self.ny, self.batch = int(nx), int(ny), int(batch)
+        self.dir = N.FFT_INVERSE if inverse else N.FFT_FORWARD
+        self.precision = precision
+        self._lib = lib
+        self._p = lib.fft_plan_create(self.nx, self.ny, self.batch, self.dir, _PREC[precision])
+        if not self._p:
+            raise N.FFTError(lib.fft_last_error(), f"fft_plan_create({nx}, {ny}, {batch})")
+
+    @property
+    def numel(self) -> int:
+        return self.nx * self.ny * self.batch
+
+    def _io(self, x, out):
+        _check_tensor(x, torch.complex64, "input")
+        if x.numel() != self.numel:
+            raise ValueError(f"input has {x.numel()} elements, plan expects {self.numel}")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _check_tensor(out, torch.complex64, "out")
+            if out.numel() != self.numel:
+                raise ValueError("out has the wrong size")
+        return out
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self._io(x, out)
+        N.check(self._lib.fft_execute(self._p, x.data_ptr(), out.data_ptr(),
+                                      _stream_handle(x.device)), "fft_execute")
+        return out
+
+    def backward(self, g: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self._io(g, out)
+        N.check(self._lib.fft_backward(self._p, g.data_ptr(), out.data_ptr(),
+                                       _stream_handle(g.device)), "fft_backward")
+        return out
+
+    def backward_weighted(self, X: torch.Tensor, w: torch.Tensor, scale: float,
+                          out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self._io(X, out)
+        _check_tensor(w, torch.float32, "w")
+        if w.numel() != self.numel:
+            raise ValueError("w has the wrong size")
+        N.check(self._lib.fft_backward_weighted(self._p, X.data_ptr(), w.data_ptr(),
+                                                ctypes.c_float(scale), out.data_ptr(),
+                                                _stream_handle(X.device)),
+                "fft_backward_weighted")
+        return out
+
+    def weighted_power(self, X: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
+        """sum w*|X|^2 as a float64 0-d tensor (partials reduced by torch)."""
+        _check_tensor(X, torch.complex64, "X")
+        _check_tensor(w, torch.float32, "w")
+        parts = self._lib.fft_weighted_power_parts(self._p)
+        partials = torch.empty(parts, dtype=torch.float32, device=X.device)
+        N.check(self._lib.fft_weighted_power(self._p, X.data_ptr(), w.data_ptr(),
+                                             partials.data_ptr(), _stream_handle(X.device)),
+                "fft_weighted_power")
+        return partials.double().sum()
+
+    def set_pass_events(self, start=None, mid=None, end=None):
+        """Record torch.cuda.Event objects around the row and column passes of
+        every following execute/backward (None, None, None turns it off)."""
+        h = [None if e is None else ctypes.c_void_p(e.cuda_event) for e in (start, mid, end)]
+        N.check(self._lib.fft_plan_set_pass_events(self._p, *h), "fft_plan_set_pass_events")
+
+    def status(self) -> int:
+        return self._lib.fft_plan_status(self._p, _stream_handle(torch.device("cuda")))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.fft_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_cache: dict = {}
+_cache_lock = threading.Lock()
+
+
+def get_plan(nx: int, ny: int, batch: int, inverse: bool, precision: str, device) -> Plan:
+    key = (nx, ny, batch, inverse, precision, torch.device(device).index)
+    with _cache_lock:
+        p = _cache.get(key)
+        if p is None:
+            with torch.cuda.device(device):
+                p = Plan(nx, ny, batch, inverse, precision)
+            _cache[key] = p
+        return p
+
+
+def _shape(x: torch.Tensor):
+    if x.dim() < 2:
+        raise ValueError("fft2 needs at least 2 dimensions ([..., ny, nx])")
+    ny, nx = x.shape[-2], x.shape[-1]
+    return nx, ny, max(1, x.numel() // max(1, nx * ny))
+
+
+class FFT2Function(torch.autograd.Function):
+    """Differentiable 2D transform: forward = fft_execute, backward = fft_backward
+    (the conjugate-transpose transform, PyTorch's conjugate-Wirtinger VJP)."""
+
+    @staticmethod
+    def forward(ctx, x, inverse: bool = False, precision: str = "fp32"):
+        x = x.contiguous()
+        nx, ny, batch = _shape(x)
+        plan = get_plan(nx, ny, batch, inverse, precision, x.device)
+        ctx.plan = plan
+        return plan.execute(x)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.plan.backward(grad.contiguous()), None, None
+
+
+def fft2(x: torch.Tensor, inverse: bool = False, precision: str = "fp32") -> torch.Tensor:
+    """Unnormalised 2D DFT over the last two axes of a complex64 CUDA tensor."""
+    return FFT2Function.apply(x, inverse, precision)
+
+
+class WeightedPowerLoss(torch.autograd.Function):
+    """L = sum w * |FFT2(x)|^2 with a fused adjoint: dL/dx = 2 F^H (w (.) F x),
+    the weighting folded into the adjoint's first pass (fft_backward_weighted)."""
+
+    @staticmethod
+    def forward(ctx, x, w, precision: str = "fp32"):
+        x = x.contiguous()
+        w = w.contiguous()
+        nx, ny, batch = _shape(x)
+        plan = get_plan(nx, ny, batch, False, precision, x.device)
+        X = plan.execute(x)
+        ctx.plan = plan
+        ctx.save_for_backward(X, w)
+        return plan.weighted_power(X, w).to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, gL):
+        X, w = ctx.saved_tensors
+        scale = 2.0 * float(gL)
+        return ctx.plan.backward_weighted(X, w, scale), None, None
+
+
+def weighted_power_loss(x: torch.Tensor, w: torch.Tensor, precision: str = "fp32") -> torch.Tensor:
+    return WeightedPowerLoss.apply(x, w, precision)
+
+
+def reorder_map(n: int, axis: int = 0, device="cuda") -> torch.Tensor:
+    """Output position of each input index under the kernels' data movement
+    alone (identity butterflies): the fused digit reversal."""
+    lib = N.load()
+    m = torch.empty(n, dtype=torch.int32, device=device)
+    N.check(lib.fft_debug_reorder_map(n, axis, m.data_ptr(), _stream_handle(m.device)),
+            "fft_debug_reorder_map")
+    return m
+
+
+def radices(n: int, axis: int = 0) -> list:
+    lib = N.load()
+    buf = (ctypes.c_int * 16)()
+    k = lib.fft_debug_radices(n, axis, buf)
+    if k < 0:
+        raise N.FFTError(k, "fft_debug_radices")
+    return [buf[i] for i in range(k)]

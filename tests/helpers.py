@@ -1,0 +1,47 @@
+"""Shared test utilities: error metric, tolerances, digit reversal."""
+import math
+import os
+
+import numpy as np
+
+ORACLE_THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def rel_l2(got, ref) -> float:
+    got = np.asarray(got, dtype=np.complex128).ravel()
+    ref = np.asarray(ref, dtype=np.complex128).ravel()
+    den = np.linalg.norm(ref)
+    return float(np.linalg.norm(got - ref) / (den if den > 0 else 1.0))
+
+
+def worst_rel_l2(got, ref, per) -> float:
+    """Worst relative L2 error over transforms of `per` elements each."""
+    got = np.asarray(got).reshape(-1, per)
+    ref = np.asarray(ref).reshape(-1, per)
+    return max(rel_l2(g, r) for g, r in zip(got, ref))
+
+
+def tol_fp32(N: int) -> float:
+    """Plain FP32 path bound: rel L2 <= 2e-7 * log2(N), N points per transform."""
+    return 2e-7 * max(1.0, math.log2(N))
+
+
+def tol_split_tc(N: int) -> float:
+    return 1e-6 * max(1.0, math.log2(N))
+
+
+def digit_reversal(n: int, radices) -> np.ndarray:
+    """map[i] for the mixed-radix digit reversal: write i with digits d_0 (radix
+    R_0, most significant) ... d_{S-1}, then map[i] = d_0 + d_1 R_0 + d_2 R_0 R_1 + ..."""
+    i = np.arange(n, dtype=np.int64)
+    out = np.zeros(n, dtype=np.int64)
+    w = n
+    mult = 1
+    rem = i.copy()
+    for R in radices:
+        w //= R
+        d = rem // w
+        rem = rem % w
+        out += d * mult
+        mult *= R
+    return out

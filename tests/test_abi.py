@@ -1,0 +1,117 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol include/gb300fft.h declares, and its host-side logic (argument
+validation, error strings, stage schedules) behaves -- no GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests.helpers import digit_reversal
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gb300fft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_15437_gb300 import build
+    build.build()
+    from paper_2506_15437_gb300 import _native
+    return _native.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(fft_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_core_abi():
+    names = declared_functions()
+    for n in ["fft_plan_create", "fft_execute", "fft_backward", "fft_plan_destroy",
+              "fft_plan_create_ragged", "fft_execute_ragged", "fft_plan_status",
+              "fft_debug_reorder_map"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in gb300fft.h but not exported"
+
+
+def test_binding_covers_header():
+    from paper_2506_15437_gb300 import _native
+    bound = {n for n, _, _ in _native.SIGNATURES}
+    assert set(declared_functions()) == bound
+
+
+def test_error_strings(lib):
+    for code in [0, -1, -2, -3, -4, -5, -6, 12345]:
+        s = lib.fft_error_string(code)
+        assert isinstance(s, bytes) and len(s) > 0
+    assert b"timed out" in lib.fft_error_string(-6)
+
+
+@pytest.mark.parametrize("nx,ny,batch", [(3, 4, 1), (4, 6, 1), (0, 8, 1), (8, 8, 0),
+                                         (16384, 2, 1), (2, 16384, 1), (-4, 4, 1)])
+def test_invalid_sizes_rejected_without_touching_the_gpu(lib, nx, ny, batch):
+    assert lib.fft_plan_create(nx, ny, batch, -1, 0) is None
+    assert lib.fft_last_error() == -1
+
+
+def test_invalid_direction_and_precision(lib):
+    assert lib.fft_plan_create(8, 8, 1, 0, 0) is None
+    assert lib.fft_last_error() == -2
+    assert lib.fft_plan_create(8, 8, 1, -1, 7) is None
+    assert lib.fft_last_error() == -2
+
+
+def test_null_plan_calls(lib):
+    assert lib.fft_plan_destroy(None) == 0
+    assert lib.fft_execute(None, None, None, None) == -2
+    assert lib.fft_backward(None, None, None, None) == -2
+    assert lib.fft_plan_status(None, None) == -2
+    off = ctypes.c_longlong(0)
+    assert lib.fft_ragged_offset(None, 0, ctypes.byref(off)) < 0
+
+
+def test_ragged_rejects_out_of_range_sizes(lib):
+    nx = (ctypes.c_int * 2)(32, 2048)
+    ny = (ctypes.c_int * 2)(32, 32)
+    assert lib.fft_plan_create_ragged(2, nx, ny, -1, 0) is None
+    assert lib.fft_last_error() in (-1, -5)
+    assert lib.fft_plan_create_ragged(0, nx, ny, -1, 0) is None
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_stage_schedules(lib, axis):
+    buf = (ctypes.c_int * 16)()
+    for L in range(0, 14):
+        n = 1 << L
+        k = lib.fft_debug_radices(n, axis, buf)
+        assert k >= 1
+        rad = [buf[i] for i in range(k)]
+        assert int(np.prod(rad)) == n
+        assert all(r & (r - 1) == 0 for r in rad)
+        assert all(r <= 32 for r in rad)
+    assert lib.fft_debug_radices(12, axis, buf) < 0
+
+
+def test_digit_reversal_helper_is_a_bijection_and_bit_reversal_for_radix2():
+    for L in range(1, 12):
+        n = 1 << L
+        m = digit_reversal(n, [2] * L)
+        assert sorted(m) == list(range(n))
+        br = [int(format(i, f"0{L}b")[::-1], 2) for i in range(n)]
+        assert list(m) == br
+
+
+def test_product_path_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    import paper_2506_15437_gb300 as g
+    x = torch.zeros(8, 8, dtype=torch.complex64)
+    with pytest.raises((ValueError, RuntimeError)):
+        g.fft2(x)

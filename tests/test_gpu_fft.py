@@ -1,0 +1,213 @@
+"""GPU parity of the plain FP32 path against the FP64 oracle (same seeded
+inputs on both sides), through the C ABI via the ctypes binding.
+
+Bar: relative L2 error per transform <= 2e-7 * log2(nx*ny); the reorder
+index maps bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import ORACLE_THREADS, digit_reversal, rel_l2, tol_fp32, worst_rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_15437_gb300 import build
+    build.build()
+    import paper_2506_15437_gb300 as g
+    return g
+
+
+def run_plan(g, x: np.ndarray, inverse=False, inplace=False):
+    ny, nx = x.shape[-2], x.shape[-1]
+    batch = x.size // (nx * ny)
+    plan = g.get_plan(nx, ny, batch, inverse, "fp32", "cuda")
+    d = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = plan.execute(d, out=d if inplace else None)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return out.cpu().numpy()
+
+
+def check_full(g, x, inverse=False, inplace=False):
+    ny, nx = x.shape[-2], x.shape[-1]
+    got = run_plan(g, x, inverse, inplace)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    err = worst_rel_l2(got, ref, nx * ny)
+    assert err <= tol_fp32(nx * ny), (x.shape, inverse, err, tol_fp32(nx * ny))
+    return err
+
+
+# every power-of-two shape with nx*ny <= 2^16 and a ragged batch of 3
+SHAPES = [(1 << ly, 1 << lx) for ly in range(0, 14) for lx in range(0, 14)
+          if (1 << lx) * (1 << ly) <= (1 << 16)]
+
+
+@pytest.mark.parametrize("ny,nx", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+def test_small_shapes_forward_and_inverse(g, ny, nx):
+    x = synth.uniform_complex((3, ny, nx), seed=1000 + 31 * nx + ny)
+    check_full(g, x, inverse=False)
+    check_full(g, x, inverse=True)
+
+
+def test_config1_256x256(g):
+    x = synth.uniform_complex((256, 256), seed=2506)
+    err = check_full(g, x)
+    assert err < 2e-7 * 16
+
+
+@pytest.mark.parametrize("n", [1024, 2048, 4096])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_config2_square_full(g, n, inverse):
+    x = synth.normal_complex((n, n), seed=2506)
+    check_full(g, x, inverse=inverse)
+
+
+@pytest.mark.parametrize("inverse", [False, True])
+def test_config2_8192_sampled(g, inverse):
+    """8192^2 in the bench's launch configuration: sampled output rows and
+    columns against the oracle's one-row / one-column evaluation, plus
+    Parseval over the whole transform."""
+    n = 8192
+    x = synth.normal_complex((n, n), seed=2506)
+    got = run_plan(g, x, inverse)
+    d = 1 if inverse else -1
+    rng = np.random.default_rng(7)
+    ky = np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 4)])
+    kx = np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 4)])
+    rows = oracle.fft2d_rows(x, ky, dir=d, threads=ORACLE_THREADS)
+    cols = oracle.fft2d_cols(x, kx, dir=d, threads=ORACLE_THREADS)
+    tol = tol_fp32(n * n)
+    for t, k in enumerate(ky):
+        assert rel_l2(got[k], rows[t]) <= tol, ("row", k)
+    for t, k in enumerate(kx):
+        assert rel_l2(got[:, k], cols[t]) <= tol, ("col", k)
+    e_in = np.sum(np.abs(x.astype(np.complex128)) ** 2)
+    e_out = np.sum(np.abs(got.astype(np.complex128)) ** 2)
+    assert abs(e_out / (n * n * e_in) - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("ny,nx", [(8192, 2), (2, 8192), (8192, 16), (16, 8192), (4096, 64),
+                                   (32, 4096), (8192, 8), (1, 8192), (8192, 1)])
+def test_extreme_aspect_ratios(g, ny, nx):
+    x = synth.uniform_complex((ny, nx), seed=ny + 7 * nx)
+    check_full(g, x)
+    check_full(g, x, inverse=True)
+
+
+def test_batched_2d(g):
+    x = synth.uniform_complex((5, 128, 512), seed=3)
+    check_full(g, x)
+
+
+def test_batch_of_1d_signals_4096(g):
+    """nx=4096, ny=1, batch 16384 (the 1D batch workload), sampled signals."""
+    x, _ = synth.exp_mix_1d(16384, 4096, seed=2506)
+    plan = g.get_plan(4096, 1, 16384, False, "fp32", "cuda")
+    out = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    idx = np.array([0, 1, 777, 8191, 16383])
+    ref = oracle.fft1d_batch(x[idx], threads=ORACLE_THREADS)
+    assert worst_rel_l2(out[idx], ref, 4096) <= tol_fp32(4096)
+
+
+def test_exponential_spikes_2048(g):
+    """Unit exponentials land exactly on their bins (N there, ~0 elsewhere)."""
+    n = 2048
+    x, freqs = synth.exp_mix_2d(n, n, seed=11)
+    noise_free = np.zeros((n, n), np.complex64)
+    yy = np.arange(n)[:, None]
+    xx = np.arange(n)[None, :]
+    for fy, fx in freqs:
+        noise_free += np.exp(2j * np.pi * (((fx * xx) % n) / n + ((fy * yy) % n) / n)).astype(np.complex64)
+    got = run_plan(g, noise_free)
+    want = np.zeros((n, n), np.complex128)
+    for fy, fx in freqs:
+        want[fy, fx] += n * n
+    assert rel_l2(got, want) < 2e-7 * 22
+
+
+def test_inplace_equals_out_of_place(g):
+    x = synth.normal_complex((2, 1024, 2048), seed=5)
+    a = run_plan(g, x, inplace=False)
+    b = run_plan(g, x, inplace=True)
+    assert np.array_equal(a, b)
+
+
+def test_inverse_of_forward_is_N_times_identity(g):
+    n = 1024
+    x = synth.uniform_complex((n, n), seed=9)
+    d = torch.from_numpy(x).cuda()
+    X = g.get_plan(n, n, 1, False, "fp32", "cuda").execute(d)
+    y = g.get_plan(n, n, 1, True, "fp32", "cuda").execute(X)
+    assert rel_l2(y.cpu().numpy(), n * n * x.astype(np.complex128)) <= 2 * tol_fp32(n * n)
+
+
+def test_adjoint_dot_product(g):
+    """<F x, y> == <x, F^H y>: fft_backward is the conjugate transpose."""
+    ny, nx = 512, 256
+    x = synth.uniform_complex((ny, nx), seed=1)
+    y = synth.uniform_complex((ny, nx), seed=2)
+    plan = g.get_plan(nx, ny, 1, False, "fp32", "cuda")
+    Fx = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+    FHy = plan.backward(torch.from_numpy(y).cuda()).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(y.astype(np.complex128), Fx)
+    rhs = np.vdot(FHy, x.astype(np.complex128))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_graph_capture_matches_eager(g):
+    n = 1024
+    x = torch.from_numpy(synth.uniform_complex((n, n), seed=4)).cuda()
+    plan = g.get_plan(n, n, 1, False, "fp32", "cuda")
+    out = torch.empty_like(x)
+    eager = plan.execute(x).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.execute(x, out=out)  # warm the tensor-map cache outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.execute(x, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+
+
+def test_misaligned_pointer_rejected(g):
+    n = 64
+    buf = torch.zeros(n * n + 1, dtype=torch.complex64, device="cuda")
+    plan = g.get_plan(n, n, 1, False, "fp32", "cuda")
+    from paper_2506_15437_gb300 import _native as N
+    lib = N.load()
+    rc = lib.fft_execute(plan._p, buf.data_ptr() + 8, buf.data_ptr() + 8,
+                         torch.cuda.current_stream().cuda_stream)
+    assert rc == N.FFT_ERR_INVALID_ARG
+
+
+def test_rejects_wrong_dtype_and_size(g):
+    plan = g.get_plan(64, 64, 1, False, "fp32", "cuda")
+    with pytest.raises(TypeError):
+        plan.execute(torch.zeros(64, 64, dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.execute(torch.zeros(64, 32, dtype=torch.complex64, device="cuda"))
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_reorder_map_bit_exact(g, axis):
+    """The kernels' data movement alone (identity butterflies) is exactly the
+    mixed-radix digit reversal of their stage radices, for every length."""
+    for L in range(1, 14):
+        n = 1 << L
+        m = g.reorder_map(n, axis).cpu().numpy().astype(np.int64)
+        rad = g.radices(n, axis)
+        assert np.array_equal(np.sort(m), np.arange(n)), (n, "not a bijection")
+        assert np.array_equal(m, digit_reversal(n, rad)), (n, axis, rad)
