@@ -20,6 +20,7 @@ template <int N, int E, int W>
 struct ColShape {
     static constexpr int T = N / E;
     static constexpr int THREADS = T * W;
+    static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS : (THREADS >= 256 && E < 32 ? 3 : 1);
     using Eng = Engine<N, E, W, PadShift<E>::value>;
     static constexpr int ELEMS = Eng::SMEM_ELEMS > N * W ? Eng::SMEM_ELEMS : N * W;
     static constexpr int BOXR = N < 256 ? N : 256;
@@ -28,10 +29,16 @@ struct ColShape {
     static constexpr size_t SMEM = BAR_OFF + 16;
 };
 
+// With a column pre-split of P (see the row pass), each [ny][nx] slice holds
+// P independent column blocks of N = ny/P rows: block kp is the row set
+// {kp + P*i : i < N}, and its output element i belongs in row kp + P*i too, so
+// every tile reads and writes the same rows and the pass stays in place.  The
+// tensor map is 3D -- (float within row, kp, slice*N + i) -- so one TMA box
+// gathers BOXR rows P apart.
 template <int N, int E, int W>
-__global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
+__global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>::MINB)
     k_cols(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw, int nx,
-           int batch, int conj_out, int *status) {
+           int batch, int P, int conj_out, int *status, int pf_dist) {
     using Sh = ColShape<N, E, W>;
     using Eng = typename Sh::Eng;
     constexpr int R0 = Eng::R0;
@@ -45,22 +52,24 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
     const int c = t % W;
     const int tt = t / W;
     const int groups_x = nx / W;
-    const long long ntiles = (long long)groups_x * batch;
+    const long long ntiles = (long long)groups_x * P * batch;
     const float so = conj_out ? -1.f : 1.f;
+    // tile id -> (column group, kp, first row coordinate of its block)
+    auto tile_x = [&](long long id) { return (int)(id % groups_x) * 2 * W; };
+    auto tile_kp = [&](long long id) { return (int)((id / groups_x) % P); };
+    auto tile_z = [&](long long id) { return (int)((id / groups_x) / P) * N; };
 
     auto issue = [&](long long id) {  // thread 0: TMA loads of tile `id`
-        const int b = (int)(id / groups_x);
-        const int x = (int)(id % groups_x) * 2 * W;
+        const int x = tile_x(id), kp = tile_kp(id), z0 = tile_z(id);
         mbar_expect_tx(bar, Sh::TILE_BYTES);
 #pragma unroll 1
         for (int k = 0; k < N / Sh::BOXR; ++k)
-            tma_load_2d(tile + k * Sh::BOXR * W, &map, x, b * N + k * Sh::BOXR, bar);
+            tma_load_3d(tile + k * Sh::BOXR * W, &map, x, kp, z0 + k * Sh::BOXR, bar);
     };
     auto prefetch = [&](long long id) {  // thread 0: bulk L2 prefetch of tile `id`
-        const int b = (int)(id / groups_x);
-        const int x = (int)(id % groups_x) * 2 * W;
+        const int x = tile_x(id), kp = tile_kp(id), z0 = tile_z(id);
 #pragma unroll 1
-        for (int k = 0; k < N / Sh::BOXR; ++k) tma_prefetch_2d(&map, x, b * N + k * Sh::BOXR);
+        for (int k = 0; k < N / Sh::BOXR; ++k) tma_prefetch_3d(&map, x, kp, z0 + k * Sh::BOXR);
     };
 
     if (t == 0) {
@@ -73,7 +82,8 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
     uint32_t phase = 0;
     if (t == 0 && id < ntiles) {
         issue(id);
-        if (id + gridDim.x < ntiles) prefetch(id + gridDim.x);
+        for (int d = 1; d <= pf_dist; ++d)
+            if (id + (long long)d * gridDim.x < ntiles) prefetch(id + (long long)d * gridDim.x);
     }
     for (; id < ntiles; id += gridDim.x) {
         if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
@@ -87,8 +97,11 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
         }
         phase ^= 1;
         const long long next = id + gridDim.x;
-        const int b = (int)(id / groups_x);
-        float2 *dst = out + (long long)b * N * nx + (long long)(id % groups_x) * W;
+        const long long blk = id / groups_x;  // b*P + kp
+        const long long b = blk / P;
+        const int kp = (int)(blk - b * P);
+        float2 *dst = out + (b * N * P + kp) * (long long)nx + (long long)(id % groups_x) * W;
+        const long long rstride = (long long)P * nx;
 
         float2 v[E];
 #pragma unroll
@@ -102,12 +115,13 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS)
             if (t == 0 && next < ntiles) {
                 fence_proxy_async_smem();
                 issue(next);
-                if (next + gridDim.x < ntiles) prefetch(next + gridDim.x);
+                const long long pf = next + (long long)pf_dist * gridDim.x;
+                if (pf_dist > 0 && pf < ntiles) prefetch(pf);
             }
         };
         auto store = [&](int i, int cc, float2 x) {
             x.y *= so;
-            dst[(long long)i * nx + cc] = x;
+            dst[(long long)i * rstride + cc] = x;
         };
         Eng::template run<FftPolicy, true>(v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
     }
@@ -221,9 +235,11 @@ const ColEntry *col_entry(int log2n, int e, int w) {
 
 int default_col_e(int n) { return n >= 16 ? 16 : n; }
 
-// Widest tile that keeps the staged tile near 64 KiB, within the row length.
+// Widest tile that keeps the staged tile within 128 KiB and the row length:
+// rows of at least 32 bytes (W >= 4) make whole DRAM sectors, which the TMA
+// moves far faster than 16-byte rows.
 int default_col_w(int n, int nx) {
-    int w = 8192 / n;
+    int w = 16384 / n;
     if (w > 16) w = 16;
     if (w < 2) w = 2;
     while (w > nx) w >>= 1;
@@ -245,14 +261,15 @@ int col_ctas_per_sm(const ColVariant &v) {
 }
 
 cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
-                        int nx, int batch, int conj_out, int *status, int grid, cudaStream_t s) {
+                        int nx, int batch, int split, int conj_out, int *status, int grid, int pf_dist,
+                        cudaStream_t s) {
     if (v.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return e;
     }
     CUtensorMap m = map;
-    void *args[] = {(void *)&m, (void *)&out, (void *)&tw, (void *)&nx, (void *)&batch, (void *)&conj_out,
-                    (void *)&status};
+    void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&nx,     (void *)&batch,
+                    (void *)&split, (void *)&conj_out, (void *)&status, (void *)&pf_dist};
     return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 

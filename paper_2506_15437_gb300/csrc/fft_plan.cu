@@ -39,6 +39,9 @@ struct AxisPlan {
     float2 *tw = nullptr;
     int n = 1;
     int grid = 0;  // column pass: persistent grid size
+    // column pass: cached tensor map of the last output pointer
+    CUtensorMap map;
+    const void *map_base = nullptr;
 };
 
 }  // namespace
@@ -48,13 +51,18 @@ struct fft_plan_s {
     int nx = 1, ny = 1, batch = 1, dir = FFT_FORWARD, prec = FFT_PREC_FP32;
     int device = 0;
     int num_sms = 0;
-    AxisPlan rows;  // length nx (or ny when nx == 1)
-    AxisPlan cols;  // length ny, used when nx > 1 and ny > 1
+    AxisPlan rows;        // length nx (or ny when nx == 1)
+    AxisPlan cols;        // length ny, used when nx > 1 and ny > 1
+    AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
+    int split = 1;        // column pre-split P done by the row pass (out of place only)
+    float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
+    int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]
+    bool ring = false;    // long rows: TMA landing-ring row kernel
+    int row_persist = -1;  // row pass grid: 1 persistent, 0 one CTA per group, -1 persistent iff split
+    int row_pf = 1;        // persistent row pass: L2 prefetch distance in groups
+    int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
     int *status = nullptr;  // device status word
     int wp_parts = 0;
-    // cached tensor map of the last `out` pointer
-    CUtensorMap map;
-    const void *map_base = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
     std::vector<void *> allocations;
 };
@@ -107,7 +115,12 @@ bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
     ax.n = n;
     if (n == 1) return FFT_OK;
-    ax.row = row_variant(ilog2(n), default_row_e(n));
+    int e = default_row_e(n);
+    if (const char *ev = getenv("GB300FFT_ROW_E")) {
+        const int forced = atoi(ev);
+        if (row_variant(ilog2(n), forced)) e = forced;
+    }
+    ax.row = row_variant(ilog2(n), e);
     if (!ax.row) return FFT_ERR_UNSUPPORTED;
     if (ax.row->tw_size > 0) {
         ax.tw = dev_alloc<float2>(p, ax.row->tw_size);
@@ -116,13 +129,30 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
     }
     if (ax.row->smem > 48 * 1024)
         cudaFuncSetAttribute(ax.row->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ax.row->smem);
+    // long rows may go through the TMA landing-ring kernel (same E = 16
+    // schedule and twiddle table as the plain row kernel); off by default,
+    // the plain persistent kernel measured faster
+    p->ring = false;
+    if (const char *ev = getenv("GB300FFT_ROW_PERSIST")) p->row_persist = atoi(ev);
+    if (const char *ev = getenv("GB300FFT_ROW_PF")) p->row_pf = atoi(ev);
+    if (const char *ev = getenv("GB300FFT_COL_PF")) p->col_pf = atoi(ev);
+    if (const char *ev = getenv("GB300FFT_RING")) p->ring = ring_rows_available(n) && ax.row->e == 16 && atoi(ev) != 0;
     return FFT_OK;
 }
 
 int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_per_w) {
     ax.n = n;
-    const int w = default_col_w(n, nx);
-    ax.col = col_variant(ilog2(n), default_col_e(n), w);
+    int w = default_col_w(n, nx);
+    int e = default_col_e(n);
+    if (const char *ev = getenv("GB300FFT_COL_E")) {
+        const int forced = atoi(ev);
+        if (col_variant(ilog2(n), forced, w)) e = forced;
+    }
+    if (const char *ev = getenv("GB300FFT_COL_W")) {
+        const int forced = atoi(ev);
+        if (forced >= 2 && forced <= nx && col_variant(ilog2(n), e, forced)) w = forced;
+    }
+    ax.col = col_variant(ilog2(n), e, w);
     if (!ax.col) return FFT_ERR_UNSUPPORTED;
     if (ax.col->tw_size > 0) {
         ax.tw = dev_alloc<float2>(p, ax.col->tw_size);
@@ -154,23 +184,33 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         return FFT_OK;
     }
     const bool two_pass = p->cols.col != nullptr;
+    // the pre-split pairs rows across CTAs, so an in-place call must not use it
+    const int P = (two_pass && src != dst) ? p->split : 1;
+    AxisPlan &cp = (P > 1) ? p->cols_split : p->cols;
     const long long nrows = total / p->rows.n;
+    int &grid = p->row_grid[weight ? 1 : 0][P > 1 ? 1 : 0];
+    if (grid == 0)
+        grid = p->ring ? ring_rows_grid(p->rows.n, nrows, P, p->num_sms, weight != nullptr)
+                       : row_grid(*p->rows.row, nrows, p->num_sms, weight != nullptr, P,
+                                  p->row_persist < 0 ? P > 1 : p->row_persist != 0);
     if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (launch_rows(*p->rows.row, src, dst, p->rows.tw, nrows, inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, weight,
-                    wscale, s) != cudaSuccess)
-        return FFT_ERR_CUDA;
+    const cudaError_t er =
+        p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
+                                   (inv && !two_pass) ? 1 : 0, weight, wscale, p->status, grid, s)
+                : launch_rows(*p->rows.row, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
+                              (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, s);
+    if (er != cudaSuccess) return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
     if (!two_pass) {
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
-    if (p->map_base != out) {
-        if (encode_col_map(&p->map, out, p->nx, (long long)p->ny * p->batch, p->cols.col->w,
-                           p->cols.col->box_rows) != 0)
+    if (cp.map_base != out) {
+        if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.col->w, cp.col->box_rows) != 0)
             return FFT_ERR_CUDA;
-        p->map_base = out;
+        cp.map_base = out;
     }
-    if (launch_cols(*p->cols.col, p->map, dst, p->cols.tw, p->nx, p->batch, inv ? 1 : 0, p->status, p->cols.grid,
+    if (launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid, p->col_pf,
                     s) != cudaSuccess)
         return FFT_ERR_CUDA;
     if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
@@ -182,14 +222,15 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
 namespace gb300fft {
 void set_last_error(int code) { t_last_error = code; }
 
-int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int w, int box_rows) {
+int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int split, int w, int box_rows) {
     EncodeTiledFn enc = get_encode_fn();
-    if (!enc) return -1;
-    cuuint64_t dims[2] = {(cuuint64_t)2 * nx, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(float2)};
-    cuuint32_t box[2] = {(cuuint32_t)(2 * w), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+    if (!enc || split < 1 || rows % split) return -1;
+    // (float within a row, kp, row block index): row r = kp + split * i
+    cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)split, (cuuint64_t)(rows / split)};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float2), (cuuint64_t)split * nx * sizeof(float2)};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * w), 1, (cuuint32_t)box_rows};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
@@ -259,6 +300,22 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
     } else {
         rc = setup_row_axis(p, p->rows, nx);
         if (rc == FFT_OK) rc = setup_col_axis(p, p->cols, ny, nx, (long long)nx * batch);
+        // Column pre-split: a length-8192 column needs a 128 KiB tile (one CTA
+        // per SM); splitting it as 2 x 4096 halves the tile.
+        int split = ny >= 8192 ? 2 : 1;
+        if (const char *ev = getenv("GB300FFT_SPLIT")) {
+            const int forced = atoi(ev);
+            if (forced == 1 || (forced == 2 && ny >= 4)) split = forced;
+        }
+        if (rc == FFT_OK && split > 1) {
+            rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split);
+            if (rc == FFT_OK) {
+                p->twp = dev_alloc<float2>(p, ny);
+                if (!p->twp) rc = FFT_ERR_ALLOC;
+                else if (build_roots(p->twp, ny, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+            }
+            if (rc == FFT_OK) p->split = split;
+        }
     }
     if (rc == FFT_OK) {
         p->status = dev_alloc<int>(p, 1);

@@ -20,57 +20,145 @@ struct RowShape {
     static constexpr int T = N / E;
     static constexpr int ROWS = (T >= 256) ? 1 : 256 / T;
     static constexpr int THREADS = ROWS * T;
+    // resident CTAs the register budget must allow: 64 registers per thread
+    // for 512-thread CTAs with E <= 16, at most 85 for 256-thread ones
+    static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS : (THREADS >= 256 && E < 32 ? 3 : 1);
     using Eng = Engine<N, E, 1, PadShift<E>::value>;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
 };
 
-template <int N, int E, bool WEIGHTED>
-__global__ void __launch_bounds__(RowShape<N, E>::THREADS)
-    k_rows(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw, long long nrows,
-           int conj_in, int conj_out, const float *__restrict__ weight, float wscale) {
+// Column pre-split (P > 1).  A column transform of length ny = P*Q can be
+// split as X[kp + P*kq] = sum_q w_Q^{q*kq} * w_ny^{q*kp} * (sum_p x[q + Q*p] w_P^{p*kp}).
+// With P > 1 the row pass computes the bracket -- the P-point DFT across the
+// rows q + Q*p and the scalar twiddle w_ny^{q*kp} -- while it loads, and
+// writes the transformed row to row kp + P*q; the column pass then runs
+// length-Q transforms over the row sets {kp + P*q : q < Q} and writes output
+// kq of set kp to row kp + P*kq, i.e. back into the rows it read.  Because the
+// row FFT acts along x and the split along y, the two commute and the result
+// is the same 2D DFT.  Output rows r and r+1 (kp = 0, 1) read the same input
+// rows, so neighbouring groups share them through L2.
+//
+// The grid is either one CTA per row group, or persistent: a CTA walks row
+// groups blockIdx.x, blockIdx.x + gridDim.x, ... and asks L2 for its next
+// group's rows (bulk prefetch) before transforming the current one.
+template <int N, int E, bool WEIGHTED, int P>
+__global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
+    k_rows(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
+           const float2 *__restrict__ twp, long long nrows, int ny, int conj_in, int conj_out,
+           const float *__restrict__ weight, float wscale, int pf_dist) {
     using Sh = RowShape<N, E>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
     constexpr int R0 = Eng::R0;
+    constexpr int ROWS = Sh::ROWS;
     extern __shared__ __align__(16) float2 smem[];
     const int g = threadIdx.x / T;
     const int tt = threadIdx.x - g * T;
-    const long long row = (long long)blockIdx.x * Sh::ROWS + g;
-    const bool active = row < nrows;
-    const float2 *src = in + row * N;
-    float2 *dst = out + row * N;
     const float si = conj_in ? -1.f : 1.f;
     const float so = conj_out ? -1.f : 1.f;
-
-    float2 v[E];
-#pragma unroll
-    for (int b = 0; b < E / R0; ++b) {
-        const int j = tt + b * T;
-#pragma unroll
-        for (int r = 0; r < R0; ++r) {
-            const int i = j + r * (N / R0);
-            float2 x = active ? __ldg(src + i) : make_float2(0.f, 0.f);
-            if constexpr (WEIGHTED) {
-                const float wv = active ? __ldg(weight + row * N + i) * wscale : 0.f;
-                x.x *= wv;
-                x.y *= wv;
-            }
-            x.y *= si;
-            v[b * R0 + r] = x;
-        }
-    }
+    const int Q = ny / P;
     float2 *sm = smem + g * Eng::SMEM_ELEMS;
-    auto store = [&](int i, int, float2 x) {
-        if (active) {
-            x.y *= so;
-            dst[i] = x;
+    const long long step = (long long)gridDim.x * ROWS;
+
+    // first input row of output row r, for input part p (P == 1: r itself)
+    auto in_row = [&](long long r, int p) -> long long {
+        if constexpr (P == 1) {
+            return r;
+        } else {
+            const long long b = r / ny;
+            const int y = (int)(r - b * ny);
+            return b * ny + (y / P) + (long long)Q * p;
         }
     };
-    auto none = [] {};
-    if constexpr (Eng::NT >= 32)
-        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncBlock{}, none, store);
-    else
-        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncWarp{}, none, store);
+
+    bool first = true;
+    if (threadIdx.x == 0 && pf_dist > 1) {  // warm L2 with the groups after the first
+        for (int d = 1; d < pf_dist; ++d) {
+            const long long nb = (long long)blockIdx.x * ROWS + d * step;
+            if (nb >= nrows) break;
+            if constexpr (P == 1) {
+                const long long cnt = (nrows - nb) < ROWS ? (nrows - nb) : ROWS;
+                bulk_prefetch_l2(in + nb * N, (uint32_t)(cnt * N * sizeof(float2)));
+            } else {
+                for (int gg = 0; gg < ROWS && nb + gg < nrows; ++gg)
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        bulk_prefetch_l2(in + in_row(nb + gg, p) * N, (uint32_t)(N * sizeof(float2)));
+            }
+        }
+    }
+    for (long long base = (long long)blockIdx.x * ROWS; base < nrows; base += step) {
+        const long long nb = base + (long long)(pf_dist > 0 ? pf_dist : 1) * step;
+        if (threadIdx.x == 0 && pf_dist > 0 && nb < nrows) {
+            if constexpr (P == 1) {
+                const long long cnt = (nrows - nb) < ROWS ? (nrows - nb) : ROWS;
+                bulk_prefetch_l2(in + nb * N, (uint32_t)(cnt * N * sizeof(float2)));
+            } else {
+                for (int gg = 0; gg < ROWS && nb + gg < nrows; ++gg)
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        bulk_prefetch_l2(in + in_row(nb + gg, p) * N, (uint32_t)(N * sizeof(float2)));
+            }
+        }
+        if (!first) __syncthreads();  // the previous group's last shared-memory reads are done
+        first = false;
+
+        const long long row = base + g;
+        const bool active = row < nrows;
+        int kp = 0, q = 0;
+        if constexpr (P > 1) {
+            const int y = active ? (int)(row % ny) : 0;
+            kp = y % P;
+            q = y / P;
+        }
+        float2 v[E];
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) {
+            const int j = tt + b * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int i = j + r * (N / R0);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const long long ir = active ? in_row(row, p) : 0;
+                    float2 x = active ? __ldg(in + ir * N + i) : make_float2(0.f, 0.f);
+                    if constexpr (WEIGHTED) {
+                        const float wv = active ? __ldg(weight + ir * N + i) * wscale : 0.f;
+                        x.x *= wv;
+                        x.y *= wv;
+                    }
+                    x.y *= si;
+                    if constexpr (P == 1) {
+                        acc = x;
+                    } else {
+                        // P == 2: w_2^{p*kp} = (-1)^{p*kp}
+                        acc = (p == 1 && kp == 1) ? csub(acc, x) : cadd(acc, x);
+                    }
+                }
+                v[b * R0 + r] = acc;
+            }
+        }
+        if constexpr (P > 1) {
+            if (kp != 0) {
+                const float2 w = __ldg(twp + (long long)q * kp);
+#pragma unroll
+                for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
+            }
+        }
+        float2 *dst = out + row * N;
+        auto store = [&](int i, int, float2 x) {
+            if (active) {
+                x.y *= so;
+                dst[i] = x;
+            }
+        };
+        auto none = [] {};
+        if constexpr (Eng::NT >= 32)
+            Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncBlock{}, none, store);
+        else
+            Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncWarp{}, none, store);
+    }
 }
 
 // Movement-only twin of k_rows for one row: integer tags instead of values,
@@ -101,7 +189,7 @@ __global__ void __launch_bounds__(N / E) k_rows_movemap(int *map) {
 // ---------------------------------------------------------------------------
 namespace {
 struct RowEntry {
-    RowVariant plain, weighted;
+    RowVariant plain, weighted, split2, split2_weighted;
     const void *movemap = nullptr;
     size_t movemap_smem = 0;
     int movemap_threads = 0;
@@ -122,10 +210,16 @@ RowEntry make_row_entry() {
     v.rows_per_cta = Sh::ROWS;
     v.smem = Sh::SMEM;
     v.tw_size = Sched<N, E>::tw_size;
-    v.fn = (const void *)k_rows<N, E, false>;
+    v.fn = (const void *)k_rows<N, E, false, 1>;
     en.plain = v;
-    v.fn = (const void *)k_rows<N, E, true>;
+    v.fn = (const void *)k_rows<N, E, true, 1>;
     en.weighted = v;
+    if constexpr (E == (N >= 16 ? 16 : N) || (E == 32 && N >= 4096)) {
+        v.fn = (const void *)k_rows<N, E, false, 2>;
+        en.split2 = v;
+        v.fn = (const void *)k_rows<N, E, true, 2>;
+        en.split2_weighted = v;
+    }
     en.movemap = (const void *)k_rows_movemap<N, E>;
     en.movemap_smem = sizeof(float2) * (size_t)Sh::Eng::SMEM_ELEMS;
     en.movemap_threads = N / E;
@@ -173,37 +267,51 @@ const RowEntry *row_entry(int log2n, int e) {
 }
 }  // namespace
 
-int default_row_e(int n) { return n >= 16 ? 16 : (n >= 8 ? 8 : n); }
+int default_row_e(int n) { return n >= 8192 ? 32 : n >= 16 ? 16 : (n >= 8 ? 8 : n); }
 
 const RowVariant *row_variant(int log2n, int e) {
     const RowEntry *en = row_entry(log2n, e);
     return en ? &en->plain : nullptr;
 }
 
-static const RowVariant *row_variant_weighted(int log2n, int e) {
-    const RowEntry *en = row_entry(log2n, e);
-    return en ? &en->weighted : nullptr;
+static const void *row_fn(const RowVariant &v, bool weighted, int split) {
+    const RowEntry *en = row_entry(ilog2(v.n), v.e);
+    if (!en) return nullptr;
+    const RowVariant &k = split == 2 ? (weighted ? en->split2_weighted : en->split2)
+                                     : (weighted ? en->weighted : en->plain);
+    return k.fn;
 }
 
-cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw,
-                        long long nrows, int conj_in, int conj_out, const float *weight,
-                        float wscale, cudaStream_t s) {
+int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, int split, bool persistent) {
+    const void *fn = row_fn(v, weighted, split);
+    if (!fn) return 0;
+    if (v.smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, v.threads, v.smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long groups = (nrows + v.rows_per_cta - 1) / v.rows_per_cta;
+    long long grid = persistent ? (long long)num_sms * per_sm : groups;
+    if (grid > groups) grid = groups;
+    if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
+    return grid < 1 ? 1 : (int)grid;
+}
+
+cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                        long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
+                        float wscale, int grid, int pf_dist, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
-    const void *fn = v.fn;
-    if (weight) {
-        const RowVariant *w = row_variant_weighted(ilog2(v.n), v.e);
-        if (!w) return cudaErrorInvalidValue;
-        fn = w->fn;
-    }
+    if (split != 1 && split != 2) return cudaErrorInvalidValue;
+    const void *fn = row_fn(v, weight != nullptr, split);
+    if (!fn) return cudaErrorInvalidValue;
     if (v.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return e;
     }
-    const long long grid = (nrows + v.rows_per_cta - 1) / v.rows_per_cta;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&nrows, (void *)&conj_in,
-                    (void *)&conj_out, (void *)&weight, (void *)&wscale};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    void *args[] = {(void *)&in,  (void *)&out,     (void *)&tw,       (void *)&twp,    (void *)&nrows,
+                    (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&weight, (void *)&wscale,
+                    (void *)&pf_dist};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s) {

@@ -52,6 +52,19 @@ cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+__global__ void k_roots(float2 *t, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double sv, cv;
+    sincospi(2.0 * (double)k / (double)n, &sv, &cv);
+    t[k] = make_float2((float)cv, (float)(-sv));
+}
+
+cudaError_t build_roots(float2 *t, int n, cudaStream_t s) {
+    k_roots<<<(n + 255) / 256, 256, 0, s>>>(t, n);
+    return cudaGetLastError();
+}
+
 // Partial sums of sum_i w[i] * |X[i]|^2: one float partial per CTA.  Each
 // thread keeps a compensated (Kahan) float sum over its grid-stride share,
 // then the CTA adds its threads' sums as a tree.  The caller adds the

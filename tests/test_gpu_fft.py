@@ -211,3 +211,32 @@ def test_reorder_map_bit_exact(g, axis):
         rad = g.radices(n, axis)
         assert np.array_equal(np.sort(m), np.arange(n)), (n, "not a bijection")
         assert np.array_equal(m, digit_reversal(n, rad)), (n, axis, rad)
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(16, 8, 3), (64, 32, 2), (256, 128, 1), (1024, 16, 2),
+                                         (4096, 4, 1), (8192, 2, 1)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_forced_column_presplit(g, monkeypatch, ny, nx, batch, inverse):
+    """The column pre-split (2-point DFT across rows y, y + ny/2 in the row
+    pass, length-ny/2 columns after) forced on shapes that would not use it."""
+    monkeypatch.setenv("GB300FFT_SPLIT", "2")
+    plan = g.Plan(nx, ny, batch, inverse=inverse)
+    monkeypatch.delenv("GB300FFT_SPLIT")
+    x = synth.uniform_complex((batch, ny, nx), seed=ny * nx + batch)
+    got = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.status() == 0
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    assert worst_rel_l2(got, ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.close()
+
+
+def test_presplit_inplace_falls_back_to_unsplit(g):
+    """In place, the pre-split pairing would overwrite rows a partner CTA
+    still reads, so in-place calls take the unsplit path; both agree."""
+    ny, nx = 8192, 64
+    x = synth.normal_complex((ny, nx), seed=21)
+    a = run_plan(g, x, inplace=False)
+    b = run_plan(g, x, inplace=True)
+    ref = oracle.fft2d(x, threads=ORACLE_THREADS)
+    assert rel_l2(a, ref) <= tol_fp32(nx * ny)
+    assert rel_l2(b, ref) <= tol_fp32(nx * ny)
