@@ -262,7 +262,41 @@ def forms(torch, g, steps, warmup, dev):
     out["fp32_1d_4096x16384"] = {"ms": ms, "GFLOP/s": flops_2d(4096, 1, 16384) / ms / 1e6,
                                  "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
     del x, y
+    out.update(ragged_form(torch, g, steps, dev))
     return out
+
+
+def time_fn(torch, fn, steps, warmup=3):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def ragged_form(torch, g, steps, dev):
+    """512 independent 2D FFTs, each axis log-uniform on 32..1024 (seed 2506):
+    one persistent launch replayed from a CUDA graph, against one plain
+    launch pair per instance."""
+    import synth
+    nx, ny, offs, packed = synth.ragged_batch(512, seed=SEED)
+    plan = g.RaggedPlan(nx, ny)
+    x = torch.from_numpy(packed).to(dev)
+    y = torch.empty_like(x)
+    fl = sum(flops_2d(int(a), int(b)) for a, b in zip(nx, ny))
+    ms_graph = time_fn(torch, lambda: plan.execute(x, out=y), max(10, steps // 4))
+    ms_loop = time_fn(torch, lambda: plan.execute_loop(x, out=y), max(5, steps // 10))
+    plan.close()
+    return {"ragged_512": {"ms_graph": ms_graph, "ms_loop": ms_loop, "GFLOP/s": fl / ms_graph / 1e6,
+                           "GFLOP/s_loop": fl / ms_loop / 1e6, "speedup_vs_loop": ms_loop / ms_graph,
+                           "points": int(packed.size),
+                           "HBM_GB/s_algorithmic_2pass": 32.0 * packed.size / ms_graph / 1e6}}
 
 
 def main():

@@ -6,6 +6,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/gb300fft.h"
+
 namespace gb300fft {
 
 constexpr int kMaxLog2 = 13;  // n <= 8192 per axis
@@ -79,4 +83,53 @@ void set_last_error(int code);
 int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int split, int w,
                    int box_rows);
 
+// One axis of a dense plan: a row-pass length (contiguous) or a column-pass
+// length (strided), its kernel variant and its twiddle table.
+struct AxisPlan {
+    const RowVariant *row = nullptr;
+    const ColVariant *col = nullptr;
+    float2 *tw = nullptr;
+    int n = 1;
+    int grid = 0;  // column pass: persistent grid size
+    // column pass: cached tensor map of the last output pointer
+    CUtensorMap map;
+    const void *map_base = nullptr;
+};
+
+
+struct RaggedState;
+void ragged_destroy(RaggedState *r);
+
+}  // namespace gb300fft
+
+// A plan (opaque to the C ABI): dense or ragged.
+struct fft_plan_s {
+    int kind = 0;  // 0 dense, 1 ragged
+    gb300fft::RaggedState *ragged = nullptr;
+    int nx = 1, ny = 1, batch = 1, dir = FFT_FORWARD, prec = FFT_PREC_FP32;
+    int device = 0;
+    int num_sms = 0;
+    gb300fft::AxisPlan rows;        // length nx (or ny when nx == 1)
+    gb300fft::AxisPlan cols;        // length ny, used when nx > 1 and ny > 1
+    gb300fft::AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
+    int split = 1;        // column pre-split P done by the row pass (out of place only)
+    float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
+    int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]
+    bool ring = false;    // long rows: TMA landing-ring row kernel
+    int row_persist = -1;  // row pass grid: 1 persistent, 0 one CTA per group, -1 persistent iff split
+    int row_pf = 1;        // persistent row pass: L2 prefetch distance in groups
+    int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
+    int *status = nullptr;  // device status word
+    int wp_parts = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
+    std::vector<void *> allocations;
+};
+
+namespace gb300fft {
+// out = DFT_sign(in) of a dense plan (optionally weighted by wscale * w on
+// load); returns an FFT_* code.  Defined in fft_plan.cu.
+int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
+              cudaStream_t s);
+// Frees a plan and everything it owns.
+void free_plan(fft_plan_s *p);
 }  // namespace gb300fft

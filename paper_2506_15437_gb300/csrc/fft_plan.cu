@@ -31,44 +31,6 @@ namespace {
 
 thread_local int t_last_error = FFT_OK;
 
-// One axis of a dense plan: a row-pass length (contiguous) or a column-pass
-// length (strided), its kernel variant and its twiddle table.
-struct AxisPlan {
-    const RowVariant *row = nullptr;
-    const ColVariant *col = nullptr;
-    float2 *tw = nullptr;
-    int n = 1;
-    int grid = 0;  // column pass: persistent grid size
-    // column pass: cached tensor map of the last output pointer
-    CUtensorMap map;
-    const void *map_base = nullptr;
-};
-
-}  // namespace
-
-struct fft_plan_s {
-    int kind = 0;  // 0 dense, 1 ragged
-    int nx = 1, ny = 1, batch = 1, dir = FFT_FORWARD, prec = FFT_PREC_FP32;
-    int device = 0;
-    int num_sms = 0;
-    AxisPlan rows;        // length nx (or ny when nx == 1)
-    AxisPlan cols;        // length ny, used when nx > 1 and ny > 1
-    AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
-    int split = 1;        // column pre-split P done by the row pass (out of place only)
-    float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
-    int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]
-    bool ring = false;    // long rows: TMA landing-ring row kernel
-    int row_persist = -1;  // row pass grid: 1 persistent, 0 one CTA per group, -1 persistent iff split
-    int row_pf = 1;        // persistent row pass: L2 prefetch distance in groups
-    int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
-    int *status = nullptr;  // device status word
-    int wp_parts = 0;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
-    std::vector<void *> allocations;
-};
-
-namespace {
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -104,11 +66,6 @@ T *dev_alloc(fft_plan_s *p, size_t count) {
     return static_cast<T *>(d);
 }
 
-void free_plan(fft_plan_s *p) {
-    if (!p) return;
-    for (void *d : p->allocations) cudaFree(d);
-    delete p;
-}
 
 bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
@@ -167,6 +124,16 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
     return FFT_OK;
 }
 
+}  // namespace
+
+namespace gb300fft {
+void free_plan(fft_plan_s *p) {
+    if (!p) return;
+    if (p->ragged) ragged_destroy(p->ragged);
+    for (void *d : p->allocations) cudaFree(d);
+    delete p;
+}
+
 // out = DFT_{sign}(in) (optionally weighted by scale*w on load) for a dense plan.
 int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
               cudaStream_t s) {
@@ -217,9 +184,6 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     return FFT_OK;
 }
 
-}  // namespace
-
-namespace gb300fft {
 void set_last_error(int code) { t_last_error = code; }
 
 int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int split, int w, int box_rows) {

@@ -205,3 +205,73 @@ def radices(n: int, axis: int = 0) -> list:
     if k < 0:
         raise N.FFTError(k, "fft_debug_radices")
     return [buf[i] for i in range(k)]
+
+
+class RaggedPlan:
+    """Many independent 2D transforms of mixed sizes (each axis a power of two
+    in 32..1024), packed back to back, run as one persistent launch from a
+    captured CUDA graph (fft_execute_ragged)."""
+
+    def __init__(self, nx, ny, inverse: bool = False, precision: str = "fp32"):
+        lib = N.load()
+        self._lib = lib
+        nx = [int(v) for v in nx]
+        ny = [int(v) for v in ny]
+        if len(nx) != len(ny):
+            raise ValueError("nx and ny must have the same length")
+        self.nx, self.ny = nx, ny
+        self.count = len(nx)
+        ax = (ctypes.c_int * self.count)(*nx)
+        ay = (ctypes.c_int * self.count)(*ny)
+        self.dir = N.FFT_INVERSE if inverse else N.FFT_FORWARD
+        self._p = lib.fft_plan_create_ragged(self.count, ax, ay, self.dir, _PREC[precision])
+        if not self._p:
+            raise N.FFTError(lib.fft_last_error(), "fft_plan_create_ragged")
+
+    def offset(self, i: int) -> int:
+        v = ctypes.c_longlong(0)
+        N.check(self._lib.fft_ragged_offset(self._p, int(i), ctypes.byref(v)), "fft_ragged_offset")
+        return int(v.value)
+
+    @property
+    def total(self) -> int:
+        return self.offset(self.count)
+
+    def _io(self, x, out):
+        _check_tensor(x, torch.complex64, "input")
+        if x.numel() != self.total:
+            raise ValueError(f"packed input has {x.numel()} elements, plan expects {self.total}")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _check_tensor(out, torch.complex64, "out")
+            if out.numel() != self.total:
+                raise ValueError("out has the wrong size")
+        return out
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self._io(x, out)
+        N.check(self._lib.fft_execute_ragged(self._p, x.data_ptr(), out.data_ptr(),
+                                             _stream_handle(x.device)), "fft_execute_ragged")
+        return out
+
+    def execute_loop(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The same transforms as one plain launch pair per instance (baseline)."""
+        out = self._io(x, out)
+        N.check(self._lib.fft_execute_ragged_loop(self._p, x.data_ptr(), out.data_ptr(),
+                                                  _stream_handle(x.device)), "fft_execute_ragged_loop")
+        return out
+
+    def status(self) -> int:
+        return self._lib.fft_plan_status(self._p, _stream_handle(torch.device("cuda")))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.fft_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
