@@ -144,6 +144,33 @@ int fft_execute_ragged(fft_plan_t p, const void *in, void *out, void *stream);
 int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *stream);
 
 /*
+ * fft_execute_ragged_noalloc -- the ragged transform of fft_execute_ragged
+ * (same persistent kernel, same packing: instance i starts at the sum of the
+ * earlier nx*ny) for callers that cannot allocate device memory, e.g. code
+ * running while a CUDA graph is being captured, or a process whose device
+ * memory belongs to a pool or framework allocator it must not go around.  The
+ * paper has no counterpart; it is an addition of this library.
+ *   count    1..1024 instances; nx[i], ny[i] powers of two in 32..1024 (host
+ *            arrays, read during the call); at most 65536 work items (one item
+ *            is 8192 elements of one pass; a 512 x 512 instance takes 64).
+ *            Larger requests return FFT_ERR_INVALID_SIZE without launching.
+ *   dir      FFT_FORWARD or FFT_INVERSE.
+ *   in, out  caller-owned device buffers of the packed batch (may be equal).
+ *   status   optional caller-owned device int: a kernel that times out on
+ *            its bounded wait writes FFT_ERR_TIMEOUT there (NULL: not reported).
+ * It allocates nothing.  Its scratch is one fixed array of about 1.1 MiB
+ * inside the library, present on every GPU that loads the library until the
+ * process exits.  The first call on each device looks up that array's address
+ * and fills its twiddle tables (a short synchronising set-up with the device
+ * current), so make it before any stream capture.  Every call reuses the same
+ * array and it keeps the previous call's contents; the call clears what must
+ * start at zero.  Calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race on the array: serialise them.
+ */
+int fft_execute_ragged_noalloc(int count, const int *nx, const int *ny, int dir, const void *in,
+                               void *out, int *status, void *stream);
+
+/*
  * fft_plan_status -- synchronise `stream`, return the plan's device status
  * word (FFT_OK, or the FFT_ERR_* a kernel recorded) and clear it.
  */

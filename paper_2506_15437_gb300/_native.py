@@ -43,6 +43,7 @@ SIGNATURES = [
     ("fft_ragged_offset", _I, [_P, _I, ctypes.POINTER(_LL)]),
     ("fft_execute_ragged", _I, [_P, _P, _P, _P]),
     ("fft_execute_ragged_loop", _I, [_P, _P, _P, _P]),
+    ("fft_execute_ragged_noalloc", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _P, _P, _P, _P]),
     ("fft_plan_status", _I, [_P, _P]),
     ("fft_plan_set_pass_events", _I, [_P, _P, _P, _P]),
     ("fft_debug_reorder_map", _I, [_I, _I, _P, _P]),

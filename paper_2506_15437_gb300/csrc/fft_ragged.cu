@@ -25,6 +25,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -627,3 +628,141 @@ int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *strea
 }
 
 }  // extern "C"
+
+namespace gb300fft {
+
+// ---------------------------------------------------------------------------
+// Ragged execution without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code running while a CUDA graph is
+// being captured, processes whose device memory is owned by a pool or a
+// framework allocator they must not bypass, and runtimes that forbid device
+// allocation after start-up.  fft_execute_ragged_noalloc serves them: it runs
+// the same persistent kernel as fft_execute_ragged, but its scratch (work
+// queue, instance table, offsets, completion counters and twiddle tables)
+// lives in the fixed array below instead of a plan.  The array is part of the
+// library image, so every GPU that loads the library holds its
+// kNoAllocBytes until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxCount = 1024;   // instances per call
+constexpr int kNoAllocMaxItems = 65536;  // work items per call
+constexpr size_t kNoAllocTwOffset = 0;   // twiddle tables, 2048 float2 (filled once per device)
+constexpr size_t kNoAllocTwElems = 2048;
+constexpr size_t kNoAllocItemsOffset = kNoAllocTwOffset + kNoAllocTwElems * sizeof(float2);
+constexpr size_t kNoAllocInstOffset = kNoAllocItemsOffset + (size_t)kNoAllocMaxItems * sizeof(int4);
+constexpr size_t kNoAllocOffsOffset = kNoAllocInstOffset + (size_t)kNoAllocMaxCount * sizeof(int4);
+constexpr size_t kNoAllocCountersOffset = kNoAllocOffsOffset + (size_t)(kNoAllocMaxCount + 1) * sizeof(long long);
+constexpr size_t kNoAllocBytes =
+    (kNoAllocCountersOffset + (size_t)(kNoAllocMaxCount + 1) * sizeof(int) + 255) / 256 * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+const float2 *g_noalloc_tw[kNoAllocMaxDevices][11] = {};
+
+// Once per device, with that device current: look up the array's device
+// address (the host-side symbol is only a stand-in) and fill the twiddle
+// tables.  Returns FFT_OK or an error code.
+int noalloc_setup(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[dev]) return FFT_OK;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return FFT_ERR_CUDA;
+    unsigned char *base = static_cast<unsigned char *>(ptr);
+    float2 *tw = reinterpret_cast<float2 *>(base + kNoAllocTwOffset);
+    size_t used = 0;
+    for (int l = 5; l <= 10; ++l) {
+        int rad[16];
+        const int S = schedule_radices(1 << l, kRagE, rad);
+        long long sz = 0, ns = rad[0];
+        for (int k = 1; k < S; ++k) {
+            sz += (long long)(rad[k] - 1) * ns;
+            ns *= rad[k];
+        }
+        if (used + (size_t)sz > kNoAllocTwElems) return FFT_ERR_UNSUPPORTED;
+        g_noalloc_tw[dev][l] = tw + used;
+        if (sz > 0 && build_twiddles(tw + used, 1 << l, kRagE, s) != cudaSuccess) return FFT_ERR_CUDA;
+        used += (size_t)sz;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FFT_ERR_CUDA;
+    g_noalloc_ptr[dev] = base;
+    return FFT_OK;
+}
+}  // namespace
+
+}  // namespace gb300fft (no-alloc helpers)
+
+extern "C" int fft_execute_ragged_noalloc(int count, const int *nx, const int *ny, int dir, const void *in, void *out,
+                                          int *status, void *stream) {
+    using namespace gb300fft;
+    auto pow2_in = [](int n) { return n >= 32 && n <= 1024 && (n & (n - 1)) == 0; };
+    if (count < 1 || count > kNoAllocMaxCount) return FFT_ERR_INVALID_SIZE;
+    if (!nx || !ny || !in || !out || (dir != FFT_FORWARD && dir != FFT_INVERSE)) return FFT_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) return FFT_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!pow2_in(nx[i]) || !pow2_in(ny[i])) return FFT_ERR_INVALID_SIZE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    int sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    const int rc0 = noalloc_setup(dev, s);
+    if (rc0 != FFT_OK) return rc0;
+    unsigned char *base = g_noalloc_ptr[dev];
+
+    // host-side schedule (same rules as a ragged plan)
+    RaggedState r;
+    r.count = count;
+    r.nx.assign(nx, nx + count);
+    r.ny.assign(ny, ny + count);
+    r.offs.resize(count + 1);
+    r.offs[0] = 0;
+    for (int i = 0; i < count; ++i) r.offs[i + 1] = r.offs[i] + (long long)nx[i] * ny[i];
+    int per_sm = 0;
+    if (cudaFuncSetAttribute((const void *)k_ragged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRagSmem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_ragged, kRagThreads, kRagSmem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return FFT_ERR_CUDA;
+    r.grid = sms * per_sm;
+    std::vector<int4> inst;
+    const std::vector<int4> items = build_items(r, r.grid, true, inst);
+    if (items.size() > (size_t)kNoAllocMaxItems) return FFT_ERR_INVALID_SIZE;
+
+    int4 *d_items = reinterpret_cast<int4 *>(base + kNoAllocItemsOffset);
+    int4 *d_inst = reinterpret_cast<int4 *>(base + kNoAllocInstOffset);
+    long long *d_offs = reinterpret_cast<long long *>(base + kNoAllocOffsOffset);
+    int *d_counters = reinterpret_cast<int *>(base + kNoAllocCountersOffset);
+    // pageable sources: each copy returns once the host data has been staged
+    if (cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_inst, inst.data(), inst.size() * sizeof(int4), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_offs, r.offs.data(), (count + 1) * sizeof(long long), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(d_counters, 0, (count + 1) * sizeof(int), s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    RagArgs a;
+    a.items = d_items;
+    a.nitems = (int)items.size();
+    a.inst = d_inst;
+    a.offs = d_offs;
+    a.in = static_cast<const float2 *>(in);
+    a.out = static_cast<float2 *>(out);
+    a.head = d_counters;
+    a.done = d_counters + 1;
+    a.status = status;
+    a.si = dir > 0 ? -1.f : 1.f;
+    a.so = dir > 0 ? -1.f : 1.f;
+    a.withhold = 0;
+    a.spin_limit_ns = 1000000000LL;
+    for (int k = 0; k < 11; ++k) a.tw.p[k] = g_noalloc_tw[dev][k];
+    void *args[] = {(void *)&a};
+    if (cudaLaunchKernel((const void *)k_ragged, dim3(r.grid), dim3(kRagThreads), args, kRagSmem, s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    return FFT_OK;
+}
