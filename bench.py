@@ -263,7 +263,31 @@ def forms(torch, g, steps, warmup, dev):
                                  "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
     del x, y
     out.update(ragged_form(torch, g, steps, dev))
+    out.update(diff_form(torch, g, steps, dev))
     return out
+
+
+def diff_form(torch, g, steps, dev):
+    """L = sum w * |FFT2(x)|^2 for x [8][2048][2048], w U[0,1): one step is the
+    forward transform, the loss reduction and the fused adjoint (gradient)."""
+    import synth
+    b, n = 8, 2048
+    x = torch.from_numpy(synth.uniform_complex((b, n, n), seed=SEED)).to(dev)
+    w = torch.from_numpy(synth.mask((b, n, n), seed=SEED + 1)).to(dev)
+    plan = g.get_plan(n, n, b, False, "fp32", dev)
+    X = torch.empty_like(x)
+    G = torch.empty_like(x)
+
+    def step():
+        plan.execute(x, out=X)
+        plan.weighted_power(X, w)
+        plan.backward_weighted(X, w, 2.0, out=G)
+
+    ms = time_fn(torch, step, max(10, steps // 4))
+    fl = 2 * flops_2d(n, n, b)
+    byts = 2 * 32.0 * b * n * n + 12.0 * b * n * n  # two 2-pass transforms, loss read, w read twice
+    return {"diff_8x2048x2048": {"ms": ms, "GFLOP/s_two_transforms": fl / ms / 1e6,
+                                 "HBM_GB/s_algorithmic": byts / ms / 1e6}}
 
 
 def time_fn(torch, fn, steps, warmup=3):
