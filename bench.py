@@ -254,6 +254,29 @@ def forms(torch, g, steps, warmup, dev):
                 "HBM_GB/s_algorithmic": 32.0 * n * n / ms / 1e6,
                 "note": "fits L2 (hot)" if n <= 2048 else "larger than L2"}
         del x, y
+    # split-FP16 tensor-core form on the precision workloads (noise + 8
+    # exponentials), beside the FP32 path; relative difference of the two
+    # results (the error against FP64 comes from the parity tests)
+    xe = torch.from_numpy(synth.exp_mix_2d(8192, 8192, seed=SEED)[0]).to(dev)
+    ye = torch.empty_like(xe)
+    ref = g.get_plan(8192, 8192, 1, False, "fp32", dev).execute(xe).clone()
+    plan = g.get_plan(8192, 8192, 1, False, "split_tc", dev)
+    ms, _ = time_plan(torch, plan, xe, ye, max(10, steps // 4), 3)
+    diff = float(torch.linalg.vector_norm(ye - ref) / torch.linalg.vector_norm(ref))
+    out["split_tc_fwd_8192"] = {"ms": ms, "GFLOP/s": flops_2d(8192, 8192) / ms / 1e6,
+                                "HBM_GB/s_algorithmic": 32.0 * 8192 * 8192 / ms / 1e6,
+                                "rel_l2_vs_fp32_path": diff}
+    del xe, ye, ref
+    x1 = torch.from_numpy(synth.exp_mix_1d(16384, 4096, seed=SEED)[0]).to(dev)
+    y1 = torch.empty_like(x1)
+    ref = g.get_plan(4096, 1, 16384, False, "fp32", dev).execute(x1).clone()
+    plan = g.get_plan(4096, 1, 16384, False, "split_tc", dev)
+    ms, _ = time_plan(torch, plan, x1, y1, max(10, steps // 4), 3)
+    diff = float(torch.linalg.vector_norm(y1 - ref) / torch.linalg.vector_norm(ref))
+    out["split_tc_1d_4096x16384"] = {"ms": ms, "GFLOP/s": flops_2d(4096, 1, 16384) / ms / 1e6,
+                                     "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6,
+                                     "rel_l2_vs_fp32_path": diff}
+    del x1, y1, ref
     # batch of 16384 1D length-4096 signals (one pass)
     x = torch.from_numpy(synth.exp_mix_1d(16384, 4096, seed=SEED)[0]).to(dev)
     y = torch.empty_like(x)

@@ -68,7 +68,10 @@ enum {
  *              batch of 1D transforms along the other axis).
  *   batch      >= 1; slices are stored back to back, nx*ny elements apart.
  *   dir        FFT_FORWARD or FFT_INVERSE: the exponent sign of fft_execute.
- *   precision  FFT_PREC_FP32 or FFT_PREC_SPLIT_FP16_TC.
+ *   precision  FFT_PREC_FP32 or FFT_PREC_SPLIT_FP16_TC.  The split form needs
+ *              every transformed length >= 16 (a radix-16 stage) and, for 2D,
+ *              (ny / 16) * min(nx, 32) >= 32 (a column tile fills a warp);
+ *              other sizes return NULL with FFT_ERR_UNSUPPORTED.
  * Returns NULL on failure (reason in fft_last_error()).  Must be called with
  * the device that will run the plan current; allocates device memory.
  */

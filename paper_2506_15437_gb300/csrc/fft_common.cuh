@@ -164,14 +164,14 @@ struct Sched {
 struct FftPolicy {
     using T = float2;
     template <int R>
-    __device__ static __forceinline__ void butterfly(T *a) { dft<R>(a); }
-    __device__ static __forceinline__ T twiddle(T a, float2 w) { return cmul(a, w); }
+    __device__ __forceinline__ void butterfly(T *a) const { dft<R>(a); }
+    __device__ __forceinline__ T twiddle(T a, float2 w) const { return cmul(a, w); }
 };
 struct MovePolicy {
     using T = float2;  // integer tags carried bit-for-bit in the .x lane
     template <int R>
-    __device__ static __forceinline__ void butterfly(T *) {}
-    __device__ static __forceinline__ T twiddle(T a, float2) { return a; }
+    __device__ __forceinline__ void butterfly(T *) const {}
+    __device__ __forceinline__ T twiddle(T a, float2) const { return a; }
 };
 
 struct SyncBlock {
@@ -209,10 +209,18 @@ struct Engine {
     __device__ static __forceinline__ void run(typename Pol::T (&v)[E], typename Pol::T *sm,
                                                const float2 *__restrict__ tw, int tt, int c,
                                                Sync sync, AfterReads after_reads, Store store) {
+        run_with<Pol, SRC_IN_SMEM>(Pol{}, v, sm, tw, tt, c, sync, after_reads, store);
+    }
+
+    // Same, with a policy object (a stateful butterfly, e.g. the tensor-core one).
+    template <class Pol, bool SRC_IN_SMEM, class Sync, class AfterReads, class Store>
+    __device__ static __forceinline__ void run_with(const Pol &pol, typename Pol::T (&v)[E], typename Pol::T *sm,
+                                                    const float2 *__restrict__ tw, int tt, int c, Sync sync,
+                                                    AfterReads after_reads, Store store) {
         using V = typename Pol::T;
         // stage 0: butterflies in registers, no twiddles
 #pragma unroll
-        for (int b = 0; b < E / R0; ++b) Pol::template butterfly<R0>(&v[b * R0]);
+        for (int b = 0; b < E / R0; ++b) pol.template butterfly<R0>(&v[b * R0]);
         if constexpr (S == 1) {
             after_reads();
         } else {
@@ -236,8 +244,8 @@ struct Engine {
                 if (s == S - 1) after_reads();
                 const float2 *tws = tw + Sc::tw_off(s) + m;
 #pragma unroll
-                for (int r = 1; r < E; ++r) v[r] = Pol::twiddle(v[r], __ldg(tws + (r - 1) * Ns));
-                Pol::template butterfly<E>(v);
+                for (int r = 1; r < E; ++r) v[r] = pol.twiddle(v[r], __ldg(tws + (r - 1) * Ns));
+                pol.template butterfly<E>(v);
             }
         }
         // natural-order outputs of the last stage: position j + k*N/RL

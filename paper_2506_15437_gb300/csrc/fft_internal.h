@@ -62,6 +62,17 @@ int ring_rows_grid(int n, long long nrows, int split, int num_sms, bool weighted
 cudaError_t launch_rows_ring(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
                              float wscale, int *status, int grid, cudaStream_t s);
+// Split-FP16 tensor-core variants (fft_tc.cu), E = 16.
+cudaError_t build_w16_table(void *t, cudaStream_t s);
+bool tc_rows_available(int n);
+int tc_col_width(int n, int nx);
+int tc_col_box_rows(int n);
+int tc_cols_grid(int n, int w, long long ntiles, int num_sms);
+cudaError_t launch_rows_tc(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                           const void *w16, long long nrows, int ny, int split, int conj_in, int conj_out,
+                           cudaStream_t s);
+cudaError_t launch_cols_tc(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w16,
+                           int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
 // Column pass of column length v.n over `batch` slices of P*v.n rows each.
 cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out,
                         const float2 *tw, int nx, int batch, int split, int conj_out, int *status,
@@ -91,6 +102,7 @@ struct AxisPlan {
     float2 *tw = nullptr;
     int n = 1;
     int grid = 0;  // column pass: persistent grid size
+    int tc_w = 0;  // tensor-core column pass: tile width
     // column pass: cached tensor map of the last output pointer
     CUtensorMap map;
     const void *map_base = nullptr;
@@ -120,6 +132,7 @@ struct fft_plan_s {
     int row_pf = 1;        // persistent row pass: L2 prefetch distance in groups
     int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
     int *status = nullptr;  // device status word
+    void *w16 = nullptr;    // split-FP16 plans: hi/lo W16 table (FP64-built)
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
     std::vector<void *> allocations;

@@ -73,7 +73,10 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
     ax.n = n;
     if (n == 1) return FFT_OK;
     int e = default_row_e(n);
-    if (const char *ev = getenv("GB300FFT_ROW_E")) {
+    if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
+        if (!tc_rows_available(n)) return FFT_ERR_UNSUPPORTED;
+        e = 16;
+    } else if (const char *ev = getenv("GB300FFT_ROW_E")) {
         const int forced = atoi(ev);
         if (row_variant(ilog2(n), forced)) e = forced;
     }
@@ -99,6 +102,19 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
 
 int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_per_w) {
     ax.n = n;
+    if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
+        ax.tc_w = tc_col_width(n, nx);
+        if (ax.tc_w == 0) return FFT_ERR_UNSUPPORTED;
+        ax.col = col_variant(ilog2(n), 16 > n ? n : 16, 2);  // twiddle schedule (E = 16) and box rows
+        if (!ax.col) return FFT_ERR_UNSUPPORTED;
+        if (ax.col->tw_size > 0) {
+            ax.tw = dev_alloc<float2>(p, ax.col->tw_size);
+            if (!ax.tw) return FFT_ERR_ALLOC;
+            if (build_twiddles(ax.tw, n, ax.col->e, 0) != cudaSuccess) return FFT_ERR_CUDA;
+        }
+        ax.grid = tc_cols_grid(n, ax.tc_w, tiles_per_w / ax.tc_w, p->num_sms);
+        return ax.grid > 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
+    }
     int w = default_col_w(n, nx);
     int e = default_col_e(n);
     if (const char *ev = getenv("GB300FFT_COL_E")) {
@@ -155,6 +171,27 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     const int P = (two_pass && src != dst) ? p->split : 1;
     AxisPlan &cp = (P > 1) ? p->cols_split : p->cols;
     const long long nrows = total / p->rows.n;
+    if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
+        if (weight) return FFT_ERR_UNSUPPORTED;
+        if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (launch_rows_tc(p->rows.n, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P, inv ? 1 : 0,
+                           (inv && !two_pass) ? 1 : 0, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (two_pass) {
+            if (cp.map_base != out) {
+                if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.tc_w,
+                                   tc_col_box_rows(cp.n)) != 0)
+                    return FFT_ERR_CUDA;
+                cp.map_base = out;
+            }
+            if (launch_cols_tc(cp.n, cp.tc_w, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P, inv ? 1 : 0, p->status,
+                               cp.grid, s) != cudaSuccess)
+                return FFT_ERR_CUDA;
+        }
+        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
     int &grid = p->row_grid[weight ? 1 : 0][P > 1 ? 1 : 0];
     if (grid == 0)
         grid = p->ring ? ring_rows_grid(p->rows.n, nrows, P, p->num_sms, weight != nullptr)
@@ -234,10 +271,6 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
         fail(FFT_ERR_INVALID_ARG);
         return nullptr;
     }
-    if (precision == FFT_PREC_SPLIT_FP16_TC) {
-        fail(FFT_ERR_UNSUPPORTED);
-        return nullptr;
-    }
     if ((long long)nx * ny * batch > (1LL << 31)) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
@@ -259,7 +292,13 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
         return nullptr;
     }
     int rc = FFT_OK;
-    if (nx == 1 || ny == 1) {
+    if (precision == FFT_PREC_SPLIT_FP16_TC) {
+        p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
+        if (!p->w16) rc = FFT_ERR_ALLOC;
+        else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    if (rc != FFT_OK) {
+    } else if (nx == 1 || ny == 1) {
         rc = setup_row_axis(p, p->rows, nx == 1 ? ny : nx);
     } else {
         rc = setup_row_axis(p, p->rows, nx);

@@ -1,0 +1,109 @@
+"""Split-FP16 tensor-core form against the FP64 oracle.
+
+Bar: relative L2 error per transform <= 1e-6 * log2(N) (the FP32 path's is
+2e-7 * log2(N)); each test reports both paths' errors on the same input."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import ORACLE_THREADS, rel_l2, tol_fp32, tol_split_tc, worst_rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_15437_gb300 import build
+    build.build()
+    import paper_2506_15437_gb300 as g
+    return g
+
+
+def both(g, x, inverse=False):
+    ny, nx = x.shape[-2], x.shape[-1]
+    batch = x.size // (nx * ny)
+    d = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = {}
+    for prec in ("split_tc", "fp32"):
+        plan = g.get_plan(nx, ny, batch, inverse, prec, "cuda")
+        out[prec] = plan.execute(d).cpu().numpy()
+        assert plan.status() == 0
+    return out["split_tc"], out["fp32"]
+
+
+SHAPES = [(32, 64), (64, 32), (128, 128), (256, 16), (16, 256), (512, 512), (1024, 256),
+          (256, 1024), (2048, 64), (64, 2048), (4096, 16), (16, 4096), (8192, 16)]
+
+
+@pytest.mark.parametrize("ny,nx", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_split_tc_small_shapes(g, ny, nx, inverse):
+    x = synth.uniform_complex((2, ny, nx), seed=ny * 3 + nx)
+    tc, fp = both(g, x, inverse)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    N = nx * ny
+    e_tc, e_fp = worst_rel_l2(tc, ref, N), worst_rel_l2(fp, ref, N)
+    print(f"split-TC {ny}x{nx} inv={inverse}: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    assert e_tc <= tol_split_tc(N)
+    assert e_fp <= tol_fp32(N)
+
+
+def test_split_tc_8192_exponential_mix(g):
+    """U[-1,1) noise + 8 unit exponentials, 8192^2: sampled output rows and
+    columns against the oracle, both paths."""
+    n = 8192
+    x, freqs = synth.exp_mix_2d(n, n, seed=2506)
+    tc, fp = both(g, x)
+    ky = np.concatenate([freqs[:, 0], [0, 1, n - 1]])
+    kx = np.concatenate([freqs[:, 1], [0, 1, n - 1]])
+    rows = oracle.fft2d_rows(x, ky, threads=ORACLE_THREADS)
+    cols = oracle.fft2d_cols(x, kx, threads=ORACLE_THREADS)
+    e_tc = max(max(rel_l2(tc[k], rows[t]) for t, k in enumerate(ky)),
+               max(rel_l2(tc[:, k], cols[t]) for t, k in enumerate(kx)))
+    e_fp = max(max(rel_l2(fp[k], rows[t]) for t, k in enumerate(ky)),
+               max(rel_l2(fp[:, k], cols[t]) for t, k in enumerate(kx)))
+    print(f"split-TC 8192^2 exp-mix: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    assert e_tc <= tol_split_tc(n * n)
+    assert e_fp <= tol_fp32(n * n)
+    # the spikes: each exponential puts N = n*n at its bin
+    for fy, fx in freqs:
+        assert abs(tc[fy, fx] - n * n) / (n * n) < 1e-3
+
+
+def test_split_tc_1d_batch_4096(g):
+    """16384 signals of length 4096 (noise + 8 exponentials per signal)."""
+    x, _ = synth.exp_mix_1d(16384, 4096, seed=2506)
+    d = torch.from_numpy(x).cuda()
+    tc = g.get_plan(4096, 1, 16384, False, "split_tc", "cuda").execute(d).cpu().numpy()
+    fp = g.get_plan(4096, 1, 16384, False, "fp32", "cuda").execute(d).cpu().numpy()
+    idx = np.array([0, 5, 4097, 9999, 16383])
+    ref = oracle.fft1d_batch(x[idx], threads=ORACLE_THREADS)
+    e_tc, e_fp = worst_rel_l2(tc[idx], ref, 4096), worst_rel_l2(fp[idx], ref, 4096)
+    print(f"split-TC 1D 4096 x 16384: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    assert e_tc <= tol_split_tc(4096)
+    assert e_fp <= tol_fp32(4096)
+
+
+def test_split_tc_handles_large_dynamic_range(g):
+    """Per-butterfly power-of-two scaling: inputs spanning 1e-20..1e20 stay
+    accurate (no float16 overflow or flush)."""
+    n = 256
+    x = synth.uniform_complex((n, n), seed=4).astype(np.complex128)
+    x *= np.logspace(-20, 20, n)[:, None]
+    x = x.astype(np.complex64)
+    tc, _ = both(g, x)
+    ref = oracle.fft2d(x, threads=ORACLE_THREADS)
+    assert np.isfinite(tc).all()
+    assert rel_l2(tc, ref) <= tol_split_tc(n * n)
+
+
+def test_split_tc_unsupported_shapes_fail_loudly(g):
+    from paper_2506_15437_gb300 import FFTError
+    with pytest.raises(FFTError):
+        g.Plan(8, 8, 1, precision="split_tc")   # no radix-16 stage at all
+    with pytest.raises(FFTError):
+        g.Plan(16, 16, 1, precision="split_tc")  # a 16-row column tile needs 32 columns for a full warp
