@@ -451,14 +451,16 @@ def main():
     nbytes = NX * NY * 8
 
     peak, peak_kind, _ = read_peaks()
-    dom_name, dom_ms = ("k_rows<8192,16>", rows_ms) if rows_ms >= cols_ms else ("k_cols<8192,16,2>", cols_ms)
+    sched = plan.describe()
+    dom_name, dom_ms = ((sched["rows"]["kernel"], rows_ms) if rows_ms >= cols_ms
+                        else (sched["cols"]["kernel"], cols_ms))
     achieved = 16.0 * NX * NY / (dom_ms * 1e-3) / 1e9
     traffic = read_traffic(dom_name)
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "traffic": traffic, "algorithmic_bytes_per_launch": 16 * NX * NY,
-                "passes_ms": {"rows": rows_ms, "cols": cols_ms},
+                "passes_ms": {"rows": rows_ms, "cols": cols_ms}, "schedule": sched,
                 "whole_step_frac": (32.0 * NX * NY / (ms * 1e-3) / 1e9) / peak}
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,

@@ -201,6 +201,28 @@ int fft_debug_reorder_map(int n, int axis, void *map, void *stream);
  */
 int fft_plan_set_pass_events(fft_plan_t p, void *ev_start, void *ev_mid, void *ev_end);
 
+/*
+ * fft_plan_autotune -- time the plan's candidate schedules (row-pass elements
+ * per thread and grid, column pre-split, column kernel: TMA tile or DSMEM
+ * cluster) on scratch buffers of the plan's size and keep the fastest.  The
+ * choice is appended to the tuning cache ($GB300FFT_TUNE_CACHE, default
+ * ~/.cache/gb300fft/tune.jsonl), which later fft_plan_create calls for the
+ * same shape and GPU read.  Allocates and frees two scratch buffers of the
+ * plan's size; synchronises `stream`.  Creating a plan with the environment
+ * variable GB300FFT_AUTOTUNE=1 runs it when the cache has no entry.  Split
+ * tensor-core plans have a single schedule (no-op).
+ */
+int fft_plan_autotune(fft_plan_t p, void *stream);
+
+/*
+ * fft_plan_describe -- the schedule a plan runs, as a NUL-terminated JSON
+ * object written to the host buffer `buf` of `len` bytes: kernel names,
+ * elements per thread, tile widths, column pre-split, grids and stage radices
+ * of each pass.  Returns the number of characters needed (excluding the NUL);
+ * the output is truncated when that is >= len.
+ */
+int fft_plan_describe(fft_plan_t p, char *buf, int len);
+
 /* Stage radices the kernels use for length n along an axis (0 rows, 1
  * columns), first stage first; returns the number of stages written to
  * `radices` (capacity 16) or a negative error. */

@@ -46,6 +46,8 @@ SIGNATURES = [
     ("fft_execute_ragged_noalloc", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _P, _P, _P, _P]),
     ("fft_plan_status", _I, [_P, _P]),
     ("fft_plan_set_pass_events", _I, [_P, _P, _P, _P]),
+    ("fft_plan_describe", _I, [_P, ctypes.c_char_p, _I]),
+    ("fft_plan_autotune", _I, [_P, _P]),
     ("fft_debug_reorder_map", _I, [_I, _I, _P, _P]),
     ("fft_debug_radices", _I, [_I, _I, ctypes.POINTER(_I)]),
     ("fft_version", ctypes.c_char_p, []),

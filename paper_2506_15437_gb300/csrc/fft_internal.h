@@ -73,6 +73,19 @@ cudaError_t launch_rows_tc(int n, const float2 *in, float2 *out, const float2 *t
                            cudaStream_t s);
 cudaError_t launch_cols_tc(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w16,
                            int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+// Column pass by 2-CTA clusters (fft_cols_pair.cu): block length n = 2 * N2.
+int pair_cols_width(int n, int e, int nx);
+int pair_cols_tw_size(int n, int e);
+cudaError_t launch_cols_pair(int n, int e, float2 *data, const float2 *tw, const float2 *roots, int nx, int batch,
+                             int split, int conj_out, cudaStream_t s);
+// Column pass by C-CTA clusters sharing a block through DSMEM
+// (fft_cols_cluster.cu): block length n = C * NQ, NQ in {1024, 2048}.
+int cluster_cols_width(int n, int e, int C, int nx);
+int cluster_cols_tw_size(int n, int e, int C);
+int cluster_cols_box_rows(int n, int e, int C);
+cudaError_t launch_cols_cluster(int n, int e, int C, const CUtensorMap &map, float2 *out, const float2 *tw,
+                                const float2 *roots, int nx, int batch, int split, int conj_out, int *status,
+                                cudaStream_t s);
 // Column pass of column length v.n over `batch` slices of P*v.n rows each.
 cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out,
                         const float2 *tw, int nx, int batch, int split, int conj_out, int *status,
@@ -94,6 +107,21 @@ void set_last_error(int code);
 int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int split, int w,
                    int box_rows);
 
+// Tunable schedule of a dense plan (every field has a default).
+enum { kColTile = 0, kColPair = 1, kColCluster = 2 };
+struct Schedule {
+    int row_e = 0;         // elements per thread of the row pass (0: default)
+    int row_persist = -1;  // 1 persistent row grid, 0 one CTA per group, -1 persistent iff pre-split
+    int row_pf = 1;        // persistent row pass: L2 prefetch distance (groups)
+    int ring = 0;          // long rows through the TMA landing-ring kernel
+    int split = 0;         // column pre-split P (0: default, 2 when ny >= 8192)
+    int col_kind = kColTile;
+    int col_e = 0;         // elements per thread of the column pass (0: default)
+    int col_w = 0;         // TMA tile width (0: default)
+    int col_c = 2;         // cluster size of the DSMEM column kernel
+    int col_pf = 0;        // TMA column pass: L2 prefetch distance (tiles)
+};
+
 // One axis of a dense plan: a row-pass length (contiguous) or a column-pass
 // length (strided), its kernel variant and its twiddle table.
 struct AxisPlan {
@@ -103,6 +131,9 @@ struct AxisPlan {
     int n = 1;
     int grid = 0;  // column pass: persistent grid size
     int tc_w = 0;  // tensor-core column pass: tile width
+    int pair_e = 0;  // >0: column pass by 2-CTA clusters with this E (length n/2 sub-FFTs)
+    int cl_c = 0, cl_e = 0;  // >0: column pass by cl_c-CTA DSMEM clusters with E = cl_e
+    float2 *roots = nullptr;  // pair column pass: exp(-2*pi*i*k/n), k < n
     // column pass: cached tensor map of the last output pointer
     CUtensorMap map;
     const void *map_base = nullptr;
@@ -135,6 +166,7 @@ struct fft_plan_s {
     void *w16 = nullptr;    // split-FP16 plans: hi/lo W16 table (FP64-built)
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
+    gb300fft::Schedule sched;  // the schedule this plan was built with
     std::vector<void *> allocations;
 };
 

@@ -15,6 +15,8 @@
 #include <mutex>
 #include <new>
 #include <vector>
+#include <string>
+#include <sys/stat.h>
 
 #include "../../include/gb300fft.h"
 #include "fft_common.cuh"
@@ -69,16 +71,120 @@ T *dev_alloc(fft_plan_s *p, size_t count) {
 
 bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
-int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
+Schedule default_schedule(int nx, int ny) {
+    Schedule sc;
+    (void)nx;
+    sc.split = ny >= 8192 ? 2 : 1;
+    return sc;
+}
+
+// GB300FFT_* environment overrides (experiments and tests).
+void apply_env_overrides(Schedule *sc) {
+    auto geti = [](const char *name, int *dst) {
+        if (const char *ev = getenv(name)) *dst = atoi(ev);
+    };
+    geti("GB300FFT_ROW_E", &sc->row_e);
+    geti("GB300FFT_ROW_PERSIST", &sc->row_persist);
+    geti("GB300FFT_ROW_PF", &sc->row_pf);
+    geti("GB300FFT_RING", &sc->ring);
+    geti("GB300FFT_SPLIT", &sc->split);
+    geti("GB300FFT_COL_E", &sc->col_e);
+    geti("GB300FFT_COL_W", &sc->col_w);
+    geti("GB300FFT_COL_PF", &sc->col_pf);
+    if (const char *ev = getenv("GB300FFT_COL_CLUSTER")) {
+        const int c = atoi(ev);
+        if (c == 2 || c == 4) {
+            sc->col_kind = kColCluster;
+            sc->col_c = c;
+        }
+    }
+    if (const char *ev = getenv("GB300FFT_COL_PAIR"))
+        if (atoi(ev)) sc->col_kind = kColPair;
+}
+
+// ---------------------------------------------------------------------------
+// Autotune cache: one JSON object per line,
+//   {"key": "<nx>x<ny>x<batch>:<prec>:<gpu>:<sms>", "row_e": .., ...}
+// in $GB300FFT_TUNE_CACHE (default ~/.cache/gb300fft/tune.jsonl).
+// ---------------------------------------------------------------------------
+std::string tune_cache_path() {
+    if (const char *ev = getenv("GB300FFT_TUNE_CACHE")) return ev;
+    const char *home = getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/gb300fft/tune.jsonl";
+}
+
+std::string tune_key(int nx, int ny, int batch, int prec) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &ch : name)
+        if (ch == '"' || ch == ':') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%dx%dx%d:%d:%s:%d", nx, ny, batch, prec, name.c_str(), sms);
+    return buf;
+}
+
+int json_int(const std::string &line, const char *field, int dflt) {
+    const std::string pat = std::string("\"") + field + "\": ";
+    const size_t pos = line.find(pat);
+    if (pos == std::string::npos) return dflt;
+    return atoi(line.c_str() + pos + pat.size());
+}
+
+bool tune_cache_lookup(int nx, int ny, int batch, int prec, Schedule *sc) {
+    FILE *f = fopen(tune_cache_path().c_str(), "r");
+    if (!f) return false;
+    const std::string key = "\"key\": \"" + tune_key(nx, ny, batch, prec) + "\"";
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        if (l.find(key) == std::string::npos) continue;
+        sc->row_e = json_int(l, "row_e", sc->row_e);
+        sc->row_persist = json_int(l, "row_persist", sc->row_persist);
+        sc->row_pf = json_int(l, "row_pf", sc->row_pf);
+        sc->split = json_int(l, "split", sc->split);
+        sc->col_kind = json_int(l, "col_kind", sc->col_kind);
+        sc->col_e = json_int(l, "col_e", sc->col_e);
+        sc->col_w = json_int(l, "col_w", sc->col_w);
+        sc->col_c = json_int(l, "col_c", sc->col_c);
+        found = true;  // the last matching line wins
+    }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(int nx, int ny, int batch, int prec, const Schedule &sc, float ms) {
+    const std::string path = tune_cache_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        // create the directory chain (best effort)
+        std::string dir = path.substr(0, slash);
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    }
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"key\": \"%s\", \"row_e\": %d, \"row_persist\": %d, \"row_pf\": %d, \"split\": %d, "
+            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"ms\": %.5f}\n",
+            tune_key(nx, ny, batch, prec).c_str(), sc.row_e, sc.row_persist, sc.row_pf, sc.split, sc.col_kind,
+            sc.col_e, sc.col_w, sc.col_c, ms);
+    fclose(f);
+}
+
+int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n, const Schedule &sc) {
     ax.n = n;
     if (n == 1) return FFT_OK;
     int e = default_row_e(n);
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (!tc_rows_available(n)) return FFT_ERR_UNSUPPORTED;
         e = 16;
-    } else if (const char *ev = getenv("GB300FFT_ROW_E")) {
-        const int forced = atoi(ev);
-        if (row_variant(ilog2(n), forced)) e = forced;
+    } else if (sc.row_e > 0 && row_variant(ilog2(n), sc.row_e)) {
+        e = sc.row_e;
     }
     ax.row = row_variant(ilog2(n), e);
     if (!ax.row) return FFT_ERR_UNSUPPORTED;
@@ -89,18 +195,16 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n) {
     }
     if (ax.row->smem > 48 * 1024)
         cudaFuncSetAttribute(ax.row->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ax.row->smem);
+    p->row_persist = sc.row_persist;
+    p->row_pf = sc.row_pf;
+    p->col_pf = sc.col_pf;
     // long rows may go through the TMA landing-ring kernel (same E = 16
-    // schedule and twiddle table as the plain row kernel); off by default,
-    // the plain persistent kernel measured faster
-    p->ring = false;
-    if (const char *ev = getenv("GB300FFT_ROW_PERSIST")) p->row_persist = atoi(ev);
-    if (const char *ev = getenv("GB300FFT_ROW_PF")) p->row_pf = atoi(ev);
-    if (const char *ev = getenv("GB300FFT_COL_PF")) p->col_pf = atoi(ev);
-    if (const char *ev = getenv("GB300FFT_RING")) p->ring = ring_rows_available(n) && ax.row->e == 16 && atoi(ev) != 0;
+    // schedule and twiddle table as the plain row kernel)
+    p->ring = sc.ring && ring_rows_available(n) && ax.row->e == 16 && p->prec == FFT_PREC_FP32;
     return FFT_OK;
 }
 
-int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_per_w) {
+int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_per_w, const Schedule &sc) {
     ax.n = n;
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         ax.tc_w = tc_col_width(n, nx);
@@ -115,16 +219,41 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
         ax.grid = tc_cols_grid(n, ax.tc_w, tiles_per_w / ax.tc_w, p->num_sms);
         return ax.grid > 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
     }
+    if (sc.col_kind == kColCluster) {
+        const int ce = sc.col_e > 0 ? sc.col_e : 16;
+        const int ccl = sc.col_c;
+        if (cluster_cols_width(n, ce, ccl, nx) > 0) {
+            ax.cl_c = ccl;
+            ax.cl_e = ce;
+            const int sz = cluster_cols_tw_size(n, ce, ccl);
+            ax.tw = dev_alloc<float2>(p, sz > 0 ? sz : 1);
+            ax.roots = dev_alloc<float2>(p, n);
+            if (!ax.tw || !ax.roots) return FFT_ERR_ALLOC;
+            if ((sz > 0 && build_twiddles(ax.tw, n / ccl, ce, 0) != cudaSuccess) ||
+                build_roots(ax.roots, n, 0) != cudaSuccess)
+                return FFT_ERR_CUDA;
+            ax.col = col_variant(ilog2(n), default_col_e(n), 2);  // keeps ax.col non-null
+            return ax.col ? FFT_OK : FFT_ERR_UNSUPPORTED;
+        }
+    }
+    if (sc.col_kind == kColPair) {
+        const int pe = sc.col_e > 0 ? sc.col_e : 16;
+        if (pair_cols_width(n, pe, nx) > 0) {
+            ax.pair_e = pe;
+            const int sz = pair_cols_tw_size(n, pe);
+            ax.tw = dev_alloc<float2>(p, sz > 0 ? sz : 1);
+            ax.roots = dev_alloc<float2>(p, n);
+            if (!ax.tw || !ax.roots) return FFT_ERR_ALLOC;
+            if ((sz > 0 && build_twiddles(ax.tw, n / 2, pe, 0) != cudaSuccess) || build_roots(ax.roots, n, 0) != cudaSuccess)
+                return FFT_ERR_CUDA;
+            ax.col = col_variant(ilog2(n), default_col_e(n), 2);  // unused by the pair kernel; keeps ax.col non-null
+            return ax.col ? FFT_OK : FFT_ERR_UNSUPPORTED;
+        }
+    }
     int w = default_col_w(n, nx);
     int e = default_col_e(n);
-    if (const char *ev = getenv("GB300FFT_COL_E")) {
-        const int forced = atoi(ev);
-        if (col_variant(ilog2(n), forced, w)) e = forced;
-    }
-    if (const char *ev = getenv("GB300FFT_COL_W")) {
-        const int forced = atoi(ev);
-        if (forced >= 2 && forced <= nx && col_variant(ilog2(n), e, forced)) w = forced;
-    }
+    if (sc.col_kind == kColTile && sc.col_e > 0 && col_variant(ilog2(n), sc.col_e, w)) e = sc.col_e;
+    if (sc.col_kind == kColTile && sc.col_w >= 2 && sc.col_w <= nx && col_variant(ilog2(n), e, sc.col_w)) w = sc.col_w;
     ax.col = col_variant(ilog2(n), e, w);
     if (!ax.col) return FFT_ERR_UNSUPPORTED;
     if (ax.col->tw_size > 0) {
@@ -138,6 +267,65 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
     if (grid < 1) grid = 1;
     ax.grid = (int)grid;
     return FFT_OK;
+}
+
+// A dense plan for (nx, ny, batch, dir, prec) running schedule `sc`.
+fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, const Schedule &sc, int *rc_out) {
+    fft_plan_s *p = new (std::nothrow) fft_plan_s();
+    if (!p) {
+        *rc_out = FFT_ERR_ALLOC;
+        return nullptr;
+    }
+    p->nx = nx;
+    p->ny = ny;
+    p->batch = batch;
+    p->dir = dir;
+    p->prec = precision;
+    p->sched = sc;
+    int rc = FFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        rc = FFT_ERR_CUDA;
+    if (rc == FFT_OK && precision == FFT_PREC_SPLIT_FP16_TC) {
+        p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
+        if (!p->w16) rc = FFT_ERR_ALLOC;
+        else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    if (rc != FFT_OK) {
+    } else if (nx == 1 || ny == 1) {
+        rc = setup_row_axis(p, p->rows, nx == 1 ? ny : nx, sc);
+    } else {
+        rc = setup_row_axis(p, p->rows, nx, sc);
+        // the unsplit column pass serves in-place calls
+        Schedule plain = sc;
+        if (rc == FFT_OK) rc = setup_col_axis(p, p->cols, ny, nx, (long long)nx * batch, plain);
+        // Column pre-split: a length-8192 column needs a 128 KiB tile (one CTA
+        // per SM); splitting it as 2 x 4096 halves the tile.
+        const int split = (sc.split == 2 && ny >= 4) ? 2 : 1;
+        if (rc == FFT_OK && split > 1) {
+            rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split, sc);
+            if (rc == FFT_OK) {
+                p->twp = dev_alloc<float2>(p, ny);
+                if (!p->twp) rc = FFT_ERR_ALLOC;
+                else if (build_roots(p->twp, ny, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+            }
+            if (rc == FFT_OK) p->split = split;
+        }
+    }
+    if (rc == FFT_OK) {
+        p->status = dev_alloc<int>(p, 1);
+        if (!p->status) rc = FFT_ERR_ALLOC;
+        else if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    p->wp_parts = p->num_sms * 4;
+    if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
+    if (rc != FFT_OK) {
+        free_plan(p);
+        *rc_out = rc;
+        return nullptr;
+    }
+    *rc_out = FFT_OK;
+    return p;
 }
 
 }  // namespace
@@ -209,6 +397,26 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
+    if (cp.cl_c > 0) {
+        if (cp.map_base != out) {
+            if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P,
+                               cluster_cols_width(cp.n, cp.cl_e, cp.cl_c, p->nx),
+                               cluster_cols_box_rows(cp.n, cp.cl_e, cp.cl_c)) != 0)
+                return FFT_ERR_CUDA;
+            cp.map_base = out;
+        }
+        if (launch_cols_cluster(cp.n, cp.cl_e, cp.cl_c, cp.map, dst, cp.tw, cp.roots, p->nx, p->batch, P, inv ? 1 : 0,
+                                p->status, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
+    if (cp.pair_e > 0) {
+        if (launch_cols_pair(cp.n, cp.pair_e, dst, cp.tw, cp.roots, p->nx, p->batch, P, inv ? 1 : 0, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
     if (cp.map_base != out) {
         if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.col->w, cp.col->box_rows) != 0)
             return FFT_ERR_CUDA;
@@ -275,62 +483,23 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
     }
-    fft_plan_s *p = new (std::nothrow) fft_plan_s();
-    if (!p) {
-        fail(FFT_ERR_ALLOC);
-        return nullptr;
-    }
-    p->nx = nx;
-    p->ny = ny;
-    p->batch = batch;
-    p->dir = dir;
-    p->prec = precision;
-    if (cudaGetDevice(&p->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
-        free_plan(p);
-        fail(FFT_ERR_CUDA);
-        return nullptr;
-    }
+    Schedule sc = default_schedule(nx, ny);
+    const bool cached = precision == FFT_PREC_FP32 && tune_cache_lookup(nx, ny, batch, precision, &sc);
+    apply_env_overrides(&sc);
     int rc = FFT_OK;
-    if (precision == FFT_PREC_SPLIT_FP16_TC) {
-        p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
-        if (!p->w16) rc = FFT_ERR_ALLOC;
-        else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
-    }
-    if (rc != FFT_OK) {
-    } else if (nx == 1 || ny == 1) {
-        rc = setup_row_axis(p, p->rows, nx == 1 ? ny : nx);
-    } else {
-        rc = setup_row_axis(p, p->rows, nx);
-        if (rc == FFT_OK) rc = setup_col_axis(p, p->cols, ny, nx, (long long)nx * batch);
-        // Column pre-split: a length-8192 column needs a 128 KiB tile (one CTA
-        // per SM); splitting it as 2 x 4096 halves the tile.
-        int split = ny >= 8192 ? 2 : 1;
-        if (const char *ev = getenv("GB300FFT_SPLIT")) {
-            const int forced = atoi(ev);
-            if (forced == 1 || (forced == 2 && ny >= 4)) split = forced;
-        }
-        if (rc == FFT_OK && split > 1) {
-            rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split);
-            if (rc == FFT_OK) {
-                p->twp = dev_alloc<float2>(p, ny);
-                if (!p->twp) rc = FFT_ERR_ALLOC;
-                else if (build_roots(p->twp, ny, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
-            }
-            if (rc == FFT_OK) p->split = split;
-        }
-    }
-    if (rc == FFT_OK) {
-        p->status = dev_alloc<int>(p, 1);
-        if (!p->status) rc = FFT_ERR_ALLOC;
-        else if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = FFT_ERR_CUDA;
-    }
-    p->wp_parts = p->num_sms * 4;
-    if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
-    if (rc != FFT_OK) {
-        free_plan(p);
+    fft_plan_s *p = create_dense(nx, ny, batch, dir, precision, sc, &rc);
+    if (!p) {
         fail(rc);
         return nullptr;
+    }
+    const char *ev = getenv("GB300FFT_AUTOTUNE");
+    if (!cached && ev && atoi(ev) != 0 && precision == FFT_PREC_FP32) {
+        rc = fft_plan_autotune(p, nullptr);
+        if (rc != FFT_OK) {
+            free_plan(p);
+            fail(rc);
+            return nullptr;
+        }
     }
     return p;
 }
@@ -393,6 +562,144 @@ int fft_plan_set_pass_events(fft_plan_t p, void *ev_start, void *ev_mid, void *e
     p->ev[1] = static_cast<cudaEvent_t>(ev_mid);
     p->ev[2] = static_cast<cudaEvent_t>(ev_end);
     return FFT_OK;
+}
+
+int fft_plan_autotune(fft_plan_t p, void *stream) {
+    if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
+    if (p->prec != FFT_PREC_FP32) return FFT_OK;  // one schedule only
+    cudaSetDevice(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long total = (long long)p->nx * p->ny * p->batch;
+    float2 *a = nullptr, *b = nullptr;
+    if (cudaMalloc(&a, total * sizeof(float2)) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (cudaMalloc(&b, total * sizeof(float2)) != cudaSuccess) {
+        cudaFree(a);
+        return FFT_ERR_ALLOC;
+    }
+    cudaMemsetAsync(a, 0x3e, total * sizeof(float2), s);
+    // candidates: row E, row persistence, column pre-split, column kernel
+    std::vector<Schedule> cands;
+    const bool twod = p->nx > 1 && p->ny > 1;
+    const int rown = p->nx > 1 ? p->nx : p->ny;
+    for (int re : {16, 32, 8}) {
+        if (rown < re || !row_variant(ilog2(rown), re)) continue;
+        for (int persist : {-1, 0, 1}) {
+            if (!twod) {
+                Schedule c;
+                c.row_e = re;
+                c.row_persist = persist < 0 ? 0 : persist;
+                c.split = 1;
+                cands.push_back(c);
+                continue;
+            }
+            for (int split : {1, 2}) {
+                if (split == 2 && p->ny < 4) continue;
+                Schedule c;
+                c.row_e = re;
+                c.row_persist = persist;
+                c.split = split;
+                const int cn = p->ny / split;
+                c.col_kind = kColTile;
+                cands.push_back(c);
+                if (cluster_cols_width(cn, 16, 2, p->nx) > 0) {
+                    Schedule d = c;
+                    d.col_kind = kColCluster;
+                    d.col_c = 2;
+                    d.col_e = 16;
+                    cands.push_back(d);
+                }
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Schedule bestsc = p->sched;
+    for (const Schedule &c : cands) {
+        int rc = FFT_OK;
+        fft_plan_s *q = create_dense(p->nx, p->ny, p->batch, p->dir, p->prec, c, &rc);
+        if (!q) continue;
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = run_dense(q, a, b, q->dir, nullptr, 1.f, s) == FFT_OK;
+        const int reps = total >= (1LL << 24) ? 5 : 20;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < reps && ok; ++k) ok = run_dense(q, a, b, q->dir, nullptr, 1.f, s) == FFT_OK;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ok && cudaGetLastError() == cudaSuccess && ms / reps < best) {
+            best = ms / reps;
+            bestsc = c;
+        }
+        free_plan(q);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+    // rebuild this plan with the winner, keeping its identity (handle)
+    int rc = FFT_OK;
+    fft_plan_s *q = create_dense(p->nx, p->ny, p->batch, p->dir, p->prec, bestsc, &rc);
+    if (!q) return rc;
+    std::swap(*p, *q);
+    free_plan(q);
+    tune_cache_store(p->nx, p->ny, p->batch, p->prec, bestsc, best);
+    return FFT_OK;
+}
+
+int fft_plan_describe(fft_plan_t p, char *buf, int len) {
+    if (!p || (len > 0 && !buf) || len < 0) return FFT_ERR_INVALID_ARG;
+    char tmp[1024];
+    int k = 0;
+    auto rad = [](int n, int e, char *o, int cap) {
+        int r[16];
+        const int S = schedule_radices(n, e, r);
+        int w = snprintf(o, cap, "[");
+        for (int i = 0; i < S && w < cap; ++i) w += snprintf(o + w, cap - w, i ? ",%d" : "%d", r[i]);
+        if (w < cap) w += snprintf(o + w, cap - w, "]");
+        return w;
+    };
+    if (p->kind == 1) {
+        k = snprintf(tmp, sizeof tmp, "{\"kind\": \"ragged\", \"kernel\": \"k_ragged\"}");
+    } else {
+        const bool tc = p->prec == FFT_PREC_SPLIT_FP16_TC;
+        char r1[96] = "[]", r2[96] = "[]";
+        const int re = p->rows.row ? (tc ? 16 : p->rows.row->e) : 1;
+        if (p->rows.row) rad(p->rows.n, re, r1, sizeof r1);
+        const gb300fft::AxisPlan &cp = p->split > 1 ? p->cols_split : p->cols;
+        if (cp.cl_c > 0) {
+            char r3[96];
+            rad(cp.n / cp.cl_c, cp.cl_e, r3, sizeof r3);
+            snprintf(r2, sizeof r2, "[%d,%s", cp.cl_c, r3 + 1);
+        } else if (cp.pair_e > 0) {
+            char r3[96];
+            rad(cp.n / 2, cp.pair_e, r3, sizeof r3);
+            snprintf(r2, sizeof r2, "[2,%s", r3 + 1);
+        } else if (cp.col) {
+            rad(cp.n, tc ? 16 : cp.col->e, r2, sizeof r2);
+        }
+        k = snprintf(tmp, sizeof tmp,
+                     "{\"kind\": \"dense\", \"precision\": \"%s\", \"rows\": {\"kernel\": \"%s<%d,%d,split%d>\", "
+                     "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
+                     "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
+                     "\"grid\": %d}, \"split\": %d}",
+                     tc ? "split_fp16_tc" : "fp32", tc ? "k_rows_tc" : (p->ring ? "k_rows_ring" : "k_rows"), p->rows.n, re,
+                     p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
+                     tc ? "k_cols_tc" : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : "k_cols"), cp.n,
+                     cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
+                     cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
+                     cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
+                     cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0, r2,
+                     cp.grid, p->split);
+    }
+    if (len > 0) {
+        const int c = k < len - 1 ? k : len - 1;
+        memcpy(buf, tmp, (size_t)c);
+        buf[c] = 0;
+    }
+    return k;
 }
 
 int fft_debug_radices(int n, int axis, int *radices) {

@@ -15,6 +15,10 @@
 
 namespace gb300fft {
 
+#ifndef ROWMINB32
+#define ROWMINB32 2  // 256-thread CTAs with E = 32: two per SM (128 registers)
+#endif
+
 template <int N, int E>
 struct RowShape {
     static constexpr int T = N / E;
@@ -22,7 +26,8 @@ struct RowShape {
     static constexpr int THREADS = ROWS * T;
     // resident CTAs the register budget must allow: 64 registers per thread
     // for 512-thread CTAs with E <= 16, at most 85 for 256-thread ones
-    static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS : (THREADS >= 256 && E < 32 ? 3 : 1);
+    static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS
+                                               : (THREADS >= 256 ? (E < 32 ? 3 : ROWMINB32) : 1);
     using Eng = Engine<N, E, 1, PadShift<E>::value>;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
 };

@@ -106,6 +106,17 @@ class Plan:
     def status(self) -> int:
         return self._lib.fft_plan_status(self._p, _stream_handle(torch.device("cuda")))
 
+    def autotune(self):
+        """Time the candidate schedules and keep the fastest (cached on disk)."""
+        N.check(self._lib.fft_plan_autotune(self._p, _stream_handle(torch.device("cuda"))), "fft_plan_autotune")
+
+    def describe(self) -> dict:
+        """The schedule this plan runs (kernels, elements per thread, tiles)."""
+        import json
+        buf = ctypes.create_string_buffer(2048)
+        self._lib.fft_plan_describe(self._p, buf, 2048)
+        return json.loads(buf.value.decode())
+
     def close(self):
         if getattr(self, "_p", None):
             self._lib.fft_plan_destroy(self._p)

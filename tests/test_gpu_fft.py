@@ -240,3 +240,57 @@ def test_presplit_inplace_falls_back_to_unsplit(g):
     ref = oracle.fft2d(x, threads=ORACLE_THREADS)
     assert rel_l2(a, ref) <= tol_fp32(nx * ny)
     assert rel_l2(b, ref) <= tol_fp32(nx * ny)
+
+
+@pytest.mark.parametrize("e", ["16", "32"])
+@pytest.mark.parametrize("ny,nx,batch,split", [(2048, 8, 2, "1"), (4096, 4, 1, "1"), (4096, 16, 1, "2"),
+                                               (8192, 4, 1, "2"), (8192, 2, 1, "1"), (2048, 64, 1, "1")])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_column_pass_by_cta_pairs(g, monkeypatch, e, ny, nx, batch, split, inverse):
+    """Column pass by 2-CTA clusters (radix-2 split of each column block,
+    both halves loaded by both CTAs, cluster barrier before the in-place
+    stores), forced on; out of place and in place."""
+    monkeypatch.setenv("GB300FFT_COL_PAIR", "1")
+    monkeypatch.setenv("GB300FFT_COL_E", e)
+    monkeypatch.setenv("GB300FFT_SPLIT", split)
+    plan = g.Plan(nx, ny, batch, inverse=inverse)
+    for k in ("GB300FFT_COL_PAIR", "GB300FFT_COL_E", "GB300FFT_SPLIT"):
+        monkeypatch.delenv(k)
+    assert plan.describe()["cols"]["kernel"].startswith("k_cols_pair")
+    x = synth.uniform_complex((batch, ny, nx), seed=ny + nx + batch)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    d = torch.from_numpy(x).cuda()
+    out = plan.execute(d)
+    assert worst_rel_l2(out.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.execute(d, out=d)
+    assert worst_rel_l2(d.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.close()
+
+
+@pytest.mark.parametrize("e", ["16", "32"])
+@pytest.mark.parametrize("c,ny,nx,batch,split", [("2", 2048, 8, 2, "1"), ("2", 4096, 4, 1, "1"),
+                                                 ("2", 8192, 16, 1, "2"), ("4", 4096, 4, 2, "1"),
+                                                 ("4", 8192, 4, 1, "1"), ("4", 8192, 8, 1, "2")])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_column_pass_by_dsmem_clusters(g, monkeypatch, e, c, ny, nx, batch, split, inverse):
+    """Column pass by C-CTA clusters: each CTA stages 1/C of a column block with
+    TMA, the radix-C combination reads the partners' slices through
+    distributed shared memory; out of place and in place."""
+    monkeypatch.setenv("GB300FFT_COL_CLUSTER", c)
+    monkeypatch.setenv("GB300FFT_COL_E", e)
+    monkeypatch.setenv("GB300FFT_SPLIT", split)
+    plan = g.Plan(nx, ny, batch, inverse=inverse)
+    for k in ("GB300FFT_COL_CLUSTER", "GB300FFT_COL_E", "GB300FFT_SPLIT"):
+        monkeypatch.delenv(k)
+    desc = plan.describe()
+    if not desc["cols"]["kernel"].startswith("k_cols_cluster"):
+        pytest.skip(f"no cluster variant for column block {desc['cols']['n']}")
+    x = synth.uniform_complex((batch, ny, nx), seed=ny + 3 * nx + batch)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    d = torch.from_numpy(x).cuda()
+    out = plan.execute(d)
+    assert plan.status() == 0
+    assert worst_rel_l2(out.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.execute(d, out=d)
+    assert worst_rel_l2(d.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.close()
