@@ -128,6 +128,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside)}
 
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """Largest `value` over all ranks (the step time every rank reports)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(world: int, flops_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: every rank transforms its own replica (weak
+    scaling), timed by the slowest rank."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -409,11 +425,7 @@ def main():
     if pg:
         pg.barrier()
     plan.set_pass_events(None, None, None)
-    ms = start.elapsed_time(end) / args.steps
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(pg, start.elapsed_time(end) / args.steps, dev)
     status = plan.status()
     rows_ms = sum(t[0].elapsed_time(t[1]) for t in evs) / args.steps
     cols_ms = sum(t[1].elapsed_time(t[2]) for t in evs) / args.steps
@@ -421,7 +433,7 @@ def main():
     clocks.stop()
     clk = clocks.summary()
 
-    value = world * flops_2d(NX, NY) / (ms * 1e-3) / 1e9
+    value = job_gflops(world, flops_2d(NX, NY), ms)
 
     # end to end through the public API: pinned host input -> device, transform,
     # device -> pinned host output, all inside the timed region
@@ -443,11 +455,7 @@ def main():
         out_host.copy_(out, non_blocking=True)
     b.record()
     torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b) / e2e_steps
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(pg, a.elapsed_time(b) / e2e_steps, dev)
     nbytes = NX * NY * 8
 
     peak, peak_kind, _ = read_peaks()
@@ -470,7 +478,7 @@ def main():
                        "precision": "fp32", "inputs": "re/im N(0,1), seed 2506 (+rank)",
                        "l2": "inputs and outputs 512 MiB each, larger than L2; no flush"},
             "roofline": roofline,
-            "e2e": {"value": world * flops_2d(NX, NY) / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "e2e": {"value": job_gflops(world, flops_2d(NX, NY), e2e_ms), "unit": "GFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": 2 * args.steps,
             "clocks": clk, "status": status}
