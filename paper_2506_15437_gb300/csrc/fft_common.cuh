@@ -9,6 +9,11 @@
 // stores, the intermediate orders live only in shared memory and registers,
 // and no separate bit-reversal pass or HBM round trip exists.
 //
+// Twiddle tables: stage s >= 1 (radix R, span Ns) stores, for pair k < R/2
+// and m < Ns, the float4 (w^{(2k+1) m}, w^{(2k+2) m}) with w = w_{Ns*R}, at
+// float4 index k*Ns + m, so a warp's threads (consecutive m) load adjacent
+// 16-byte words.
+//
 // Stage s of a length-N transform has radix R and span Ns = R_0 * ... * R_{s-1}.
 // Butterfly j (0 <= j < N/R), with m = j mod Ns, reads a_r = d[j + r*N/R],
 // multiplies a_r by w_{Ns*R}^{r*m} (w_K = exp(-2*pi*i/K)), takes the length-R
@@ -151,8 +156,9 @@ struct Sched {
     static constexpr int R0 = N >> (LE * (S - 1));
     // span Ns of stage s
     static constexpr int ns(int s) { return s == 0 ? 1 : R0 * ipow(E, s - 1); }
-    // offset of stage s's twiddle table (stage 1 starts at 0)
-    static constexpr int tw_off(int s) { return s <= 1 ? 0 : tw_off(s - 1) + (E - 1) * ns(s - 1); }
+    // offset of stage s's twiddle table in float2 units (stage 1 starts at
+    // 0); a stage of radix R and span Ns holds R/2 float4 pairs per m
+    static constexpr int tw_off(int s) { return s <= 1 ? 0 : tw_off(s - 1) + E * ns(s - 1); }
     static constexpr int tw_size = tw_off(S);
 };
 
@@ -163,12 +169,14 @@ struct Sched {
 // ---------------------------------------------------------------------------
 struct FftPolicy {
     using T = float2;
+    static constexpr bool kUsesTwiddles = true;
     template <int R>
     __device__ __forceinline__ void butterfly(T *a) const { dft<R>(a); }
     __device__ __forceinline__ T twiddle(T a, float2 w) const { return cmul(a, w); }
 };
 struct MovePolicy {
     using T = float2;  // integer tags carried bit-for-bit in the .x lane
+    static constexpr bool kUsesTwiddles = false;
     template <int R>
     __device__ __forceinline__ void butterfly(T *) const {}
     __device__ __forceinline__ T twiddle(T a, float2) const { return a; }
@@ -242,9 +250,16 @@ struct Engine {
 #pragma unroll
                 for (int r = 0; r < E; ++r) v[r] = sm[pad((tt + r * T) * W + c)];
                 if (s == S - 1) after_reads();
-                const float2 *tws = tw + Sc::tw_off(s) + m;
+                if constexpr (Pol::kUsesTwiddles) {
+                    // twiddles r = 2k+1, 2k+2 of this butterfly in one 16-byte load
+                    const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
 #pragma unroll
-                for (int r = 1; r < E; ++r) v[r] = pol.twiddle(v[r], __ldg(tws + (r - 1) * Ns));
+                    for (int k = 0; k < E / 2; ++k) {
+                        const float4 w2 = __ldg(tws + k * Ns);
+                        v[2 * k + 1] = pol.twiddle(v[2 * k + 1], make_float2(w2.x, w2.y));
+                        if (2 * k + 2 < E) v[2 * k + 2] = pol.twiddle(v[2 * k + 2], make_float2(w2.z, w2.w));
+                    }
+                }
                 pol.template butterfly<E>(v);
             }
         }
@@ -263,7 +278,7 @@ struct Engine {
 // most once per half-warp (checked by a bank model on the CPU).
 template <int E>
 struct PadShift {
-    static constexpr int value = (E >= 32) ? 5 : 4;
+    static constexpr int value = (E >= 64) ? 6 : (E >= 32) ? 5 : 4;
 };
 
 // ---------------------------------------------------------------------------

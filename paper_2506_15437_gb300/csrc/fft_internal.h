@@ -39,6 +39,7 @@ const RowVariant *row_variant(int log2n, int e);           // nullptr if not com
 const ColVariant *col_variant(int log2n, int e, int w);    // nullptr if not compiled
 int default_row_e(int n);
 int default_col_e(int n);
+int preferred_col_e(int n, int w);
 int default_col_w(int n, int nx);
 
 // Stage radices of the (n, e) schedule, first stage first; returns count.

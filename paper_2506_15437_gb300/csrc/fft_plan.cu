@@ -251,7 +251,7 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
         }
     }
     int w = default_col_w(n, nx);
-    int e = default_col_e(n);
+    int e = preferred_col_e(n, w);
     if (sc.col_kind == kColTile && sc.col_e > 0 && col_variant(ilog2(n), sc.col_e, w)) e = sc.col_e;
     if (sc.col_kind == kColTile && sc.col_w >= 2 && sc.col_w <= nx && col_variant(ilog2(n), e, sc.col_w)) w = sc.col_w;
     ax.col = col_variant(ilog2(n), e, w);
@@ -601,6 +601,13 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                 const int cn = p->ny / split;
                 c.col_kind = kColTile;
                 cands.push_back(c);
+                for (int ce : {16, 64}) {
+                    if (!col_variant(ilog2(cn), ce, default_col_w(cn, p->nx)) || ce == preferred_col_e(cn, default_col_w(cn, p->nx)))
+                        continue;
+                    Schedule d = c;
+                    d.col_e = ce;
+                    cands.push_back(d);
+                }
                 if (cluster_cols_width(cn, 16, 2, p->nx) > 0) {
                     Schedule d = c;
                     d.col_kind = kColCluster;

@@ -563,7 +563,7 @@ fft_plan_t fft_plan_create_ragged(int count, const int *nx, const int *ny, int d
         const int S = schedule_radices(1 << l, kRagE, rad);
         long long sz = 0, ns = rad[0];
         for (int s2 = 1; s2 < S; ++s2) {
-            sz += (long long)(rad[s2] - 1) * ns;
+            sz += (long long)rad[s2] * ns;
             ns *= rad[s2];
         }
         r->d_tw[l] = static_cast<float2 *>(dalloc((size_t)(sz > 0 ? sz : 1) * sizeof(float2)));
@@ -646,8 +646,8 @@ namespace gb300fft {
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxCount = 1024;   // instances per call
 constexpr int kNoAllocMaxItems = 65536;  // work items per call
-constexpr size_t kNoAllocTwOffset = 0;   // twiddle tables, 2048 float2 (filled once per device)
-constexpr size_t kNoAllocTwElems = 2048;
+constexpr size_t kNoAllocTwOffset = 0;   // twiddle tables, 4096 float2 (filled once per device)
+constexpr size_t kNoAllocTwElems = 4096;
 constexpr size_t kNoAllocItemsOffset = kNoAllocTwOffset + kNoAllocTwElems * sizeof(float2);
 constexpr size_t kNoAllocInstOffset = kNoAllocItemsOffset + (size_t)kNoAllocMaxItems * sizeof(int4);
 constexpr size_t kNoAllocOffsOffset = kNoAllocInstOffset + (size_t)kNoAllocMaxCount * sizeof(int4);
@@ -679,7 +679,7 @@ int noalloc_setup(int dev, cudaStream_t s) {
         const int S = schedule_radices(1 << l, kRagE, rad);
         long long sz = 0, ns = rad[0];
         for (int k = 1; k < S; ++k) {
-            sz += (long long)(rad[k] - 1) * ns;
+            sz += (long long)rad[k] * ns;
             ns *= rad[k];
         }
         if (used + (size_t)sz > kNoAllocTwElems) return FFT_ERR_UNSUPPORTED;

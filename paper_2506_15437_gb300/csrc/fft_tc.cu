@@ -75,6 +75,7 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *p) {
 
 struct TcPolicy {
     using T = float2;
+    static constexpr bool kUsesTwiddles = true;
     uint32_t wr_hi[4], wi_hi[4], wr_lo[4], wi_lo[4];
     unsigned char *stage;  // this warp's staging area (shared memory)
 

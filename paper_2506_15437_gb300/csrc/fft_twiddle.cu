@@ -3,10 +3,11 @@
 // The paper computes its twiddle factors once at initialisation and keeps
 // them on chip because they do not change from step to step (Section 4).
 // Here each plan builds, once, one table per (length n, elements per thread
-// E): stage s >= 1 of the schedule (radix E, span Ns) owns the entries
-//     tw[off_s + (r-1)*Ns + m] = exp(-2*pi*i * r*m / (Ns*E)),  1 <= r < E, m < Ns,
-// laid out so that the threads of a warp (consecutive m) read consecutive
-// entries.  Values are computed in double precision with sincospi of the
+// E): stage s >= 1 of the schedule (radix E, span Ns) owns E*Ns float2
+// entries holding, as float4 pairs at float4 index k*Ns + m,
+//     (exp(-2*pi*i*(2k+1)*m/(Ns*E)), exp(-2*pi*i*(2k+2)*m/(Ns*E))),  k < E/2,
+// so that the threads of a warp (consecutive m) read consecutive 16-byte
+// words, two twiddles per load.  Values are computed in double precision with sincospi of the
 // exact dyadic argument 2*r*m/(Ns*E) and rounded once to float -- the only
 // place double precision runs on the GPU.
 #include "fft_common.cuh"
@@ -20,14 +21,15 @@ __global__ void k_twiddles(float2 *tw, int r0, int e, int stages, int total) {
     int off = 0;
     long long ns = r0;
     for (int s = 1; s < stages; ++s) {
-        const long long sz = (long long)(e - 1) * ns;
+        const long long sz = (long long)e * ns;
         if (idx < off + sz) {
-            const long long k = idx - off;
-            const long long r = k / ns + 1;
-            const long long m = k % ns;
+            const long long k2 = idx - off;          // float2 index within the stage
+            const long long f = k2 >> 1;             // float4 index = pair * Ns + m
+            const long long r = 2 * (f / ns) + 1 + (k2 & 1);
+            const long long m = f % ns;
             const long long K = ns * e;
             double sv, cv;
-            sincospi(2.0 * (double)(r * m) / (double)K, &sv, &cv);
+            sincospi(2.0 * (double)((r * m) % K) / (double)K, &sv, &cv);
             tw[idx] = make_float2((float)cv, (float)(-sv));
             return;
         }
@@ -42,7 +44,7 @@ cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s) {
     if (S < 0) return cudaErrorInvalidValue;
     long long total = 0, ns = rad[0];
     for (int k = 1; k < S; ++k) {
-        total += (long long)(rad[k] - 1) * ns;
+        total += (long long)rad[k] * ns;
         ns *= rad[k];
     }
     if (total == 0) return cudaSuccess;

@@ -294,3 +294,22 @@ def test_column_pass_by_dsmem_clusters(g, monkeypatch, e, c, ny, nx, batch, spli
     plan.execute(d, out=d)
     assert worst_rel_l2(d.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
     plan.close()
+
+
+@pytest.mark.parametrize("e", ["16", "32", "64"])
+@pytest.mark.parametrize("ny,nx,batch", [(4096, 4, 2), (4096, 64, 1), (8192, 8, 1), (8192, 2, 1)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_column_pass_elements_per_thread(g, monkeypatch, e, ny, nx, batch, inverse):
+    """TMA column pass with 16, 32 or 64 elements per thread (one shared-memory
+    exchange for a 4096-point column at E = 64); out of place and in place."""
+    monkeypatch.setenv("GB300FFT_COL_E", e)
+    plan = g.Plan(nx, ny, batch, inverse=inverse)
+    monkeypatch.delenv("GB300FFT_COL_E")
+    x = synth.uniform_complex((batch, ny, nx), seed=5 * ny + nx)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    d = torch.from_numpy(x).cuda()
+    assert worst_rel_l2(plan.execute(d).cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    plan.execute(d, out=d)
+    assert worst_rel_l2(d.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
+    assert plan.status() == 0
+    plan.close()
