@@ -68,12 +68,15 @@ cudaError_t build_w16_table(void *t, cudaStream_t s);
 bool tc_rows_available(int n);
 int tc_col_width(int n, int nx);
 int tc_col_box_rows(int n);
-int tc_cols_grid(int n, int w, long long ntiles, int num_sms);
-cudaError_t launch_rows_tc(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
-                           const void *w16, long long nrows, int ny, int split, int conj_in, int conj_out,
+// tcg: 1 = tcgen05/TMEM butterfly, 0 = mma.sync butterfly
+bool tcg_available(int rown, int coln, int colw);
+int tc_cols_grid(int n, int w, int tcg, long long ntiles, int num_sms);
+cudaError_t launch_rows_tc(int n, int tcg, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                           const void *w16, long long nrows, int ny, int split, int conj_in, int conj_out, int *status,
                            cudaStream_t s);
-cudaError_t launch_cols_tc(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w16,
-                           int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+cudaError_t launch_cols_tc(int n, int w, int tcg, const CUtensorMap &map, float2 *out, const float2 *tw,
+                           const void *w16, int nx, int batch, int split, int conj_out, int *status, int grid,
+                           cudaStream_t s);
 // Column pass by 2-CTA clusters (fft_cols_pair.cu): block length n = 2 * N2.
 int pair_cols_width(int n, int e, int nx);
 int pair_cols_tw_size(int n, int e);
@@ -132,6 +135,7 @@ struct AxisPlan {
     int n = 1;
     int grid = 0;  // column pass: persistent grid size
     int tc_w = 0;  // tensor-core column pass: tile width
+    int tcg = 0;   // tensor-core column pass: 1 tcgen05 butterflies, 0 mma.sync
     int pair_e = 0;  // >0: column pass by 2-CTA clusters with this E (length n/2 sub-FFTs)
     int cl_c = 0, cl_e = 0;  // >0: column pass by cl_c-CTA DSMEM clusters with E = cl_e
     float2 *roots = nullptr;  // pair column pass: exp(-2*pi*i*k/n), k < n
@@ -165,6 +169,7 @@ struct fft_plan_s {
     int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
     int *status = nullptr;  // device status word
     void *w16 = nullptr;    // split-FP16 plans: hi/lo W16 table (FP64-built)
+    int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
     gb300fft::Schedule sched;  // the schedule this plan was built with

@@ -216,7 +216,8 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
             if (!ax.tw) return FFT_ERR_ALLOC;
             if (build_twiddles(ax.tw, n, ax.col->e, 0) != cudaSuccess) return FFT_ERR_CUDA;
         }
-        ax.grid = tc_cols_grid(n, ax.tc_w, tiles_per_w / ax.tc_w, p->num_sms);
+        ax.tcg = (p->tcg && tcg_available(p->rows.n, n, ax.tc_w)) ? 1 : 0;
+        ax.grid = tc_cols_grid(n, ax.tc_w, ax.tcg, tiles_per_w / ax.tc_w, p->num_sms);
         return ax.grid > 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
     }
     if (sc.col_kind == kColCluster) {
@@ -287,6 +288,8 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
         rc = FFT_ERR_CUDA;
     if (rc == FFT_OK && precision == FFT_PREC_SPLIT_FP16_TC) {
+        if (const char *ev = getenv("GB300FFT_TC_MMA")) p->tcg = strcmp(ev, "sync") != 0;
+        if (p->tcg && !tcg_available(nx > 1 ? nx : ny, 1, 0)) p->tcg = 0;
         p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
         if (!p->w16) rc = FFT_ERR_ALLOC;
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
@@ -362,8 +365,8 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (weight) return FFT_ERR_UNSUPPORTED;
         if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
-        if (launch_rows_tc(p->rows.n, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P, inv ? 1 : 0,
-                           (inv && !two_pass) ? 1 : 0, s) != cudaSuccess)
+        if (launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P, inv ? 1 : 0,
+                           (inv && !two_pass) ? 1 : 0, p->status, s) != cudaSuccess)
             return FFT_ERR_CUDA;
         if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
         if (two_pass) {
@@ -373,8 +376,8 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                     return FFT_ERR_CUDA;
                 cp.map_base = out;
             }
-            if (launch_cols_tc(cp.n, cp.tc_w, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P, inv ? 1 : 0, p->status,
-                               cp.grid, s) != cudaSuccess)
+            if (launch_cols_tc(cp.n, cp.tc_w, cp.tcg, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P, inv ? 1 : 0,
+                               p->status, cp.grid, s) != cudaSuccess)
                 return FFT_ERR_CUDA;
         }
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
@@ -692,9 +695,9 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
                      "\"grid\": %d}, \"split\": %d}",
-                     tc ? "split_fp16_tc" : "fp32", tc ? "k_rows_tc" : (p->ring ? "k_rows_ring" : "k_rows"), p->rows.n, re,
+                     tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
-                     tc ? "k_cols_tc" : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : "k_cols"), cp.n,
+                     !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : "k_cols"), cp.n,
                      cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
                      cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,

@@ -79,6 +79,13 @@ struct TcPolicy {
     uint32_t wr_hi[4], wi_hi[4], wr_lo[4], wi_lo[4];
     unsigned char *stage;  // this warp's staging area (shared memory)
 
+    // per-CTA extra shared memory: one staging area per warp
+    static constexpr size_t stage_bytes(int threads) { return (size_t)((threads + 31) / 32) * kTcStageStride; }
+    __device__ __forceinline__ void init(const __half *__restrict__ table, unsigned char *stage_base, int *) {
+        load(table, stage_base + (threadIdx.x >> 5) * kTcStageStride);
+    }
+    __device__ __forceinline__ void finish() {}
+
     // A-operand fragments of the four 16x16 parts, from the FP64-built table.
     __device__ __forceinline__ void load(const __half *__restrict__ table, unsigned char *warp_stage) {
         stage = warp_stage;
@@ -189,11 +196,203 @@ struct TcPolicy {
     }
 };
 
+
+// ---------------------------------------------------------------------------
+// The same split-FP16 radix-16 butterfly on the 5th-generation tensor cores:
+// tcgen05.mma with operands in shared memory and accumulators in TMEM.
+//
+// Per group of 128 threads (one butterfly each) and per stage:
+//   A = the group's 128 butterflies as rows, K = 32 (16 re, 16 im) halves,
+//       once as x_hi and once as x_lo, in the K-major canonical layout
+//       (core matrices of 8 rows x 16 bytes; K-adjacent cores 128 bytes
+//       apart, 8-row groups 512 bytes apart);
+//   B = the 32 x 32 real DFT-16 matrix [[Wr,-Wi],[Wi,Wr]] split hi/lo,
+//       rows = outputs, K-major, built once per CTA from the FP64 table;
+//   D1 = A_hi B_hi^T, D2 = A_lo B_hi^T + A_hi B_lo^T in TMEM (32 columns
+//       each; M = 128, N = 32, K = 16 per instruction, 6 instructions),
+// issued by one thread, committed to the group's mbarrier; then every
+// thread reads its own row (lane) of D1 and D2 with tcgen05.ld and forms
+// y = s (D1 + 2^-11 D2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    // start >> 4 | LBO (K-adjacent cores: 128 B) | SBO (8-row groups: 512 B) | version 1
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+// kind::f16, D = F32, A = B = F16, both K-major, N = 32, M = 128
+constexpr uint32_t kUmmaIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kUmmaIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+constexpr int kTcgGroupStage = 2 * 128 * 64;  // A_hi + A_lo of one 128-thread group (bytes)
+
+struct TcgPolicy {
+    using T = float2;
+    static constexpr bool kUsesTwiddles = true;
+    unsigned char *bmat;   // B_hi at bmat, B_lo at bmat + 2048
+    unsigned char *astage; // this group's A_hi (8 KiB) then A_lo (8 KiB)
+    uint64_t *bar;         // this group's mbarrier
+    uint32_t tmem;         // this group's first accumulator column (lane field 0)
+    int *status;
+    mutable uint32_t phase;
+
+    // layout: [B: 4 KiB][mbarriers: 16 x 8 B][TMEM base: 16 B][A staging: groups x 16 KiB]
+    static constexpr size_t stage_bytes(int threads) {
+        return 4096 + 128 + 16 + (size_t)(threads / 128) * kTcgGroupStage;
+    }
+    static constexpr int tmem_cols(int threads) {
+        return (threads / 128) * 64 <= 32 ? 32 : (threads / 128) * 64 <= 64 ? 64 : (threads / 128) * 64 <= 128 ? 128 : 256;
+    }
+
+    // Per-CTA set-up; every thread of the CTA must call it (it synchronises).
+    __device__ void init(const __half *__restrict__ table, unsigned char *base, int *status_word) {
+        const int t = threadIdx.x;
+        const int nthreads = blockDim.x;
+        status = status_word;
+        bmat = base;
+        bar = reinterpret_cast<uint64_t *>(base + 4096) + (t >> 7);
+        uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 4096 + 128);
+        astage = base + 4096 + 128 + 16 + (t >> 7) * kTcgGroupStage;
+        phase = 0;
+        // B = [[Wr, -Wi], [Wi, Wr]] (rows n = outputs re 0-15 / im 16-31,
+        // columns k = inputs re 0-15 / im 16-31), hi then lo
+        for (int idx = t; idx < 2 * 32 * 32; idx += nthreads) {
+            const int part = idx >> 10;  // 0 hi, 1 lo
+            const int n = (idx >> 5) & 31, k = idx & 31;
+            const int kr = k & 15, nr = n & 15;
+            const bool wr = (n < 16) == (k < 16);
+            __half h = table[(wr ? 0 : 2) * 256 + part * 256 + nr * 16 + kr];
+            if (n < 16 && k >= 16) h = __hneg(h);
+            *reinterpret_cast<__half *>(base + part * 2048 + (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 +
+                                        (k & 7) * 2) = h;
+        }
+        if (t < 32) {
+            const int cols = tmem_cols(nthreads);
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                         "r"(cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        if (t == 0) {
+            for (int g = 0; g < nthreads / 128; ++g)
+                mbar_init(reinterpret_cast<uint64_t *>(base + 4096) + g, 1);
+            fence_mbar_init();
+        }
+        fence_proxy_async_smem();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = *tmem_slot + (uint32_t)((t >> 7) * 64);
+    }
+
+    // Per-CTA tear-down: every thread calls it; frees the TMEM columns.
+    __device__ void finish() {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x < 32) {
+            const uint32_t base_col = tmem - (uint32_t)((threadIdx.x >> 7) * 64);
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base_col),
+                         "r"(tmem_cols(blockDim.x))
+                         : "memory");
+        }
+    }
+
+    template <int R>
+    __device__ __forceinline__ void butterfly(float2 *a) const {
+        if constexpr (R == 16)
+            tc_dft16(a);
+        else
+            dft<R>(a);
+    }
+    __device__ __forceinline__ float2 twiddle(float2 a, float2 w) const { return cmul(a, w); }
+
+    // The calling thread's length-16 DFT; every thread of the CTA must call it.
+    __device__ __forceinline__ void tc_dft16(float2 *v) const {
+        const int r = threadIdx.x & 127;
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].x), fabsf(v[k].y)));
+        const int eb = (__float_as_int(m) >> 23) & 0xff;
+        const float s = __int_as_float((eb + 1) << 23);
+        const float inv_s = __int_as_float((253 - eb) << 23);
+        // row r of A_hi / A_lo: 4 core-matrix chunks of 8 halves (re 0-7, re 8-15, im 0-7, im 8-15)
+        unsigned char *row_hi = astage + (r >> 3) * 512 + (r & 7) * 16;
+        unsigned char *row_lo = row_hi + 8192;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k0 = (c & 1) * 8 + 2 * q;
+                const float x0 = ((c & 2) ? v[k0].y : v[k0].x) * inv_s;
+                const float x1 = ((c & 2) ? v[k0 + 1].y : v[k0 + 1].x) * inv_s;
+                const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+                wh[q] = pack_half2(h0, h1);
+                wl[q] = pack_half2(__float2half_rn((x0 - __half2float(h0)) * 2048.f),
+                                   __float2half_rn((x1 - __half2float(h1)) * 2048.f));
+            }
+            *reinterpret_cast<uint4 *>(row_hi + c * 128) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4 *>(row_lo + c * 128) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (r == 0) {
+            const uint32_t a_hi = smem_u32(astage), a_lo = a_hi + 8192;
+            const uint32_t b_hi = smem_u32(bmat), b_lo = b_hi + 2048;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {  // K = 32 as two K = 16 steps (two core chunks each)
+                umma_f16(tmem, umma_desc(a_hi + ks * 256), umma_desc(b_hi + ks * 256), ks);
+                umma_f16(tmem + 32, umma_desc(a_lo + ks * 256), umma_desc(b_hi + ks * 256), ks);
+                umma_f16(tmem + 32, umma_desc(a_hi + ks * 256), umma_desc(b_lo + ks * 256), 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        if (!mbar_wait_bounded(bar, phase)) record_status(status, kStatusTimeout);
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lane = (uint32_t)((threadIdx.x & 96)) << 16;  // this warp's 32 TMEM lanes
+        uint32_t d1[32], d2[32];
+        tmem_ld32(tmem + lane, d1);
+        tmem_ld32(tmem + 32 + lane, d2);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float yr = s * fmaf(__int_as_float(d2[k]), 1.f / 2048.f, __int_as_float(d1[k]));
+            const float yi = s * fmaf(__int_as_float(d2[16 + k]), 1.f / 2048.f, __int_as_float(d1[16 + k]));
+            v[k] = make_float2(yr, yi);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Row pass (E = 16), optional column pre-split P = 2: the FP32 row kernel's
 // structure with the tensor-core butterfly.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, class Pol>
 struct TcRowShape {
     static constexpr int E = N >= 16 ? 16 : N;
     static constexpr int T = N / E;
@@ -201,24 +400,24 @@ struct TcRowShape {
     static constexpr int THREADS = ROWS * T;
     using Eng = Engine<N, E, 1, PadShift<E>::value>;
     static constexpr size_t EX_BYTES = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
-    static constexpr size_t STAGE_OFF = (EX_BYTES + 127) / 128 * 128;
-    static constexpr size_t SMEM = STAGE_OFF + (size_t)(THREADS / 32) * kTcStageStride;
+    static constexpr size_t STAGE_OFF = (EX_BYTES + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM = STAGE_OFF + Pol::stage_bytes(THREADS);
 };
 
-template <int N, int P>
-__global__ void __launch_bounds__(TcRowShape<N>::THREADS, 1)
+template <int N, int P, class Pol>
+__global__ void __launch_bounds__(TcRowShape<N, Pol>::THREADS, 1)
     k_rows_tc(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
               const float2 *__restrict__ twp, const __half *__restrict__ w16, long long nrows, int ny, int conj_in,
-              int conj_out) {
-    using Sh = TcRowShape<N>;
+              int conj_out, int *status) {
+    using Sh = TcRowShape<N, Pol>;
     using Eng = typename Sh::Eng;
     constexpr int E = Sh::E;
     constexpr int T = Sh::T;
     constexpr int R0 = Eng::R0;
-    extern __shared__ __align__(128) unsigned char raw[];
+    extern __shared__ __align__(1024) unsigned char raw[];
     float2 *smem = reinterpret_cast<float2 *>(raw);
-    TcPolicy pol;
-    pol.load(w16, raw + Sh::STAGE_OFF + (threadIdx.x >> 5) * kTcStageStride);
+    Pol pol;
+    pol.init(w16, raw + Sh::STAGE_OFF, status);
     const int g = threadIdx.x / T;
     const int tt = threadIdx.x - g * T;
     const long long row = (long long)blockIdx.x * Sh::ROWS + g;
@@ -268,18 +467,17 @@ __global__ void __launch_bounds__(TcRowShape<N>::THREADS, 1)
     };
     auto none = [] {};
     if constexpr (Eng::NT >= 32)
-        Eng::template run_with<TcPolicy, false>(pol, v, smem + g * Eng::SMEM_ELEMS, tw, tt, 0, SyncBlock{}, none,
-                                                store);
+        Eng::template run_with<Pol, false>(pol, v, smem + g * Eng::SMEM_ELEMS, tw, tt, 0, SyncBlock{}, none, store);
     else
-        Eng::template run_with<TcPolicy, false>(pol, v, smem + g * Eng::SMEM_ELEMS, tw, tt, 0, SyncWarp{}, none,
-                                                store);
+        Eng::template run_with<Pol, false>(pol, v, smem + g * Eng::SMEM_ELEMS, tw, tt, 0, SyncWarp{}, none, store);
+    pol.finish();
 }
 
 // ---------------------------------------------------------------------------
 // Column pass (E = 16): the TMA-staged persistent column kernel with the
 // tensor-core butterfly.
 // ---------------------------------------------------------------------------
-template <int N, int W>
+template <int N, int W, class Pol>
 struct TcColShape {
     static constexpr int E = N >= 16 ? 16 : N;
     static constexpr int T = N / E;
@@ -289,25 +487,25 @@ struct TcColShape {
     static constexpr int BOXR = N < 256 ? N : 256;
     static constexpr uint32_t TILE_BYTES = (uint32_t)N * W * sizeof(float2);
     static constexpr size_t BAR_OFF = ((size_t)ELEMS * sizeof(float2) + 127) / 128 * 128;
-    static constexpr size_t STAGE_OFF = BAR_OFF + 128;
-    static constexpr size_t SMEM = STAGE_OFF + (size_t)((THREADS + 31) / 32) * kTcStageStride;
+    static constexpr size_t STAGE_OFF = (BAR_OFF + 128 + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM = STAGE_OFF + Pol::stage_bytes(THREADS);
 };
 
-template <int N, int W>
-__global__ void __launch_bounds__(TcColShape<N, W>::THREADS, 1)
+template <int N, int W, class Pol>
+__global__ void __launch_bounds__(TcColShape<N, W, Pol>::THREADS, 1)
     k_cols_tc(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw,
               const __half *__restrict__ w16, int nx, int batch, int P, int conj_out, int *status) {
-    using Sh = TcColShape<N, W>;
+    using Sh = TcColShape<N, W, Pol>;
     using Eng = typename Sh::Eng;
     constexpr int E = Sh::E;
     constexpr int R0 = Eng::R0;
     constexpr int T = Sh::T;
-    extern __shared__ __align__(128) unsigned char raw[];
+    extern __shared__ __align__(1024) unsigned char raw[];
     float2 *tile = reinterpret_cast<float2 *>(raw);
     uint64_t *bar = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
     __shared__ int s_ok;
-    TcPolicy pol;
-    pol.load(w16, raw + Sh::STAGE_OFF + (threadIdx.x >> 5) * kTcStageStride);
+    Pol pol;
+    pol.init(w16, raw + Sh::STAGE_OFF, status);
 
     const int t = threadIdx.x;
     const int c = t % W;
@@ -342,7 +540,7 @@ __global__ void __launch_bounds__(TcColShape<N, W>::THREADS, 1)
                 record_status(status, kStatusTimeout);
                 mbar_wait_bounded(bar, phase);
             }
-            return;
+            break;  // leave through finish(): the TMEM columns must be freed
         }
         phase ^= 1;
         const long long next = id + gridDim.x;
@@ -369,23 +567,25 @@ __global__ void __launch_bounds__(TcColShape<N, W>::THREADS, 1)
             x.y *= so;
             dst[(long long)i * rstride + cc] = x;
         };
-        Eng::template run_with<TcPolicy, true>(pol, v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
+        Eng::template run_with<Pol, true>(pol, v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
     }
+    pol.finish();
 }
 
 // ---------------------------------------------------------------------------
 // Variant tables and launchers.
 // ---------------------------------------------------------------------------
 namespace {
+// [policy: 0 mma.sync, 1 tcgen05]
 struct TcRowEntry {
-    const void *fn[2] = {nullptr, nullptr};  // [P == 2]
+    const void *fn[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [policy][P == 2]
     int threads = 0, rows_per_cta = 0;
-    size_t smem = 0;
+    size_t smem[2] = {0, 0};
 };
 struct TcColEntry {
-    const void *fn = nullptr;
+    const void *fn[2] = {nullptr, nullptr};
     int threads = 0, w = 0, box_rows = 0;
-    size_t smem = 0;
+    size_t smem[2] = {0, 0};
 };
 TcRowEntry g_tc_rows[kMaxLog2 + 1];
 TcColEntry g_tc_cols[kMaxLog2 + 1][5];  // W slot: 2, 4, 8, 16, 32
@@ -395,23 +595,32 @@ int tc_w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3
 
 template <int N>
 void reg_tc_row() {
-    using Sh = TcRowShape<N>;
+    using Sh0 = TcRowShape<N, TcPolicy>;
+    using Sh1 = TcRowShape<N, TcgPolicy>;
     TcRowEntry &en = g_tc_rows[ilog2(N)];
-    en.fn[0] = (const void *)k_rows_tc<N, 1>;
-    en.fn[1] = (const void *)k_rows_tc<N, 2>;
-    en.threads = Sh::THREADS;
-    en.rows_per_cta = Sh::ROWS;
-    en.smem = Sh::SMEM;
+    en.fn[0][0] = (const void *)k_rows_tc<N, 1, TcPolicy>;
+    en.fn[0][1] = (const void *)k_rows_tc<N, 2, TcPolicy>;
+    if constexpr (Sh1::THREADS % 128 == 0) {
+        en.fn[1][0] = (const void *)k_rows_tc<N, 1, TcgPolicy>;
+        en.fn[1][1] = (const void *)k_rows_tc<N, 2, TcgPolicy>;
+    }
+    en.threads = Sh0::THREADS;
+    en.rows_per_cta = Sh0::ROWS;
+    en.smem[0] = Sh0::SMEM;
+    en.smem[1] = Sh1::SMEM;
 }
 template <int N, int W>
 void reg_tc_col() {
-    using Sh = TcColShape<N, W>;
+    using Sh0 = TcColShape<N, W, TcPolicy>;
+    using Sh1 = TcColShape<N, W, TcgPolicy>;
     TcColEntry &en = g_tc_cols[ilog2(N)][tc_w_slot(W)];
-    en.fn = (const void *)k_cols_tc<N, W>;
-    en.threads = Sh::THREADS;
+    en.fn[0] = (const void *)k_cols_tc<N, W, TcPolicy>;
+    if constexpr (Sh1::THREADS % 128 == 0 && Sh1::SMEM <= 227 * 1024) en.fn[1] = (const void *)k_cols_tc<N, W, TcgPolicy>;
+    en.threads = Sh0::THREADS;
     en.w = W;
-    en.box_rows = Sh::BOXR;
-    en.smem = Sh::SMEM;
+    en.box_rows = Sh0::BOXR;
+    en.smem[0] = Sh0::SMEM;
+    en.smem[1] = Sh1::SMEM;
 }
 template <int N>
 void reg_tc_cols() {
@@ -450,11 +659,11 @@ void init_tc() {
 
 bool tc_rows_available(int n) {
     init_tc();
-    return n >= 16 && n <= 8192 && (n & (n - 1)) == 0 && g_tc_rows[ilog2(n)].fn[0] != nullptr;
+    return n >= 16 && n <= 8192 && (n & (n - 1)) == 0 && g_tc_rows[ilog2(n)].fn[0][0] != nullptr;
 }
 
 // Column tile for length n with at most nx columns: the widest one with at
-// most 512 threads (the tensor-core butterfly needs ~150 registers), else the
+// most 512 threads (the tensor-core butterfly needs many registers), else the
 // narrowest available.
 int tc_col_width(int n, int nx) {
     init_tc();
@@ -462,7 +671,7 @@ int tc_col_width(int n, int nx) {
     int best = 0;
     for (int w = 2; w <= 32 && w <= nx; w <<= 1) {
         const TcColEntry &en = g_tc_cols[ilog2(n)][tc_w_slot(w)];
-        if (!en.fn) continue;
+        if (!en.fn[0]) continue;
         if (en.threads <= 512 || best == 0) best = w;
     }
     return best;
@@ -470,31 +679,42 @@ int tc_col_width(int n, int nx) {
 
 int tc_col_box_rows(int n) { return n < 256 ? n : 256; }
 
-cudaError_t launch_rows_tc(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
-                           const void *w16, long long nrows, int ny, int split, int conj_in, int conj_out,
+// Whether the tcgen05 kernels exist for this row length / column shape.
+bool tcg_available(int rown, int coln, int colw) {
+    init_tc();
+    if (!g_tc_rows[ilog2(rown)].fn[1][0]) return false;
+    if (coln > 1 && (tc_w_slot(colw) < 0 || !g_tc_cols[ilog2(coln)][tc_w_slot(colw)].fn[1])) return false;
+    return true;
+}
+
+cudaError_t launch_rows_tc(int n, int tcg, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                           const void *w16, long long nrows, int ny, int split, int conj_in, int conj_out, int *status,
                            cudaStream_t s) {
     init_tc();
     if (!tc_rows_available(n) || (split != 1 && split != 2)) return cudaErrorInvalidValue;
     if (nrows <= 0) return cudaSuccess;
     const TcRowEntry &en = g_tc_rows[ilog2(n)];
-    const void *fn = en.fn[split == 2 ? 1 : 0];
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    const int pk = tcg ? 1 : 0;
+    const void *fn = en.fn[pk][split == 2 ? 1 : 0];
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem[pk]);
     if (e != cudaSuccess) return e;
     const long long grid = (nrows + en.rows_per_cta - 1) / en.rows_per_cta;
     const __half *w = static_cast<const __half *>(w16);
-    void *args[] = {(void *)&in,    (void *)&out, (void *)&tw,      (void *)&twp,     (void *)&w,
-                    (void *)&nrows, (void *)&ny,  (void *)&conj_in, (void *)&conj_out};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(en.threads), args, en.smem, s);
+    void *args[] = {(void *)&in,    (void *)&out, (void *)&tw,      (void *)&twp,      (void *)&w,
+                    (void *)&nrows, (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&status};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(en.threads), args, en.smem[pk], s);
 }
 
-int tc_cols_grid(int n, int w, long long ntiles, int num_sms) {
+int tc_cols_grid(int n, int w, int tcg, long long ntiles, int num_sms) {
     init_tc();
     const int slot = tc_w_slot(w);
-    if (slot < 0 || !g_tc_cols[ilog2(n)][slot].fn) return 0;
+    if (slot < 0 || !g_tc_cols[ilog2(n)][slot].fn[tcg ? 1 : 0]) return 0;
     const TcColEntry &en = g_tc_cols[ilog2(n)][slot];
-    cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    const void *fn = en.fn[tcg ? 1 : 0];
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem[tcg ? 1 : 0]);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, en.fn, en.threads, en.smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, en.threads, en.smem[tcg ? 1 : 0]) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     long long grid = (long long)num_sms * per_sm;
@@ -502,19 +722,21 @@ int tc_cols_grid(int n, int w, long long ntiles, int num_sms) {
     return grid < 1 ? 1 : (int)grid;
 }
 
-cudaError_t launch_cols_tc(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w16,
-                           int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s) {
+cudaError_t launch_cols_tc(int n, int w, int tcg, const CUtensorMap &map, float2 *out, const float2 *tw,
+                           const void *w16, int nx, int batch, int split, int conj_out, int *status, int grid,
+                           cudaStream_t s) {
     init_tc();
     const int slot = tc_w_slot(w);
-    if (slot < 0 || !g_tc_cols[ilog2(n)][slot].fn) return cudaErrorInvalidValue;
+    const int pk = tcg ? 1 : 0;
+    if (slot < 0 || !g_tc_cols[ilog2(n)][slot].fn[pk]) return cudaErrorInvalidValue;
     const TcColEntry &en = g_tc_cols[ilog2(n)][slot];
-    cudaError_t e = cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    cudaError_t e = cudaFuncSetAttribute(en.fn[pk], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem[pk]);
     if (e != cudaSuccess) return e;
     CUtensorMap m = map;
     const __half *wt = static_cast<const __half *>(w16);
     void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&wt,     (void *)&nx,
                     (void *)&batch, (void *)&split, (void *)&conj_out, (void *)&status};
-    return cudaLaunchKernel(en.fn, dim3(grid), dim3(en.threads), args, en.smem, s);
+    return cudaLaunchKernel(en.fn[pk], dim3(grid), dim3(en.threads), args, en.smem[pk], s);
 }
 
 }  // namespace gb300fft

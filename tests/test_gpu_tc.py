@@ -23,15 +23,24 @@ def g():
     return g
 
 
+@pytest.fixture(params=["tcgen05", "sync"])
+def mma(request, monkeypatch):
+    """Which tensor-core butterfly the split plans use: tcgen05 (TMEM
+    accumulators, the default) or mma.sync."""
+    monkeypatch.setenv("GB300FFT_TC_MMA", request.param)
+    return request.param
+
+
 def both(g, x, inverse=False):
     ny, nx = x.shape[-2], x.shape[-1]
     batch = x.size // (nx * ny)
     d = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = {}
     for prec in ("split_tc", "fp32"):
-        plan = g.get_plan(nx, ny, batch, inverse, prec, "cuda")
+        plan = g.Plan(nx, ny, batch, inverse=inverse, precision=prec)
         out[prec] = plan.execute(d).cpu().numpy()
         assert plan.status() == 0
+        plan.close()
     return out["split_tc"], out["fp32"]
 
 
@@ -41,18 +50,18 @@ SHAPES = [(32, 64), (64, 32), (128, 128), (256, 16), (16, 256), (512, 512), (102
 
 @pytest.mark.parametrize("ny,nx", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
 @pytest.mark.parametrize("inverse", [False, True])
-def test_split_tc_small_shapes(g, ny, nx, inverse):
+def test_split_tc_small_shapes(g, mma, ny, nx, inverse):
     x = synth.uniform_complex((2, ny, nx), seed=ny * 3 + nx)
     tc, fp = both(g, x, inverse)
     ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
     N = nx * ny
     e_tc, e_fp = worst_rel_l2(tc, ref, N), worst_rel_l2(fp, ref, N)
-    print(f"split-TC {ny}x{nx} inv={inverse}: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    print(f"split-TC[{mma}] {ny}x{nx} inv={inverse}: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
     assert e_tc <= tol_split_tc(N)
     assert e_fp <= tol_fp32(N)
 
 
-def test_split_tc_8192_exponential_mix(g):
+def test_split_tc_8192_exponential_mix(g, mma):
     """U[-1,1) noise + 8 unit exponentials, 8192^2: sampled output rows and
     columns against the oracle, both paths."""
     n = 8192
@@ -66,7 +75,7 @@ def test_split_tc_8192_exponential_mix(g):
                max(rel_l2(tc[:, k], cols[t]) for t, k in enumerate(kx)))
     e_fp = max(max(rel_l2(fp[k], rows[t]) for t, k in enumerate(ky)),
                max(rel_l2(fp[:, k], cols[t]) for t, k in enumerate(kx)))
-    print(f"split-TC 8192^2 exp-mix: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    print(f"split-TC[{mma}] 8192^2 exp-mix: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
     assert e_tc <= tol_split_tc(n * n)
     assert e_fp <= tol_fp32(n * n)
     # the spikes: each exponential puts N = n*n at its bin
@@ -74,21 +83,21 @@ def test_split_tc_8192_exponential_mix(g):
         assert abs(tc[fy, fx] - n * n) / (n * n) < 1e-3
 
 
-def test_split_tc_1d_batch_4096(g):
+def test_split_tc_1d_batch_4096(g, mma):
     """16384 signals of length 4096 (noise + 8 exponentials per signal)."""
     x, _ = synth.exp_mix_1d(16384, 4096, seed=2506)
     d = torch.from_numpy(x).cuda()
-    tc = g.get_plan(4096, 1, 16384, False, "split_tc", "cuda").execute(d).cpu().numpy()
+    tc = g.Plan(4096, 1, 16384, precision="split_tc").execute(d).cpu().numpy()
     fp = g.get_plan(4096, 1, 16384, False, "fp32", "cuda").execute(d).cpu().numpy()
     idx = np.array([0, 5, 4097, 9999, 16383])
     ref = oracle.fft1d_batch(x[idx], threads=ORACLE_THREADS)
     e_tc, e_fp = worst_rel_l2(tc[idx], ref, 4096), worst_rel_l2(fp[idx], ref, 4096)
-    print(f"split-TC 1D 4096 x 16384: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
+    print(f"split-TC[{mma}] 1D 4096 x 16384: rel L2 {e_tc:.3e} (FP32 {e_fp:.3e})")
     assert e_tc <= tol_split_tc(4096)
     assert e_fp <= tol_fp32(4096)
 
 
-def test_split_tc_handles_large_dynamic_range(g):
+def test_split_tc_handles_large_dynamic_range(g, mma):
     """Per-butterfly power-of-two scaling: inputs spanning 1e-20..1e20 stay
     accurate (no float16 overflow or flush)."""
     n = 256
@@ -107,3 +116,10 @@ def test_split_tc_unsupported_shapes_fail_loudly(g):
         g.Plan(8, 8, 1, precision="split_tc")   # no radix-16 stage at all
     with pytest.raises(FFTError):
         g.Plan(16, 16, 1, precision="split_tc")  # a 16-row column tile needs 32 columns for a full warp
+
+
+def test_split_tc_default_is_tcgen05(g):
+    plan = g.Plan(256, 256, 1, precision="split_tc")
+    d = plan.describe()
+    assert d["rows"]["kernel"].startswith("k_rows_tcgen05")
+    assert d["cols"]["kernel"].startswith("k_cols_tcgen05")
