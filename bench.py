@@ -362,6 +362,42 @@ def ragged_form(torch, g, steps, dev):
                            "HBM_GB/s_algorithmic_2pass": 32.0 * packed.size / ms_graph / 1e6}}
 
 
+def profile_form(torch, name, steps, warmup, dev):
+    """One secondary workload alone (for ncu): plan, warm-up, `steps` runs."""
+    from paper_2506_15437_gb300 import build as _build
+    _build.build()
+    import paper_2506_15437_gb300 as g
+    import synth
+    if name == "ragged":
+        nx, ny, _, packed = synth.ragged_batch(512, seed=SEED)
+        plan = g.RaggedPlan(nx, ny)
+        x = torch.from_numpy(packed).to(dev)
+        run = lambda: plan.execute(x)  # noqa: E731
+    elif name == "diff":
+        b, n = 8, 2048
+        x = torch.from_numpy(synth.uniform_complex((b, n, n), seed=SEED)).to(dev)
+        w = torch.from_numpy(synth.mask((b, n, n), seed=SEED + 1)).to(dev)
+        plan = g.Plan(n, n, b)
+        X = torch.empty_like(x)
+        run = lambda: (plan.execute(x, out=X), plan.backward_weighted(X, w, 2.0))  # noqa: E731
+    else:
+        if name == "split_tc_8192":
+            x = synth.exp_mix_2d(8192, 8192, seed=SEED)[0]
+            plan = g.Plan(8192, 8192, 1, precision="split_tc")
+        else:
+            x = synth.exp_mix_1d(16384, 4096, seed=SEED)[0]
+            plan = g.Plan(4096, 1, 16384, precision="split_tc" if name == "split_tc_1d" else "fp32")
+        x = torch.from_numpy(x).to(dev)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
+    for _ in range(warmup + steps):
+        run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_form": name, "steps": steps, "warmup": warmup,
+                      "schedule": plan.describe() if hasattr(plan, "describe") else None}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,6 +406,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-form", default=None,
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "ragged", "diff"],
+                    help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -379,6 +418,8 @@ def main():
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.profile_form:
+        return profile_form(torch, args.profile_form, args.steps, args.warmup, dev)
     pg = None
     if world > 1:
         import torch.distributed as dist
