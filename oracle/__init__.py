@@ -15,6 +15,8 @@ Functions (all unnormalised, ``dir=-1`` forward, ``dir=+1`` inverse):
 * :func:`dft1d_brute`, :func:`dft2d_brute` -- the O(N^2) definition.
 * :func:`fft2d_rows`, :func:`fft2d_cols` -- selected output rows / columns of
   a 2D transform (definition along one axis, recursive FFT along the other).
+* :func:`dft1d_bins` -- selected bins of one long 1D transform, each from the
+  definition in one O(n) pass.
 """
 from __future__ import annotations
 
@@ -61,9 +63,10 @@ def _bind(lib):
     lib.oracle_dft2d_brute.argtypes = [d, d, L, L, i]
     lib.oracle_fft2d_rows.argtypes = [d, d, L, L, d, L, i, i]
     lib.oracle_fft2d_cols.argtypes = [d, d, L, L, d, L, i, i]
+    lib.oracle_dft1d_bins.argtypes = [d, d, L, d, L, i, i]
     for f in ("oracle_fft1d_batch", "oracle_fft2d", "oracle_dft1d_brute",
               "oracle_dft2d_brute", "oracle_fft2d_rows", "oracle_fft2d_cols",
-              "oracle_max_threads"):
+              "oracle_dft1d_bins", "oracle_max_threads"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -154,4 +157,15 @@ def fft2d_cols(x, kx, dir: int = -1, threads: int = 1, lib=None) -> np.ndarray:
     out = np.empty((k.size, ny), dtype=np.complex128)
     _check(lib.oracle_fft2d_cols(a.ctypes.data, out.ctypes.data, nx, ny, k.ctypes.data,
                                  k.size, dir, threads), "fft2d_cols")
+    return out
+
+
+def dft1d_bins(x, bins, dir: int = -1, threads: int = 1, lib=None) -> np.ndarray:
+    """Bins ``X[bins]`` of the 1D transform of the vector ``x`` (definition)."""
+    lib = lib or load()
+    a = _c128(x).reshape(-1)
+    k = np.ascontiguousarray(bins, dtype=np.int64).reshape(-1)
+    out = np.empty(k.size, dtype=np.complex128)
+    _check(lib.oracle_dft1d_bins(a.ctypes.data, out.ctypes.data, a.size, k.ctypes.data, k.size,
+                                 dir, threads), "dft1d_bins")
     return out

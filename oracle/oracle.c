@@ -23,7 +23,8 @@
  * O(N^2) definition with the phase index (j*k mod n) reduced in integers; the
  * sampled-output functions combine the definition along one axis with the
  * recursive transform along the other, for spot checks of transforms too large
- * to recompute whole.
+ * to recompute whole; oracle_dft1d_bins evaluates single bins of a long 1D
+ * transform from the definition.
  *
  * Data.  Interleaved complex128 (re, im) arrays, row-major [batch][ny][nx].
  * Inputs are never modified.  Every function returns 0 on success and a
@@ -307,6 +308,38 @@ int oracle_fft2d_cols(const double *in, double *out, long nx, long ny, const lon
         fft1d(acc, X + t * ny, ny, dir);
         free(w);
         free(acc);
+    }
+    return 0;
+}
+
+/*
+ * Selected bins of one length-n 1D transform, straight from the definition:
+ *   X[k] = sum_{j<n} x[j] * exp(dir*2*pi*i*(j*k mod n)/n),  k in bins[0..nb).
+ * One O(n) pass per bin, for spot checks of 1D transforms too long to
+ * recompute whole with the recursive form (n up to 2^26).  out is [nb].
+ */
+int oracle_dft1d_bins(const double *in, double *out, long n, const long *bins, long nb, int dir,
+                      int threads) {
+    if (!in || !out || !bins || n < 1 || nb < 0 || (dir != 1 && dir != -1)) return -1;
+    const cplx *x = (const cplx *)in;
+    cplx *X = (cplx *)out;
+    if (threads < 1) threads = 1;
+    for (long t = 0; t < nb; ++t)
+        if (bins[t] < 0 || bins[t] >= n) return -1;
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 1)
+    for (long t = 0; t < nb; ++t) {
+        long long k = bins[t];
+#if ORACLE_MUTANT == 8
+        k = (k + 1) % n; /* MUTANT 8: the neighbouring bin */
+#endif
+        double sr = 0.0, si = 0.0;
+        for (long j = 0; j < n; ++j) {
+            cplx w = root_exact(((long long)j * k) % n, n, dir);
+            sr += x[j].re * w.re - x[j].im * w.im;
+            si += x[j].re * w.im + x[j].im * w.re;
+        }
+        X[t].re = sr;
+        X[t].im = si;
     }
     return 0;
 }

@@ -172,8 +172,27 @@ def pin_sampled(lib):
     return bad
 
 
+def pin_bins(lib):
+    """Single bins of long 1D transforms: the definition per bin against the
+    recursive transform (two independent evaluations), and a closed form."""
+    bad = []
+    for n in [64, 4096, 1 << 16]:
+        x = _rand((n,), 11 + n)
+        bins = np.array(sorted({0, 1, 3, n // 2, n // 2 + 1, n - 1, (7 * n) // 11}))
+        for d in (-1, 1):
+            X = oracle.fft1d_batch(x, dir=d, lib=lib)
+            if _rel(oracle.dft1d_bins(x, bins, dir=d, threads=2, lib=lib), X[bins]) > 1e-12:
+                bad.append(f"bins n={n} dir={d}")
+    n, f = 1 << 20, 12345
+    e = np.exp(2j * np.pi * ((f * np.arange(n)) % n) / n)
+    got = oracle.dft1d_bins(e, [f, f + 1, 0], dir=-1, threads=3, lib=lib)
+    if np.abs(got - np.array([n, 0, 0])).max() > 1e-9 * n:
+        bad.append("bins exp spike")
+    return bad
+
+
 PINS = [pin_bruteforce_1d, pin_bruteforce_2d, pin_golden, pin_closed_forms,
-        pin_invariants, pin_library, pin_sampled]
+        pin_invariants, pin_library, pin_sampled, pin_bins]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -204,8 +223,9 @@ def test_bad_arguments_rejected():
 # Each mutant plants one plausible mistake in oracle.c (see ORACLE_MUTANT):
 # 1 twiddle sign, 2 dropped term, 3 off-by-one twiddle index, 4 transposed
 # length in the column pass, 5 dropped column pass, 6 conjugated input,
-# 7 brute-force sign.  Every one must fail at least one pin.
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
+# 7 brute-force sign, 8 neighbouring bin in the per-bin definition.  Every
+# one must fail at least one pin.
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_pins_catch_mutant(mutant):
     lib = oracle.load(mutant=mutant)
     failures = []
