@@ -301,8 +301,30 @@ def forms(torch, g, steps, warmup, dev):
     out["fp32_1d_4096x16384"] = {"ms": ms, "GFLOP/s": flops_2d(4096, 1, 16384) / ms / 1e6,
                                  "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
     del x, y
+    out.update(fourstep_form(torch, g, steps, dev))
     out.update(ragged_form(torch, g, steps, dev))
     out.update(diff_form(torch, g, steps, dev))
+    return out
+
+
+def fourstep_form(torch, g, steps, dev):
+    """Long 1D transforms beyond one CTA (four-step, two HBM passes):
+    4 x 2^24 and 1 x 2^26 points, both 512 MiB of input."""
+    import synth
+    out = {}
+    for n, b in ((1 << 24, 4), (1 << 26, 1)):
+        x = torch.from_numpy(synth.uniform_complex((b, n), seed=SEED)).to(dev)
+        y = torch.empty_like(x)
+        plan = g.get_plan(n, 1, b, False, "fp32", dev)
+        ms, passes = time_plan(torch, plan, x, y, max(10, steps // 4), 3, pass_events=True)
+        d = plan.describe()
+        out[f"fp32_1d_fourstep_{n}x{b}"] = {
+            "ms": ms, "GFLOP/s": flops_2d(n, 1, b) / ms / 1e6,
+            "HBM_GB/s_algorithmic": 32.0 * n * b / ms / 1e6,
+            "passes_ms": {"cols_twiddled": passes[0], "rows_transposed": passes[1]},
+            "n1_x_n2": [d["fourstep"]["n1"], d["fourstep"]["n2"]],
+            "kernels": [d["cols"]["kernel"], d["rows"]["kernel"]]}
+        del x, y
     return out
 
 
@@ -380,6 +402,12 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(n, n, b)
         X = torch.empty_like(x)
         run = lambda: (plan.execute(x, out=X), plan.backward_weighted(X, w, 2.0))  # noqa: E731
+    elif name.startswith("fourstep"):
+        n, b = (1 << 24, 4) if name == "fourstep_2p24" else (1 << 26, 1)
+        x = torch.from_numpy(synth.uniform_complex((b, n), seed=SEED)).to(dev)
+        plan = g.Plan(n, 1, b)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     else:
         if name == "split_tc_8192":
             x = synth.exp_mix_2d(8192, 8192, seed=SEED)[0]
@@ -407,7 +435,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
-                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "ragged", "diff"],
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "ragged", "diff", "fourstep_2p24",
+                             "fourstep_2p26"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

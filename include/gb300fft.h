@@ -65,8 +65,17 @@ enum {
 /*
  * fft_plan_create -- plan `batch` 2D transforms of size [ny][nx].
  *   nx, ny     powers of two, 1 <= n <= 8192 each (nx = 1 or ny = 1 gives a
- *              batch of 1D transforms along the other axis).
- *   batch      >= 1; slices are stored back to back, nx*ny elements apart.
+ *              batch of 1D transforms along the other axis).  A 1D length
+ *              (the other axis 1) may go up to 2^26: lengths above 8192 run
+ *              as the four-step decomposition the paper leaves as its next
+ *              step (Section 6) -- n = n1*n2, length-n1 FFTs down the columns
+ *              of the [n1][n2] view, then the twiddle w_n^{i2*k1} applied as
+ *              the rows are loaded and length-n2 FFTs along them, stored
+ *              transposed -- two HBM passes through a plan-owned workspace of
+ *              n*batch complex values.  Such plans are FFT_PREC_FP32 only
+ *              (else FFT_ERR_UNSUPPORTED) and have no fft_backward_weighted.
+ *   batch      >= 1; slices are stored back to back, nx*ny elements apart;
+ *              nx*ny*batch <= 2^31.
  *   dir        FFT_FORWARD or FFT_INVERSE: the exponent sign of fft_execute.
  *   precision  FFT_PREC_FP32 or FFT_PREC_SPLIT_FP16_TC.  The split form needs
  *              every transformed length >= 16 (a radix-16 stage) and, for 2D,
@@ -80,7 +89,8 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision);
 /*
  * fft_execute -- out = DFT_dir(in) for the plan's batch (Section 5: row
  * FFTs, then column FFTs, natural-order output).  `in` and `out` are device
- * pointers to batch*ny*nx complex64 each; `in` is read only when in != out.
+ * pointers to batch*ny*nx complex64 each, 16-byte aligned; in == out is
+ * allowed.  Four-step plans read `in` whole before writing `out`.
  */
 int fft_execute(fft_plan_t p, const void *in, void *out, void *stream);
 
@@ -98,6 +108,8 @@ int fft_backward(fft_plan_t p, const void *grad_out, void *grad_in, void *stream
  * L = sum w*|F x|^2, passing X = F x and scale = 2 gives dL/dx.
  *   X, grad_in  device complex64, batch*ny*nx elements (may alias).
  *   w           device float32, batch*ny*nx elements (must not alias X).
+ * Returns FFT_ERR_UNSUPPORTED for split-FP16 plans and 1D plans longer than
+ * 8192 (four-step).
  */
 int fft_backward_weighted(fft_plan_t p, const void *X, const void *w, float scale,
                           void *grad_in, void *stream);

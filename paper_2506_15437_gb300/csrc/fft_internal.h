@@ -98,6 +98,23 @@ cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out
 cudaError_t build_roots(float2 *t, int n, cudaStream_t s);
 int col_ctas_per_sm(const ColVariant &v);
 
+// Four-step large 1D FFT.  Pass A is the plain column pass (launch_cols, out
+// of place into the workspace); pass B (fft_fourstep.cu) is below: the
+// variant for row length n2 = 2^log2n (128..8192), e elements per thread and
+// w rows per CTA, or nullptr; fourstep_row_e / _w(n2) are the preferred ones.
+const ColVariant *fourstep_row_variant(int log2n, int e, int w);
+int fourstep_row_e(int n);
+int fourstep_row_w(int n);
+// Pass B: element i2 of row k1 of work [batch][n1][v.n] times w_n^{i2*k1}
+// (from lohi = [w_n^k, k < 8192 | w_n^{8192 k}, k < n/8192]), length-v.n FFTs
+// of the rows, element k2 of row k1 stored at out[b][k] with k = k1 + n1*k2,
+// or at out[b][(n - k) mod n] if reverse (which turns the forward transform
+// into the inverse).
+cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2 *out, const float2 *tw,
+                                 const float2 *lohi, int n1, int batch, int reverse, cudaStream_t s);
+// t[k] = exp(-2*pi*i*(k*stride mod n)/n), k < count, built in FP64.
+cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s);
+
 // Reorder-map debug launchers: write map[i] = output position of input i.
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s);
 cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s);
@@ -145,6 +162,21 @@ struct AxisPlan {
 };
 
 
+// A large 1D transform of length n = n1 * n2 > 8192 by the four-step
+// decomposition: pass A (columns of [n1][n2], twiddled) into `work`, pass B
+// (rows of work, stored transposed) into the output.
+struct FourStepPlan {
+    int n = 0, n1 = 0, n2 = 0;  // n1 == 0: not a four-step plan
+    const ColVariant *a = nullptr;
+    const ColVariant *b = nullptr;
+    float2 *tw_a = nullptr, *tw_b = nullptr;  // stage twiddles of the two passes
+    float2 *lohi = nullptr;                   // w_n^k (k < 8192), then w_n^{8192 k} (k < n / 8192)
+    float2 *work = nullptr;                   // [batch][n1][n2] workspace
+    int grid_a = 0;
+    CUtensorMap map;  // pass A's view of the last input pointer
+    const void *map_base = nullptr;
+};
+
 struct RaggedState;
 void ragged_destroy(RaggedState *r);
 
@@ -160,6 +192,7 @@ struct fft_plan_s {
     gb300fft::AxisPlan rows;        // length nx (or ny when nx == 1)
     gb300fft::AxisPlan cols;        // length ny, used when nx > 1 and ny > 1
     gb300fft::AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
+    gb300fft::FourStepPlan fs;      // large 1D plans (n > 8192)
     int split = 1;        // column pre-split P done by the row pass (out of place only)
     float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
     int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]

@@ -270,6 +270,60 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
     return FFT_OK;
 }
 
+// A large 1D plan (n > 8192): row length n2 (pass B) and column length
+// n1 = n / n2 (pass A), both <= 8192; both passes keep whole-sector tiles up
+// to n = 2^24, above that one length is 8192 with 16-byte tile rows.
+int setup_fourstep(fft_plan_s *p, int n) {
+    const int L = ilog2(n);
+    FourStepPlan &fs = p->fs;
+    fs.n = n;
+    // n2 = 2^ceil(L/2), except that a length-8192 row (16-byte store chunks)
+    // is avoided while n1 stays <= 8192 (2^25: 8192 x 4096 measured faster)
+    fs.n2 = 1 << ((L + 1) / 2);
+    if (fs.n2 == 8192 && n / 4096 <= 8192) fs.n2 = 4096;
+    // GB300FFT_FS_N2 / _FS_WA / _FS_EA / _FS_EB / _FS_WB: schedule
+    // experiments (row length, tile width and elements per thread of pass A,
+    // elements per thread and rows per CTA of pass B)
+    if (const char *ev = getenv("GB300FFT_FS_N2")) {
+        const int v = atoi(ev);
+        if (is_pow2(v) && v >= 128 && v <= 8192 && n / v >= 128 && n / v <= 8192) fs.n2 = v;
+    }
+    fs.n1 = n / fs.n2;
+    // pass A tile width: 4 from 2048 up, 8 at 1024, 16 below (measured; the
+    // 2D column pass's rule gives 8 at 2048, 0.31 vs 0.26 ms here)
+    int wa = fs.n1 >= 8192 ? 2 : fs.n1 >= 2048 ? 4 : fs.n1 == 1024 ? 8 : 16;
+    if (const char *ev = getenv("GB300FFT_FS_WA"))
+        if (col_variant(ilog2(fs.n1), default_col_e(fs.n1), atoi(ev)) && atoi(ev) <= fs.n2) wa = atoi(ev);
+    // E = 32 for the length-8192 column pass (measured 0.62 -> 0.52 ms at 2^26)
+    int ea = fs.n1 == 8192 ? 32 : preferred_col_e(fs.n1, wa), eb = fourstep_row_e(fs.n2);
+    int wb = fourstep_row_w(fs.n2);
+    if (const char *ev = getenv("GB300FFT_FS_EA"))
+        if (col_variant(ilog2(fs.n1), atoi(ev), wa)) ea = atoi(ev);
+    if (const char *ev = getenv("GB300FFT_FS_EB"))
+        if (fourstep_row_variant(ilog2(fs.n2), atoi(ev), wb)) eb = atoi(ev);
+    if (const char *ev = getenv("GB300FFT_FS_WB"))
+        if (fourstep_row_variant(ilog2(fs.n2), eb, atoi(ev))) wb = atoi(ev);
+    fs.a = col_variant(ilog2(fs.n1), ea, wa);
+    fs.b = fourstep_row_variant(ilog2(fs.n2), eb, wb);
+    if (!fs.a || !fs.b || fs.a->w > fs.n2 || fs.b->w > fs.n1) return FFT_ERR_UNSUPPORTED;
+    fs.tw_a = dev_alloc<float2>(p, fs.a->tw_size);
+    fs.tw_b = dev_alloc<float2>(p, fs.b->tw_size);
+    fs.lohi = dev_alloc<float2>(p, 8192 + n / 8192);
+    fs.work = dev_alloc<float2>(p, (size_t)n * p->batch);
+    if (!fs.tw_a || !fs.tw_b || !fs.lohi || !fs.work) return FFT_ERR_ALLOC;
+    if (build_twiddles(fs.tw_a, fs.n1, fs.a->e, 0) != cudaSuccess ||
+        build_twiddles(fs.tw_b, fs.n2, fs.b->e, 0) != cudaSuccess ||
+        build_roots_strided(fs.lohi, 8192, n, 1, 0) != cudaSuccess ||
+        build_roots_strided(fs.lohi + 8192, n / 8192, n, 8192, 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    const long long ntiles = (long long)p->batch * (fs.n2 / fs.a->w);
+    long long grid = (long long)p->num_sms * col_ctas_per_sm(*fs.a);
+    if (grid > ntiles) grid = ntiles;
+    fs.grid_a = (int)(grid < 1 ? 1 : grid);
+    p->rows.n = n;  // the transform length (no plain row variant)
+    return FFT_OK;
+}
+
 // A dense plan for (nx, ny, batch, dir, prec) running schedule `sc`.
 fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, const Schedule &sc, int *rc_out) {
     fft_plan_s *p = new (std::nothrow) fft_plan_s();
@@ -295,6 +349,8 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
     }
     if (rc != FFT_OK) {
+    } else if ((nx == 1 || ny == 1) && (nx > 8192 || ny > 8192)) {
+        rc = setup_fourstep(p, nx == 1 ? ny : nx);
     } else if (nx == 1 || ny == 1) {
         rc = setup_row_axis(p, p->rows, nx == 1 ? ny : nx, sc);
     } else {
@@ -341,6 +397,28 @@ void free_plan(fft_plan_s *p) {
     delete p;
 }
 
+// Large 1D transform: pass A (the plain column pass over the [n1][n2] view of
+// `in`, out of place into the workspace), pass B (twiddle on load, rows of the
+// workspace, stored transposed into `out`).  The inverse is the forward
+// transform stored at the reflected index (n - k) mod n.
+int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaStream_t s) {
+    FourStepPlan &fs = p->fs;
+    if (fs.map_base != src) {
+        if (encode_col_map(&fs.map, src, fs.n2, (long long)fs.n1 * p->batch, 1, fs.a->w, fs.a->box_rows) != 0)
+            return FFT_ERR_CUDA;
+        fs.map_base = src;
+    }
+    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (launch_cols(*fs.a, fs.map, fs.work, fs.tw_a, fs.n2, p->batch, 1, 0, p->status, fs.grid_a, 0, s) !=
+        cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
 // out = DFT_{sign}(in) (optionally weighted by scale*w on load) for a dense plan.
 int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
               cudaStream_t s) {
@@ -349,6 +427,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     float2 *dst = static_cast<float2 *>(out);
     if (!src || !dst || !aligned16(src) || !aligned16(dst)) return FFT_ERR_INVALID_ARG;
     cudaSetDevice(p->device);
+    if (p->fs.n1 > 0) return weight ? FFT_ERR_UNSUPPORTED : run_fourstep(p, src, dst, inv, s);
     const long long total = (long long)p->nx * p->ny * p->batch;
     if (p->rows.n == 1) {
         // 1x1 transforms are the identity (times the weight, if any)
@@ -470,7 +549,10 @@ const char *fft_error_string(int code) {
 
 fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
     t_last_error = FFT_OK;
-    if (!is_pow2(nx) || !is_pow2(ny) || nx > 8192 || ny > 8192 || batch < 1) {
+    // up to 8192 per axis; a single axis (1D batch) up to 2^26 by the four-step path
+    const bool large1d = (nx == 1 || ny == 1) && (nx > 8192 || ny > 8192);
+    if (!is_pow2(nx) || !is_pow2(ny) || batch < 1 || (large1d ? (nx > (1 << 26) || ny > (1 << 26))
+                                                              : (nx > 8192 || ny > 8192))) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
     }
@@ -484,6 +566,10 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
     }
     if ((long long)nx * ny * batch > (1LL << 31)) {
         fail(FFT_ERR_INVALID_SIZE);
+        return nullptr;
+    }
+    if (large1d && precision != FFT_PREC_FP32) {
+        fail(FFT_ERR_UNSUPPORTED);
         return nullptr;
     }
     Schedule sc = default_schedule(nx, ny);
@@ -569,7 +655,7 @@ int fft_plan_set_pass_events(fft_plan_t p, void *ev_start, void *ev_mid, void *e
 
 int fft_plan_autotune(fft_plan_t p, void *stream) {
     if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
-    if (p->prec != FFT_PREC_FP32) return FFT_OK;  // one schedule only
+    if (p->prec != FFT_PREC_FP32 || p->fs.n1 > 0) return FFT_OK;  // one schedule only
     cudaSetDevice(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long total = (long long)p->nx * p->ny * p->batch;
@@ -673,6 +759,19 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
     };
     if (p->kind == 1) {
         k = snprintf(tmp, sizeof tmp, "{\"kind\": \"ragged\", \"kernel\": \"k_ragged\"}");
+    } else if (p->fs.n1 > 0) {
+        const gb300fft::FourStepPlan &fs = p->fs;
+        char ra[96], rb[96];
+        rad(fs.n1, fs.a->e, ra, sizeof ra);
+        rad(fs.n2, fs.b->e, rb, sizeof rb);
+        k = snprintf(tmp, sizeof tmp,
+                     "{\"kind\": \"dense\", \"precision\": \"fp32\", \"fourstep\": {\"n\": %d, \"n1\": %d, "
+                     "\"n2\": %d}, \"rows\": {\"kernel\": \"k_rows_fourstep<%d,%d,%d>\", \"n\": %d, \"e\": %d, "
+                     "\"w\": %d, \"radices\": %s, \"persistent\": 0}, \"cols\": {\"kernel\": "
+                     "\"k_cols<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
+                     "\"grid\": %d}, \"split\": 1}",
+                     fs.n, fs.n1, fs.n2, fs.n2, fs.b->e, fs.b->w, fs.n2, fs.b->e, fs.b->w, rb, fs.n1, fs.a->e, fs.a->w,
+                     fs.n1, fs.a->e, fs.a->w, ra, fs.grid_a);
     } else {
         const bool tc = p->prec == FFT_PREC_SPLIT_FP16_TC;
         char r1[96] = "[]", r2[96] = "[]";

@@ -67,6 +67,23 @@ cudaError_t build_roots(float2 *t, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// t[k] = exp(-2*pi*i*(k*stride mod n)/n) for k < count: the two factor tables
+// of the four-step inter-pass twiddle (stride 1 and stride 8192).
+__global__ void k_roots_strided(float2 *t, int count, long long n, long long stride) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const long long a = ((long long)k * stride) % n;
+    double sv, cv;
+    sincospi(2.0 * (double)a / (double)n, &sv, &cv);
+    t[k] = make_float2((float)cv, (float)(-sv));
+}
+
+cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s) {
+    if (count < 1 || n < 1 || stride < 0) return cudaErrorInvalidValue;
+    k_roots_strided<<<(count + 255) / 256, 256, 0, s>>>(t, count, n, stride);
+    return cudaGetLastError();
+}
+
 // Partial sums of sum_i w[i] * |X[i]|^2: one float partial per CTA.  Each
 // thread keeps a compensated (Kahan) float sum over its grid-stride share,
 // then the CTA adds its threads' sums as a tree.  The caller adds the

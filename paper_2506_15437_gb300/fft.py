@@ -173,6 +173,31 @@ def fft2(x: torch.Tensor, inverse: bool = False, precision: str = "fp32") -> tor
     return FFT2Function.apply(x, inverse, precision)
 
 
+class FFT1Function(torch.autograd.Function):
+    """Differentiable 1D transform along the last axis.  Lengths up to 8192
+    run in one pass; longer ones (up to 2^26) as the two-pass four-step
+    decomposition.  backward = fft_backward, the conjugate transpose."""
+
+    @staticmethod
+    def forward(ctx, x, inverse: bool = False):
+        x = x.contiguous()
+        n = x.shape[-1]
+        plan = get_plan(n, 1, max(1, x.numel() // max(1, n)), inverse, "fp32", x.device)
+        ctx.plan = plan
+        return plan.execute(x)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.plan.backward(grad.contiguous()), None
+
+
+def fft1(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    """Unnormalised 1D DFT along the last axis of a complex64 CUDA tensor."""
+    if x.dim() < 1:
+        raise ValueError("fft1 needs at least 1 dimension")
+    return FFT1Function.apply(x, inverse)
+
+
 class WeightedPowerLoss(torch.autograd.Function):
     """L = sum w * |FFT2(x)|^2 with a fused adjoint: dL/dx = 2 F^H (w (.) F x),
     the weighting folded into the adjoint's first pass (fft_backward_weighted)."""

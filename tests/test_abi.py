@@ -56,10 +56,19 @@ def test_error_strings(lib):
 
 
 @pytest.mark.parametrize("nx,ny,batch", [(3, 4, 1), (4, 6, 1), (0, 8, 1), (8, 8, 0),
-                                         (16384, 2, 1), (2, 16384, 1), (-4, 4, 1)])
+                                         (16384, 2, 1), (2, 16384, 1), (-4, 4, 1),
+                                         (1 << 27, 1, 1), (1, 1 << 27, 1), (3 << 14, 1, 1),
+                                         (1 << 26, 1, 64)])
 def test_invalid_sizes_rejected_without_touching_the_gpu(lib, nx, ny, batch):
     assert lib.fft_plan_create(nx, ny, batch, -1, 0) is None
     assert lib.fft_last_error() == -1
+
+
+def test_long_1d_is_fp32_only(lib):
+    # the four-step path (1D lengths above 8192) has no split-FP16 form; the
+    # request is refused before any device call
+    assert lib.fft_plan_create(1 << 16, 1, 1, -1, 1) is None
+    assert lib.fft_last_error() == -5
 
 
 def test_invalid_direction_and_precision(lib):

@@ -1,0 +1,132 @@
+"""GPU parity of long 1D transforms (n = 2^14 .. 2^26, the four-step path)
+against the FP64 oracle, through the C ABI via the ctypes binding.
+
+Bar: relative L2 error per transform <= 2e-7 * log2(n).  Up to 2^22 the whole
+output is compared with the oracle's recursive transform; at 2^24 and at
+2^26 (the bench's launch configuration) sampled bins are compared with the
+oracle's per-bin definition, and Parseval and the round trip hold over the
+whole transform.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import ORACLE_THREADS, rel_l2, tol_fp32, worst_rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_15437_gb300 import build
+    build.build()
+    import paper_2506_15437_gb300 as g
+    return g
+
+
+def run(g, x, inverse=False, inplace=False):
+    n = x.shape[-1]
+    batch = x.size // n
+    plan = g.get_plan(n, 1, batch, inverse, "fp32", "cuda")
+    d = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = plan.execute(d, out=d if inplace else None)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return out.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("L", list(range(14, 22)))
+@pytest.mark.parametrize("inverse", [False, True])
+def test_full_against_oracle(g, L, inverse):
+    n = 1 << L
+    x = synth.uniform_complex((2, n), seed=300 + L)
+    got, plan = run(g, x, inverse)
+    d = plan.describe()
+    assert d["fourstep"]["n1"] * d["fourstep"]["n2"] == n
+    ref = oracle.fft1d_batch(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    err = worst_rel_l2(got, ref, n)
+    assert err <= tol_fp32(n), (L, inverse, err)
+
+
+def test_2p22_exp_mix(g):
+    n = 1 << 22
+    x, freqs = synth.exp_mix_1d(1, n, seed=2506)
+    got, _ = run(g, x)
+    ref = oracle.fft1d_batch(x, threads=ORACLE_THREADS)
+    assert rel_l2(got, ref) <= tol_fp32(n)
+    # the planted exponentials stand out at their own bins
+    assert np.all(np.abs(got[0, freqs[0]]) > 0.5 * n)
+
+
+def test_in_place(g):
+    n = 1 << 16
+    x = synth.uniform_complex((3, n), seed=77)
+    got, _ = run(g, x, inplace=True)
+    ref = oracle.fft1d_batch(x, threads=ORACLE_THREADS)
+    assert worst_rel_l2(got, ref, n) <= tol_fp32(n)
+
+
+def test_backward_is_the_opposite_sign_transform(g):
+    n = 1 << 18
+    gy = synth.uniform_complex((2, n), seed=91)
+    plan = g.get_plan(n, 1, 2, False, "fp32", "cuda")
+    d = torch.from_numpy(gy).cuda()
+    got = plan.backward(d).cpu().numpy()
+    ref = oracle.fft1d_batch(gy, dir=1, threads=ORACLE_THREADS)
+    assert worst_rel_l2(got, ref, n) <= tol_fp32(n)
+
+
+def test_fft1_autograd_matches_adjoint(g):
+    n = 1 << 15
+    x = torch.from_numpy(synth.uniform_complex((2, n), seed=5)).cuda().requires_grad_(True)
+    w = torch.from_numpy(synth.mask((2, n), seed=6)).cuda()
+    X = g.fft1(x)
+    loss = (w * X.real ** 2 + w * X.imag ** 2).sum()
+    loss.backward()
+    # dL/dx = 2 F^H (w X), F^H = the opposite-sign unnormalised transform
+    wX = w.cpu().numpy() * X.detach().cpu().numpy().astype(np.complex128)
+    ref = 2.0 * oracle.fft1d_batch(wX, dir=1, threads=ORACLE_THREADS)
+    assert worst_rel_l2(x.grad.cpu().numpy(), ref, n) <= 2 * tol_fp32(n)
+
+
+def test_weighted_adjoint_unsupported(g):
+    n = 1 << 14
+    plan = g.get_plan(n, 1, 1, False, "fp32", "cuda")
+    X = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    w = torch.zeros(n, dtype=torch.float32, device="cuda")
+    with pytest.raises(g.FFTError):
+        plan.backward_weighted(X, w, 2.0)
+
+
+@pytest.mark.parametrize("L,batch", [(24, 4), (26, 1)])
+def test_large_sampled_bins_parseval_roundtrip(g, L, batch):
+    """The bench's workloads: sampled bins of every transform against the
+    oracle's per-bin definition; Parseval and inverse(forward(x)) = n x over
+    the whole output."""
+    n = 1 << L
+    x = synth.uniform_complex((batch, n), seed=2506)
+    fwd = g.get_plan(n, 1, batch, False, "fp32", "cuda")
+    inv = g.get_plan(n, 1, batch, True, "fp32", "cuda")
+    d = torch.from_numpy(x).cuda()
+    X = fwd.execute(d)
+    back = inv.execute(X)
+    torch.cuda.synchronize()
+    assert fwd.status() == 0 and inv.status() == 0
+    tol = tol_fp32(n)
+    rng = np.random.default_rng(L)
+    bins = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 4)]))
+    Xh = X.cpu().numpy()
+    for b in range(batch):
+        ref = oracle.dft1d_bins(x[b], bins, threads=min(ORACLE_THREADS, bins.size))
+        # per-bin error relative to the transform's RMS magnitude sqrt(n)*rms(x)
+        scale = np.sqrt(n) * np.sqrt(np.mean(np.abs(x[b].astype(np.complex128)) ** 2))
+        assert np.abs(Xh[b, bins] - ref).max() <= 4 * tol * scale, b
+    e_x = np.sum(np.abs(x.astype(np.complex128)) ** 2, axis=1)
+    e_X = np.sum(np.abs(Xh.astype(np.complex128)) ** 2, axis=1)
+    assert np.all(np.abs(e_X - n * e_x) <= 2 * tol * n * e_x)
+    rt = back.cpu().numpy()
+    assert worst_rel_l2(rt, n * x.astype(np.complex128), n) <= 2 * tol
