@@ -33,55 +33,105 @@ struct FsRowShape {
     static constexpr int T = N / E;
     static constexpr int THREADS = T * W;
     using Eng = Engine<N, E, W, PadShift<E>::value>;
+    // landing layout of a tile: row c at c*ROWP (8 float2 of padding puts
+    // the W rows of a warp's reads in different bank halves)
+    static constexpr int ROWP = N + 8;
+    static constexpr int ELEMS = Eng::SMEM_ELEMS > W * ROWP ? Eng::SMEM_ELEMS : W * ROWP;
     static constexpr int GROW = E + 1;  // padded row of the twiddle-factor table
-    static constexpr size_t SMEM = sizeof(float2) * ((size_t)Eng::SMEM_ELEMS + (size_t)W * GROW);
+    static constexpr size_t G_OFF = (size_t)ELEMS * sizeof(float2);
+    static constexpr size_t BAR_OFF = (G_OFF + (size_t)W * GROW * sizeof(float2) + 15) / 16 * 16;
+    static constexpr size_t SMEM = BAR_OFF + 16;
+    static constexpr uint32_t TILE_BYTES = (uint32_t)W * N * sizeof(float2);
+    // E = 16: cap at 64 registers (several CTAs per SM); larger E: one CTA
+    static constexpr int MINB_RAW = E <= 16 ? 1024 / THREADS : 1;
+    static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 32 ? 32 : MINB_RAW);
 };
 
 __device__ __forceinline__ float2 root_n(const float2 *__restrict__ lohi, int a) {
     return cmul(__ldg(lohi + 8192 + (a >> 13)), __ldg(lohi + (a & 8191)));
 }
 
+// Persistent: CTA k takes tiles k, k + gridDim.x, ...  A tile's W rows are
+// contiguous in the workspace; W bulk copies (one per row, completion on an
+// mbarrier) land them in shared memory, the stage-0 operands are read from
+// there, and the buffer then serves as the Stockham exchange.  The next
+// tile's copies start as soon as every thread has read its last-stage
+// operands, so they overlap the last butterflies and the stores.
 template <int N, int E, int W>
-__global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS)
+__global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E, W>::MINB)
     k_rows_fourstep(const float2 *__restrict__ work, float2 *__restrict__ out, const float2 *__restrict__ tw,
-                    const float2 *__restrict__ lohi, int n1, long long ntiles, int reverse) {
+                    const float2 *__restrict__ lohi, int n1, long long ntiles, int reverse, int *status) {
     using Sh = FsRowShape<N, E, W>;
     using Eng = typename Sh::Eng;
     constexpr int R0 = Eng::R0;
     constexpr int T = Sh::T;
-    extern __shared__ __align__(16) float2 smem[];
-    float2 *G = smem + Eng::SMEM_ELEMS;  // [W][E + 1]
-    const long long id = blockIdx.x;
-    if (id >= ntiles) return;
+    extern __shared__ __align__(128) unsigned char raw[];
+    float2 *tile = reinterpret_cast<float2 *>(raw);
+    float2 *G = reinterpret_cast<float2 *>(raw + Sh::G_OFF);  // [W][E + 1]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    __shared__ int s_ok;
     const int groups = n1 / W;
-    const long long b = id / groups;  // transform within the batch
-    const int k10 = (int)(id - b * groups) * W;
     const int t = threadIdx.x;
     const int c = t % W;
     const int tt = t / W;
-    const float2 *src = work + (b * n1 + k10 + c) * (long long)N;
-    float2 v[E];
-#pragma unroll
-    for (int bb = 0; bb < E / R0; ++bb) {
-        const int j = tt + bb * T;
-#pragma unroll
-        for (int r = 0; r < R0; ++r) v[bb * R0 + r] = __ldcs(src + j + r * (N / R0));  // read once
-    }
-    for (int q = t; q < W * E; q += Sh::THREADS) {
-        const int cq = q / E, e = q % E;
-        const int me = (e / R0) * T + (e % R0) * (N / R0);
-        G[cq * Sh::GROW + e] = root_n(lohi, (k10 + cq) * me);  // k1 * m_e < n1 * n2
-    }
-    const float2 base = root_n(lohi, (k10 + c) * tt);
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(base, G[c * Sh::GROW + e]));
-    float2 *dst = out + b * (long long)n1 * N;
     const int mask = reverse ? n1 * N - 1 : -1;  // n = n1 * N is a power of two
     const int sgn = reverse ? -1 : 1;
-    auto none = [] {};
-    auto store = [&](int i, int cc, float2 x) { dst[(sgn * (k10 + cc + i * n1)) & mask] = x; };
-    Eng::template run<FftPolicy, false>(v, smem, tw, tt, c, SyncBlock{}, none, store);
+    auto issue = [&](long long id) {  // thread 0: the W row copies of tile `id`
+        mbar_expect_tx(bar, Sh::TILE_BYTES);
+        const float2 *src = work + id * (long long)W * N;
+#pragma unroll 1
+        for (int r = 0; r < W; ++r) bulk_load(tile + r * Sh::ROWP, src + (long long)r * N, N * sizeof(float2), bar);
+    };
+    if (t == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long id = blockIdx.x;
+    uint32_t phase = 0;
+    if (t == 0 && id < ntiles) issue(id);
+    for (; id < ntiles; id += gridDim.x) {
+        const long long b = id / groups;  // transform within the batch
+        const int k10 = (int)(id - b * groups) * W;
+        for (int q = t; q < W * E; q += Sh::THREADS) {
+            const int cq = q / E, e = q % E;
+            const int me = (e / R0) * T + (e % R0) * (N / R0);
+            G[cq * Sh::GROW + e] = root_n(lohi, (k10 + cq) * me);  // k1 * m_e < n1 * n2
+        }
+        const float2 base = root_n(lohi, (k10 + c) * tt);
+        if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (t == 0) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(bar, phase);  // give the copy in flight a last chance to land
+            }
+            return;
+        }
+        phase ^= 1;
+        const long long next = id + gridDim.x;
+        float2 v[E];
+#pragma unroll
+        for (int bb = 0; bb < E / R0; ++bb) {
+            const int j = tt + bb * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int e = bb * R0 + r;
+                v[e] = cmul(tile[c * Sh::ROWP + j + r * (N / R0)], cmul(base, G[c * Sh::GROW + e]));
+            }
+        }
+        float2 *dst = out + b * (long long)n1 * N;
+        auto after_reads = [&] {
+            __syncthreads();
+            if (t == 0 && next < ntiles) {
+                fence_proxy_async_smem();
+                issue(next);
+            }
+        };
+        auto store = [&](int i, int cc, float2 x) { dst[(sgn * (k10 + cc + i * n1)) & mask] = x; };
+        Eng::template run<FftPolicy, true>(v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
+    }
 }
 
 namespace {
@@ -132,10 +182,10 @@ void init_fs_rows() {
 // shared-memory exchange), 32 at 8192 (two), otherwise 16.
 int fourstep_row_e(int n) { return n == 4096 ? 64 : n == 8192 ? 32 : 16; }
 
-// Rows per CTA pass B prefers for row length n: 4 (32-byte store chunks,
-// 64-byte row segments per load; measured fastest from 128 to 4096), 2 at
-// 8192 (the exchange buffer's limit).
-int fourstep_row_w(int n) { return n >= 8192 ? 2 : 4; }
+// Rows per CTA pass B prefers for row length n: 4 (32-byte store chunks;
+// measured fastest from 256 to 4096), 8 at 128, 2 at 8192 (the exchange
+// buffer's limit).
+int fourstep_row_w(int n) { return n >= 8192 ? 2 : n <= 128 ? 8 : 4; }
 
 const ColVariant *fourstep_row_variant(int log2n, int e, int w) {
     init_fs_rows();
@@ -146,7 +196,7 @@ const ColVariant *fourstep_row_variant(int log2n, int e, int w) {
 }
 
 cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2 *out, const float2 *tw,
-                                 const float2 *lohi, int n1, int batch, int reverse, cudaStream_t s) {
+                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s) {
     if (v.w < 1 || n1 % v.w) return cudaErrorInvalidValue;
     const long long ntiles = (long long)batch * (n1 / v.w);
     if (ntiles < 1 || ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -154,9 +204,17 @@ cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2
         cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return e;
     }
-    void *args[] = {(void *)&work, (void *)&out,    (void *)&tw,     (void *)&lohi,
-                    (void *)&n1,   (void *)&ntiles, (void *)&reverse};
-    return cudaLaunchKernel(v.fn, dim3((unsigned)ntiles), dim3(v.threads), args, v.smem, s);
+    // persistent grid: every resident CTA slot once
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.threads, v.smem) != cudaSuccess)
+        return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > ntiles) grid = ntiles;
+    void *args[] = {(void *)&work, (void *)&out,    (void *)&tw,      (void *)&lohi,
+                    (void *)&n1,   (void *)&ntiles, (void *)&reverse, (void *)&status};
+    return cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
 }
 
 }  // namespace gb300fft

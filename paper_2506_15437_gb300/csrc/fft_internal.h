@@ -111,7 +111,7 @@ int fourstep_row_w(int n);
 // or at out[b][(n - k) mod n] if reverse (which turns the forward transform
 // into the inverse).
 cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2 *out, const float2 *tw,
-                                 const float2 *lohi, int n1, int batch, int reverse, cudaStream_t s);
+                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s);
 // t[k] = exp(-2*pi*i*(k*stride mod n)/n), k < count, built in FP64.
 cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s);
 

@@ -413,7 +413,8 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
         cudaSuccess)
         return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, s) != cudaSuccess)
+    if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, p->status, s) !=
+        cudaSuccess)
         return FFT_ERR_CUDA;
     if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
