@@ -302,9 +302,35 @@ def forms(torch, g, steps, warmup, dev):
                                  "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
     del x, y
     out.update(fourstep_form(torch, g, steps, dev))
+    out.update(energy_form(torch, g, dev))
     out.update(ragged_form(torch, g, steps, dev))
     out.update(diff_form(torch, g, steps, dev))
     return out
+
+
+def energy_form(torch, g, dev):
+    """Energy per transform from the board's NVML energy counter (the
+    paper's Table 3 metric: runtime, average power, joules per 2D FFT),
+    for its 1024 x 1024 workload and for 8192 x 8192; >= 2 s of back-to-back
+    transforms each, board idle power alongside."""
+    import synth
+    from paper_2506_15437_gb300.energy import EnergyMeter, NVMLError
+    try:
+        meter = EnergyMeter.for_torch_device(dev)
+        out = {"energy_idle_board_w": meter.idle_power_w(1.0)}
+        for n in (1024, 8192):
+            x = torch.from_numpy(synth.normal_complex((n, n), seed=SEED)).to(dev)
+            y = torch.empty_like(x)
+            plan = g.get_plan(n, n, 1, False, "fp32", dev)
+            for _ in range(3):
+                plan.execute(x, out=y)
+            r = meter.measure(lambda: plan.execute(x, out=y), torch.cuda.synchronize, flops_2d(n, n),
+                              min_seconds=2.0)
+            out[f"energy_fp32_fwd_{n}"] = r
+            del x, y
+        return out
+    except (NVMLError, AttributeError) as e:
+        return {"energy": {"unavailable": str(e)}}
 
 
 def fourstep_form(torch, g, steps, dev):
@@ -321,7 +347,7 @@ def fourstep_form(torch, g, steps, dev):
         out[f"fp32_1d_fourstep_{n}x{b}"] = {
             "ms": ms, "GFLOP/s": flops_2d(n, 1, b) / ms / 1e6,
             "HBM_GB/s_algorithmic": 32.0 * n * b / ms / 1e6,
-            "passes_ms": {"cols_twiddled": passes[0], "rows_transposed": passes[1]},
+            "passes_ms": {"cols": passes[0], "rows_twiddled_transposed": passes[1]},
             "n1_x_n2": [d["fourstep"]["n1"], d["fourstep"]["n2"]],
             "kernels": [d["cols"]["kernel"], d["rows"]["kernel"]]}
         del x, y
