@@ -33,9 +33,11 @@ struct FsRowShape {
     static constexpr int T = N / E;
     static constexpr int THREADS = T * W;
     using Eng = Engine<N, E, W, PadShift<E>::value>;
-    // landing layout of a tile: row c at c*ROWP (8 float2 of padding puts
-    // the W rows of a warp's reads in different bank halves)
-    static constexpr int ROWP = N + 8;
+    // landing layout of a tile: row c at c*ROWP.  A half-warp's 8-byte reads
+    // cover 16/W consecutive elements of each of its W rows; a padding of
+    // 16/W elements (at least 2, to keep each row's bulk copy 16-byte
+    // aligned) puts those W runs on disjoint banks.
+    static constexpr int ROWP = N + (16 / W > 2 ? 16 / W : 2);
     static constexpr int ELEMS = Eng::SMEM_ELEMS > W * ROWP ? Eng::SMEM_ELEMS : W * ROWP;
     static constexpr int GROW = E + 1;  // padded row of the twiddle-factor table
     static constexpr size_t G_OFF = (size_t)ELEMS * sizeof(float2);

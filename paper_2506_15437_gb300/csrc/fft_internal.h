@@ -55,7 +55,7 @@ cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s);
 cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw,
                         const float2 *twp, long long nrows, int ny, int split, int conj_in,
                         int conj_out, const float *weight, float wscale, int grid, int pf_dist,
-                        cudaStream_t s);
+                        int perm_t, int perm_g, cudaStream_t s);
 int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, int split, bool persistent);
 // Long-row pass with a TMA landing ring (fft_rows_ring.cu), n in 2048..8192.
 bool ring_rows_available(int n);
@@ -115,6 +115,14 @@ cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2
 // t[k] = exp(-2*pi*i*(k*stride mod n)/n), k < count, built in FP64.
 cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s);
 
+// Streaming column pass (fft_cols_stream.cu) over a row-permuted
+// intermediate: the variant for column length n and row length nx, or
+// nullptr; *perm_t / *perm_g receive the row permutation launch_rows must
+// apply (perm_t = stage-0 butterflies T, perm_g = butterflies per warp G).
+const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g);
+cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw, int nx,
+                               int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+
 // Reorder-map debug launchers: write map[i] = output position of input i.
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s);
 cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s);
@@ -141,6 +149,7 @@ struct Schedule {
     int col_w = 0;         // TMA tile width (0: default)
     int col_c = 2;         // cluster size of the DSMEM column kernel
     int col_pf = 0;        // TMA column pass: L2 prefetch distance (tiles)
+    int col_stream = 1;    // out-of-place calls: streaming column pass over row-permuted rows, where compiled
 };
 
 // One axis of a dense plan: a row-pass length (contiguous) or a column-pass
@@ -156,6 +165,11 @@ struct AxisPlan {
     int pair_e = 0;  // >0: column pass by 2-CTA clusters with this E (length n/2 sub-FFTs)
     int cl_c = 0, cl_e = 0;  // >0: column pass by cl_c-CTA DSMEM clusters with E = cl_e
     float2 *roots = nullptr;  // pair column pass: exp(-2*pi*i*k/n), k < n
+    // streaming column pass (out-of-place calls): kernel, the row permutation
+    // the row pass applies for it, its grid and twiddle table
+    const ColVariant *stream = nullptr;
+    int perm_t = 0, perm_g = 0, stream_grid = 0;
+    float2 *stream_tw = nullptr;
     // column pass: cached tensor map of the last output pointer
     CUtensorMap map;
     const void *map_base = nullptr;

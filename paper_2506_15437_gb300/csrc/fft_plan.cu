@@ -91,6 +91,7 @@ void apply_env_overrides(Schedule *sc) {
     geti("GB300FFT_COL_E", &sc->col_e);
     geti("GB300FFT_COL_W", &sc->col_w);
     geti("GB300FFT_COL_PF", &sc->col_pf);
+    geti("GB300FFT_COL_STREAM", &sc->col_stream);
     if (const char *ev = getenv("GB300FFT_COL_CLUSTER")) {
         const int c = atoi(ev);
         if (c == 2 || c == 4) {
@@ -151,6 +152,7 @@ bool tune_cache_lookup(int nx, int ny, int batch, int prec, Schedule *sc) {
         sc->col_e = json_int(l, "col_e", sc->col_e);
         sc->col_w = json_int(l, "col_w", sc->col_w);
         sc->col_c = json_int(l, "col_c", sc->col_c);
+        sc->col_stream = json_int(l, "col_stream", sc->col_stream);
         found = true;  // the last matching line wins
     }
     fclose(f);
@@ -170,9 +172,9 @@ void tune_cache_store(int nx, int ny, int batch, int prec, const Schedule &sc, f
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"row_e\": %d, \"row_persist\": %d, \"row_pf\": %d, \"split\": %d, "
-            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"ms\": %.5f}\n",
+            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"ms\": %.5f}\n",
             tune_key(nx, ny, batch, prec).c_str(), sc.row_e, sc.row_persist, sc.row_pf, sc.split, sc.col_kind,
-            sc.col_e, sc.col_w, sc.col_c, ms);
+            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, ms);
     fclose(f);
 }
 
@@ -267,6 +269,22 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     ax.grid = (int)grid;
+    int pt = 0, pg = 0;
+    const ColVariant *sv = sc.col_stream ? stream_col_variant(n, nx, &pt, &pg) : nullptr;
+    if (sv && sv->w == ax.col->w && sv->box_rows == ax.col->box_rows) {
+        ax.stream = sv;
+        ax.perm_t = pt;
+        ax.perm_g = pg;
+        if (ax.col->e == sv->e) {
+            ax.stream_tw = ax.tw;
+        } else {
+            ax.stream_tw = dev_alloc<float2>(p, sv->tw_size);
+            if (!ax.stream_tw) return FFT_ERR_ALLOC;
+            if (build_twiddles(ax.stream_tw, n, sv->e, 0) != cudaSuccess) return FFT_ERR_CUDA;
+        }
+        long long sg = (long long)p->num_sms * col_ctas_per_sm(*sv);
+        ax.stream_grid = (int)(sg > ntiles ? ntiles : (sg < 1 ? 1 : sg));
+    }
     return FFT_OK;
 }
 
@@ -463,6 +481,10 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
+    // out of place: the row pass may store its rows permuted for the
+    // streaming column pass (in place it must not: rows would overwrite rows
+    // other CTAs have yet to read)
+    const bool stream = two_pass && src != dst && cp.stream && !p->ring && cp.cl_c == 0 && cp.pair_e == 0;
     int &grid = p->row_grid[weight ? 1 : 0][P > 1 ? 1 : 0];
     if (grid == 0)
         grid = p->ring ? ring_rows_grid(p->rows.n, nrows, P, p->num_sms, weight != nullptr)
@@ -473,7 +495,8 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                                    (inv && !two_pass) ? 1 : 0, weight, wscale, p->status, grid, s)
                 : launch_rows(*p->rows.row, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
-                              (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, s);
+                              (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, stream ? cp.perm_t : 0,
+                              stream ? cp.perm_g : 0, s);
     if (er != cudaSuccess) return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
     if (!two_pass) {
@@ -505,9 +528,12 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
             return FFT_ERR_CUDA;
         cp.map_base = out;
     }
-    if (launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid, p->col_pf,
-                    s) != cudaSuccess)
-        return FFT_ERR_CUDA;
+    const cudaError_t ec =
+        stream ? launch_cols_stream(*cp.stream, cp.map, dst, cp.stream_tw, p->nx, p->batch, P, inv ? 1 : 0, p->status,
+                                    cp.stream_grid, s)
+               : launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid,
+                             p->col_pf, s);
+    if (ec != cudaSuccess) return FFT_ERR_CUDA;
     if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
@@ -691,6 +717,11 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                 const int cn = p->ny / split;
                 c.col_kind = kColTile;
                 cands.push_back(c);
+                if (stream_col_variant(cn, p->nx, nullptr, nullptr)) {
+                    Schedule d = c;
+                    d.col_stream = 0;
+                    cands.push_back(d);
+                }
                 for (int ce : {16, 64}) {
                     if (!col_variant(ilog2(cn), ce, default_col_w(cn, p->nx)) || ce == preferred_col_e(cn, default_col_w(cn, p->nx)))
                         continue;
@@ -797,7 +828,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"grid\": %d}, \"split\": %d}",
                      tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
-                     !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : "k_cols"), cp.n,
+                     !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
                      cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
                      cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
