@@ -17,6 +17,8 @@ Functions (all unnormalised, ``dir=-1`` forward, ``dir=+1`` inverse):
   a 2D transform (definition along one axis, recursive FFT along the other).
 * :func:`dft1d_bins` -- selected bins of one long 1D transform, each from the
   definition in one O(n) pass.
+* :func:`fft1d_any`, :func:`fft2d_any` -- any length (not only powers of two):
+  the recursion split by the smallest prime factor, primes from the definition.
 """
 from __future__ import annotations
 
@@ -64,9 +66,12 @@ def _bind(lib):
     lib.oracle_fft2d_rows.argtypes = [d, d, L, L, d, L, i, i]
     lib.oracle_fft2d_cols.argtypes = [d, d, L, L, d, L, i, i]
     lib.oracle_dft1d_bins.argtypes = [d, d, L, d, L, i, i]
+    lib.oracle_fft1d_any.argtypes = [d, d, L, L, i, i]
+    lib.oracle_fft2d_any.argtypes = [d, d, L, L, L, i, i]
     for f in ("oracle_fft1d_batch", "oracle_fft2d", "oracle_dft1d_brute",
               "oracle_dft2d_brute", "oracle_fft2d_rows", "oracle_fft2d_cols",
-              "oracle_dft1d_bins", "oracle_max_threads"):
+              "oracle_dft1d_bins", "oracle_fft1d_any", "oracle_fft2d_any",
+              "oracle_max_threads"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -168,4 +173,26 @@ def dft1d_bins(x, bins, dir: int = -1, threads: int = 1, lib=None) -> np.ndarray
     out = np.empty(k.size, dtype=np.complex128)
     _check(lib.oracle_dft1d_bins(a.ctypes.data, out.ctypes.data, a.size, k.ctypes.data, k.size,
                                  dir, threads), "dft1d_bins")
+    return out
+
+
+def fft1d_any(x, dir: int = -1, threads: int = 1, lib=None) -> np.ndarray:
+    """Transform of any length along the last axis of ``x``."""
+    lib = lib or load()
+    a = _c128(x)
+    n = a.shape[-1]
+    out = np.empty_like(a)
+    _check(lib.oracle_fft1d_any(a.ctypes.data, out.ctypes.data, n, a.size // max(n, 1), dir, threads),
+           "fft1d_any")
+    return out
+
+
+def fft2d_any(x, dir: int = -1, threads: int = 1, lib=None) -> np.ndarray:
+    """2D transform of each trailing ``[ny][nx]`` slice, any sizes."""
+    lib = lib or load()
+    a = _c128(x)
+    ny, nx = a.shape[-2], a.shape[-1]
+    out = np.empty_like(a)
+    _check(lib.oracle_fft2d_any(a.ctypes.data, out.ctypes.data, nx, ny, a.size // max(nx * ny, 1), dir,
+                                threads), "fft2d_any")
     return out

@@ -24,7 +24,9 @@
  * sampled-output functions combine the definition along one axis with the
  * recursive transform along the other, for spot checks of transforms too large
  * to recompute whole; oracle_dft1d_bins evaluates single bins of a long 1D
- * transform from the definition.
+ * transform from the definition.  oracle_fft1d_any / oracle_fft2d_any
+ * take any length: the same recursion split by the smallest prime factor
+ * instead of 2, with prime lengths from the definition.
  *
  * Data.  Interleaved complex128 (re, im) arrays, row-major [batch][ny][nx].
  * Inputs are never modified.  Every function returns 0 on success and a
@@ -182,6 +184,101 @@ int oracle_fft2d(const double *in, double *out, long nx, long ny, long batch, in
 #if ORACLE_MUTANT == 6
     free(xc);
 #endif
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Any length n >= 1 (not only powers of two).                               */
+/* ------------------------------------------------------------------------ */
+
+static long smallest_prime_factor(long n) {
+    if (n % 2 == 0) return 2;
+    for (long p = 3; p * p <= n; p += 2)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static cplx root_exact(long long p, long long n, int dir);
+
+/*
+ * Recursive mixed-radix Cooley-Tukey, decimation in time by the smallest
+ * prime factor p of n (the radix-2 split of Section 2.2 with 2 replaced by
+ * p): with m = n/p and Y_r the length-m transform of x[r], x[r+p], ...,
+ *     X[k] = sum_{r<p} exp(dir*2*pi*i*r*k/n) * Y_r[k mod m].
+ * A prime length is evaluated from the definition.  Inputs x[0], x[s], ...
+ */
+static void ct_any(const cplx *x, long s, cplx *X, long n, int dir) {
+    const long p = smallest_prime_factor(n);
+    if (p == n) {
+        for (long k = 0; k < n; ++k) {
+            double sr = 0.0, si = 0.0;
+            for (long j = 0; j < n; ++j) {
+                cplx w = root_exact(((long long)j * k) % n, n, dir);
+                cplx v = x[j * s];
+                sr += v.re * w.re - v.im * w.im;
+                si += v.re * w.im + v.im * w.re;
+            }
+            X[k].re = sr;
+            X[k].im = si;
+        }
+        return;
+    }
+    const long m = n / p;
+    cplx *Y = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    for (long r = 0; r < p; ++r) ct_any(x + r * s, s * p, Y + r * m, m, dir);
+    for (long k = 0; k < n; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (long r = 0; r < p; ++r) {
+#if ORACLE_MUTANT == 9
+            cplx w = root_exact(((long long)r * k) % m, n, dir); /* MUTANT 9: phase reduced mod m */
+#else
+            cplx w = root_exact(((long long)r * k) % n, n, dir);
+#endif
+            cplx v = Y[r * m + k % m];
+            sr += v.re * w.re - v.im * w.im;
+            si += v.re * w.im + v.im * w.re;
+        }
+        X[k].re = sr;
+        X[k].im = si;
+    }
+    free(Y);
+}
+
+/* howmany transforms of any length n >= 1 along contiguous rows. */
+int oracle_fft1d_any(const double *in, double *out, long n, long howmany, int dir, int threads) {
+    if (!in || !out || n < 1 || howmany < 0 || (dir != 1 && dir != -1)) return -1;
+    const cplx *x = (const cplx *)in;
+    cplx *X = (cplx *)out;
+    if (threads < 1) threads = 1;
+#pragma omp parallel for num_threads(threads) schedule(static)
+    for (long r = 0; r < howmany; ++r) ct_any(x + r * n, 1, X + r * n, n, dir);
+    return 0;
+}
+
+/* 2D transform of each [ny][nx] slice, any nx, ny >= 1: rows, then columns. */
+int oracle_fft2d_any(const double *in, double *out, long nx, long ny, long batch, int dir, int threads) {
+    if (!in || !out || nx < 1 || ny < 1 || batch < 0 || (dir != 1 && dir != -1)) return -1;
+    const cplx *x = (const cplx *)in;
+    cplx *X = (cplx *)out;
+    if (threads < 1) threads = 1;
+    const long N = nx * ny;
+#pragma omp parallel for num_threads(threads) schedule(static)
+    for (long r = 0; r < ny * batch; ++r) ct_any(x + r * nx, 1, X + r * nx, nx, dir);
+#pragma omp parallel num_threads(threads)
+    {
+        cplx *col = (cplx *)malloc(sizeof(cplx) * (size_t)ny);
+        cplx *res = (cplx *)malloc(sizeof(cplx) * (size_t)ny);
+#pragma omp for schedule(static)
+        for (long c = 0; c < nx * batch; ++c) {
+            const long b = c / nx, xi = c % nx;
+            cplx *base = X + b * N;
+            for (long y = 0; y < ny; ++y) col[y] = base[y * nx + xi];
+            ct_any(col, 1, res, ny, dir);
+            for (long y = 0; y < ny; ++y) base[y * nx + xi] = res[y];
+        }
+        free(col);
+        free(res);
+    }
     return 0;
 }
 

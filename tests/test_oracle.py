@@ -191,8 +191,49 @@ def pin_bins(lib):
     return bad
 
 
+def pin_any_length(lib):
+    """Any-length recursion: the definition for every n <= 64 and for
+    composite, prime and prime-power lengths; the radix-2 recursion at powers
+    of two; a closed form; Parseval and the round trip; 2D against the 2D
+    definition."""
+    bad = []
+    for n in list(range(1, 65)) + [96, 100, 127, 210, 243, 625, 1001]:
+        x = _rand((2, n), 500 + n)
+        for d in (-1, 1):
+            got = oracle.fft1d_any(x, dir=d, lib=lib)
+            for r in range(2):
+                if _rel(got[r], oracle.dft1d_brute(x[r], dir=d, lib=lib)) > 1e-13:
+                    bad.append(f"any n={n} dir={d}")
+    for n in (256, 4096):
+        x = _rand((n,), 7 * n)
+        if _rel(oracle.fft1d_any(x, lib=lib), oracle.fft1d_batch(x, lib=lib)) > 1e-13:
+            bad.append(f"any vs radix-2 n={n}")
+    n, f = 3000, 1234
+    e = np.exp(2j * np.pi * ((f * np.arange(n)) % n) / n)
+    want = np.zeros(n, np.complex128)
+    want[f] = n
+    if np.abs(oracle.fft1d_any(e, lib=lib) - want).max() > 1e-10 * n:
+        bad.append("any exp spike")
+    n = 3 * 5 * 7 * 11
+    x = _rand((n,), 99)
+    X = oracle.fft1d_any(x, lib=lib)
+    if abs(np.sum(np.abs(X) ** 2) - n * np.sum(np.abs(x) ** 2)) > 1e-12 * n * np.sum(np.abs(x) ** 2):
+        bad.append("any parseval")
+    if _rel(oracle.fft1d_any(X, dir=1, lib=lib), n * x) > 1e-13:
+        bad.append("any roundtrip")
+    for ny, nx in [(3, 5), (6, 10), (12, 7), (15, 15), (1, 9), (11, 1)]:
+        x = _rand((ny, nx), 3 * nx + ny)
+        for d in (-1, 1):
+            if _rel(oracle.fft2d_any(x, dir=d, lib=lib), oracle.dft2d_brute(x, dir=d, lib=lib)) > 1e-13:
+                bad.append(f"any 2d {ny}x{nx} dir={d}")
+    x = _rand((2, 32, 64), 17)
+    if _rel(oracle.fft2d_any(x, lib=lib), oracle.fft2d(x, lib=lib)) > 1e-13:
+        bad.append("any 2d vs radix-2")
+    return bad
+
+
 PINS = [pin_bruteforce_1d, pin_bruteforce_2d, pin_golden, pin_closed_forms,
-        pin_invariants, pin_library, pin_sampled, pin_bins]
+        pin_invariants, pin_library, pin_sampled, pin_bins, pin_any_length]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -223,9 +264,10 @@ def test_bad_arguments_rejected():
 # Each mutant plants one plausible mistake in oracle.c (see ORACLE_MUTANT):
 # 1 twiddle sign, 2 dropped term, 3 off-by-one twiddle index, 4 transposed
 # length in the column pass, 5 dropped column pass, 6 conjugated input,
-# 7 brute-force sign, 8 neighbouring bin in the per-bin definition.  Every
-# one must fail at least one pin.
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8])
+# 7 brute-force sign, 8 neighbouring bin in the per-bin definition, 9 the
+# any-length combining phase reduced modulo the wrong length.  Every one must
+# fail at least one pin.
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_pins_catch_mutant(mutant):
     lib = oracle.load(mutant=mutant)
     failures = []
