@@ -1,0 +1,157 @@
+// Transforms of any length: Bluestein's chirp-z identity on top of the
+// power-of-two path.  The paper's future work asks for uneven decompositions
+// beyond powers of two (Section 6); this is the general route.
+//
+// With c[j] = exp(dir*pi*i*j^2/n) (dir = -1 forward) and j*k = (j^2 + k^2 -
+// (k-j)^2)/2,
+//     X[k] = c[k] * sum_{j<n} (x[j] c[j]) * conj(c[k-j]),
+// a linear convolution of a[j] = x[j] c[j] with h[m] = conj(c[m]),
+// |m| < n.  Zero-padded to a power of two M >= 2n - 1 it is a circular one,
+// computed as conv = F^-1( F(a) . F(h) ) / M with the library's own
+// power-of-two transforms (one plan of length M, run forward and inverse).
+// H = F(h) / M is built once per plan and direction.  The chirp's phase
+// j^2 mod 2n is reduced in integers and evaluated in FP64 (sincospi), then
+// rounded once to FP32.
+//
+// A 2D transform whose sizes are not both powers of two runs axis by axis:
+// the x axis over all rows, a tiled transpose, the y axis over the rows of
+// the transposed array, and the transpose back.
+#include "fft_common.cuh"
+#include "fft_internal.h"
+
+namespace gb300fft {
+
+// c[j] = exp(sgn*pi*i*(j^2 mod 2n)/n), j < n
+__global__ void k_chirp(float2 *c, int n, int sgn) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const long long q = ((long long)j * j) % (2LL * n);
+    double sv, cv;
+    sincospi((double)q / (double)n, &sv, &cv);
+    c[j] = make_float2((float)cv, (float)(sgn * sv));
+}
+
+// h[m] = conj(c[|m|]) placed circularly in M slots (m and M - m), zero between
+__global__ void k_chirp_filter(float2 *h, const float2 *__restrict__ c, int n, int M) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int idx = -1;
+    if (m < n) idx = m;
+    else if (m > M - n) idx = M - m;
+    h[m] = idx >= 0 ? make_float2(c[idx].x, -c[idx].y) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_scale(float2 *a, long long count, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 v = a[i];
+        a[i] = make_float2(v.x * s, v.y * s);
+    }
+}
+
+// A[r][j] = x[r][j] * c[j] for j < n, 0 for n <= j < M
+__global__ void k_blu_pre(const float2 *__restrict__ x, float2 *__restrict__ A, const float2 *__restrict__ c, int n,
+                          int M, long long rows) {
+    const long long total = rows * M;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / M;
+        const int j = (int)(i - r * M);
+        A[i] = j < n ? cmul(__ldg(x + r * n + j), __ldg(c + j)) : make_float2(0.f, 0.f);
+    }
+}
+
+// A[r][k] *= H[k]
+__global__ void k_blu_mul(float2 *A, const float2 *__restrict__ H, int M, long long rows) {
+    const long long total = rows * M;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % M);
+        A[i] = cmul(A[i], __ldg(H + k));
+    }
+}
+
+// out[r][k] = c[k] * A[r][k], k < n
+__global__ void k_blu_post(const float2 *__restrict__ A, float2 *__restrict__ out, const float2 *__restrict__ c,
+                           int n, int M, long long rows) {
+    const long long total = rows * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / n;
+        const int k = (int)(i - r * n);
+        out[i] = cmul(__ldg(A + r * M + k), __ldg(c + k));
+    }
+}
+
+// out[b][cc][rr] = in[b][rr][cc] for [batch][rows][cols] arrays, through
+// 32 x 32 tiles in shared memory (one padding column: conflict-free both ways)
+__global__ void __launch_bounds__(256) k_transpose(const float2 *__restrict__ in, float2 *__restrict__ out, int rows,
+                                                   int cols, long long tiles_c, long long tiles_rc) {
+    __shared__ float2 tile[32][33];
+    const long long b = blockIdx.x / tiles_rc;
+    const long long rem = blockIdx.x - b * tiles_rc;
+    const int tr = (int)(rem / tiles_c), tc = (int)(rem - (long long)tr * tiles_c);
+    const float2 *src = in + b * (long long)rows * cols;
+    float2 *dst = out + b * (long long)rows * cols;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+#pragma unroll
+    for (int k = 0; k < 32; k += 8) {
+        const int r = tr * 32 + ty + k, cc = tc * 32 + tx;
+        if (r < rows && cc < cols) tile[ty + k][tx] = src[(long long)r * cols + cc];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; k += 8) {
+        const int cc = tc * 32 + ty + k, r = tr * 32 + tx;
+        if (r < rows && cc < cols) dst[(long long)cc * rows + r] = tile[tx][ty + k];
+    }
+}
+
+namespace {
+int blocks_for(long long count) {
+    long long b = (count + 255) / 256;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+}  // namespace
+
+cudaError_t build_chirp(float2 *c, int n, int sgn, cudaStream_t s) {
+    k_chirp<<<(n + 255) / 256, 256, 0, s>>>(c, n, sgn);
+    return cudaGetLastError();
+}
+
+cudaError_t build_chirp_filter(float2 *h, const float2 *c, int n, int M, cudaStream_t s) {
+    k_chirp_filter<<<(M + 255) / 256, 256, 0, s>>>(h, c, n, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float2 *a, long long count, float sc, cudaStream_t s) {
+    k_scale<<<blocks_for(count), 256, 0, s>>>(a, count, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blu_pre(const float2 *x, float2 *A, const float2 *c, int n, int M, long long rows, cudaStream_t s) {
+    k_blu_pre<<<blocks_for(rows * M), 256, 0, s>>>(x, A, c, n, M, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blu_mul(float2 *A, const float2 *H, int M, long long rows, cudaStream_t s) {
+    k_blu_mul<<<blocks_for(rows * M), 256, 0, s>>>(A, H, M, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blu_post(const float2 *A, float2 *out, const float2 *c, int n, int M, long long rows,
+                            cudaStream_t s) {
+    k_blu_post<<<blocks_for(rows * n), 256, 0, s>>>(A, out, c, n, M, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float2 *in, float2 *out, int rows, int cols, long long batch, cudaStream_t s) {
+    const long long tiles_c = (cols + 31) / 32, tiles_r = (rows + 31) / 32;
+    const long long blocks = batch * tiles_r * tiles_c;
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_transpose<<<(unsigned)blocks, 256, 0, s>>>(in, out, rows, cols, tiles_c, tiles_r * tiles_c);
+    return cudaGetLastError();
+}
+
+}  // namespace gb300fft

@@ -191,6 +191,32 @@ struct FourStepPlan {
     const void *map_base = nullptr;
 };
 
+// Any-size transforms (fft_bluestein.cu kernels, fft_plan.cu logic).  One
+// axis: `rows` transforms of length n along contiguous rows, by a
+// power-of-two sub-plan (M == 0) or by Bluestein over a length-M sub-plan.
+struct AnyAxis {
+    int n = 1, M = 0;
+    long long rows = 0;
+    fft_plan_s *sub = nullptr;           // (n or M, 1, rows), run forward and inverse
+    float2 *chirp[2] = {nullptr, nullptr};  // [0] forward exp(-pi i j^2/n), [1] its conjugate
+    float2 *H[2] = {nullptr, nullptr};      // F(filter)/M for each direction
+    float2 *A = nullptr;                    // rows * M workspace
+};
+// A plan whose sizes are not all powers of two: x axis over the rows, then
+// (2D) transpose, y axis over the rows of the transposed array, transpose back.
+struct AnyPlan {
+    AnyAxis x, y;                // y.n == 1: a 1D batch
+    float2 *t = nullptr;         // [batch][nx][ny] transposed workspace
+};
+cudaError_t build_chirp(float2 *c, int n, int sgn, cudaStream_t s);
+cudaError_t build_chirp_filter(float2 *h, const float2 *c, int n, int M, cudaStream_t s);
+cudaError_t launch_scale(float2 *a, long long count, float sc, cudaStream_t s);
+cudaError_t launch_blu_pre(const float2 *x, float2 *A, const float2 *c, int n, int M, long long rows, cudaStream_t s);
+cudaError_t launch_blu_mul(float2 *A, const float2 *H, int M, long long rows, cudaStream_t s);
+cudaError_t launch_blu_post(const float2 *A, float2 *out, const float2 *c, int n, int M, long long rows,
+                            cudaStream_t s);
+cudaError_t launch_transpose(const float2 *in, float2 *out, int rows, int cols, long long batch, cudaStream_t s);
+
 struct RaggedState;
 void ragged_destroy(RaggedState *r);
 
@@ -207,6 +233,7 @@ struct fft_plan_s {
     gb300fft::AxisPlan cols;        // length ny, used when nx > 1 and ny > 1
     gb300fft::AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
     gb300fft::FourStepPlan fs;      // large 1D plans (n > 8192)
+    gb300fft::AnyPlan *any = nullptr;  // sizes that are not all powers of two
     int split = 1;        // column pre-split P done by the row pass (out of place only)
     float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
     int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]

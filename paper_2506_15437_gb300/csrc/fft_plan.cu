@@ -405,14 +405,149 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
     return p;
 }
 
+long long next_pow2(long long v) {
+    long long m = 1;
+    while (m < v) m <<= 1;
+    return m;
+}
+
+// One axis of an any-size plan: rows transforms of length n.  A power of two
+// gets a dense sub-plan of its own; any other n gets Bluestein over a
+// length-M power-of-two sub-plan, M >= 2n - 1, with the chirps and the
+// filter transforms built here.
+int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
+    ax.n = n;
+    ax.rows = rows;
+    int rc = FFT_OK;
+    if (is_pow2(n)) {
+        ax.sub = create_dense(n, 1, (int)rows, FFT_FORWARD, FFT_PREC_FP32, default_schedule(n, 1), &rc);
+        return ax.sub ? FFT_OK : rc;
+    }
+    ax.M = (int)next_pow2(2LL * n - 1);
+    if (rows * ax.M > (1LL << 31)) return FFT_ERR_INVALID_SIZE;
+    ax.sub = create_dense(ax.M, 1, (int)rows, FFT_FORWARD, FFT_PREC_FP32, default_schedule(ax.M, 1), &rc);
+    if (!ax.sub) return rc;
+    for (int d = 0; d < 2; ++d) {
+        ax.chirp[d] = dev_alloc<float2>(p, n);
+        ax.H[d] = dev_alloc<float2>(p, ax.M);
+        if (!ax.chirp[d] || !ax.H[d]) return FFT_ERR_ALLOC;
+    }
+    ax.A = dev_alloc<float2>(p, (size_t)rows * ax.M);
+    if (!ax.A) return FFT_ERR_ALLOC;
+    // H[d] = F(filter of chirp d) / M through a one-row plan of length M
+    fft_plan_s *one = create_dense(ax.M, 1, 1, FFT_FORWARD, FFT_PREC_FP32, default_schedule(ax.M, 1), &rc);
+    if (!one) return rc;
+    for (int d = 0; d < 2 && rc == FFT_OK; ++d) {
+        if (build_chirp(ax.chirp[d], n, d == 0 ? -1 : 1, 0) != cudaSuccess ||
+            build_chirp_filter(ax.A, ax.chirp[d], n, ax.M, 0) != cudaSuccess)
+            rc = FFT_ERR_CUDA;
+        if (rc == FFT_OK) rc = run_dense(one, ax.A, ax.H[d], FFT_FORWARD, nullptr, 1.f, 0);
+        if (rc == FFT_OK && launch_scale(ax.H[d], ax.M, 1.0f / (float)ax.M, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
+    free_plan(one);
+    return rc;
+}
+
+// A plan for sizes that are not all powers of two (FP32): nx == 1 or ny == 1
+// is a 1D batch; otherwise x axis, transpose, y axis, transpose.
+fft_plan_s *create_any(int nx, int ny, int batch, int dir, int *rc_out) {
+    fft_plan_s *p = new (std::nothrow) fft_plan_s();
+    AnyPlan *ap = new (std::nothrow) AnyPlan();
+    if (!p || !ap) {
+        delete p;
+        delete ap;
+        *rc_out = FFT_ERR_ALLOC;
+        return nullptr;
+    }
+    p->nx = nx;
+    p->ny = ny;
+    p->batch = batch;
+    p->dir = dir;
+    p->prec = FFT_PREC_FP32;
+    p->any = ap;
+    int rc = FFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        rc = FFT_ERR_CUDA;
+    if (rc == FFT_OK) {
+        if (nx == 1 || ny == 1) {
+            rc = setup_any_axis(p, ap->x, nx == 1 ? ny : nx, batch);
+        } else {
+            rc = setup_any_axis(p, ap->x, nx, (long long)ny * batch);
+            if (rc == FFT_OK) rc = setup_any_axis(p, ap->y, ny, (long long)nx * batch);
+            if (rc == FFT_OK) {
+                ap->t = dev_alloc<float2>(p, (size_t)nx * ny * batch);
+                if (!ap->t) rc = FFT_ERR_ALLOC;
+            }
+        }
+    }
+    if (rc == FFT_OK) {
+        p->status = dev_alloc<int>(p, 1);
+        if (!p->status) rc = FFT_ERR_ALLOC;
+        else if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    // the sub-plans' kernels report into this plan's status word
+    if (rc == FFT_OK) {
+        if (ap->x.sub) ap->x.sub->status = p->status;
+        if (ap->y.sub) ap->y.sub->status = p->status;
+    }
+    p->wp_parts = p->num_sms * 4;
+    if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
+    if (rc != FFT_OK) {
+        free_plan(p);
+        *rc_out = rc;
+        return nullptr;
+    }
+    *rc_out = FFT_OK;
+    return p;
+}
+
 }  // namespace
 
 namespace gb300fft {
 void free_plan(fft_plan_s *p) {
     if (!p) return;
     if (p->ragged) ragged_destroy(p->ragged);
+    if (p->any) {
+        free_plan(p->any->x.sub);
+        free_plan(p->any->y.sub);
+        delete p->any;
+    }
     for (void *d : p->allocations) cudaFree(d);
     delete p;
+}
+
+// rows transforms of length ax.n along contiguous rows, in -> out (may alias)
+int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStream_t s) {
+    if (!ax.M) return run_dense(ax.sub, in, out, sign, nullptr, 1.f, s);
+    const int d = sign > 0 ? 1 : 0;
+    if (launch_blu_pre(in, ax.A, ax.chirp[d], ax.n, ax.M, ax.rows, s) != cudaSuccess) return FFT_ERR_CUDA;
+    int rc = run_dense(ax.sub, ax.A, ax.A, FFT_FORWARD, nullptr, 1.f, s);
+    if (rc != FFT_OK) return rc;
+    if (launch_blu_mul(ax.A, ax.H[d], ax.M, ax.rows, s) != cudaSuccess) return FFT_ERR_CUDA;
+    rc = run_dense(ax.sub, ax.A, ax.A, FFT_INVERSE, nullptr, 1.f, s);
+    if (rc != FFT_OK) return rc;
+    if (launch_blu_post(ax.A, out, ax.chirp[d], ax.n, ax.M, ax.rows, s) != cudaSuccess) return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
+// out = DFT_sign(in) for an any-size plan
+int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_t s) {
+    AnyPlan &ap = *p->any;
+    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    int rc = run_any_axis(ap.x, src, dst, sign, s);
+    if (rc != FFT_OK) return rc;
+    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (ap.y.sub) {
+        const long long batch = p->batch;
+        if (launch_transpose(dst, ap.t, p->ny, p->nx, batch, s) != cudaSuccess) return FFT_ERR_CUDA;
+        rc = run_any_axis(ap.y, ap.t, ap.t, sign, s);
+        if (rc != FFT_OK) return rc;
+        if (launch_transpose(ap.t, dst, p->nx, p->ny, batch, s) != cudaSuccess) return FFT_ERR_CUDA;
+    }
+    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    return FFT_OK;
 }
 
 // Large 1D transform: pass A (the plain column pass over the [n1][n2] view of
@@ -446,6 +581,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     float2 *dst = static_cast<float2 *>(out);
     if (!src || !dst || !aligned16(src) || !aligned16(dst)) return FFT_ERR_INVALID_ARG;
     cudaSetDevice(p->device);
+    if (p->any) return weight ? FFT_ERR_UNSUPPORTED : run_any(p, src, dst, sign, s);
     if (p->fs.n1 > 0) return weight ? FFT_ERR_UNSUPPORTED : run_fourstep(p, src, dst, inv, s);
     const long long total = (long long)p->nx * p->ny * p->batch;
     if (p->rows.n == 1) {
@@ -576,10 +712,14 @@ const char *fft_error_string(int code) {
 
 fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
     t_last_error = FFT_OK;
-    // up to 8192 per axis; a single axis (1D batch) up to 2^26 by the four-step path
-    const bool large1d = (nx == 1 || ny == 1) && (nx > 8192 || ny > 8192);
-    if (!is_pow2(nx) || !is_pow2(ny) || batch < 1 || (large1d ? (nx > (1 << 26) || ny > (1 << 26))
-                                                              : (nx > 8192 || ny > 8192))) {
+    // powers of two: up to 8192 per axis, a single axis (1D batch) up to 2^26
+    // by the four-step path; other sizes (Bluestein): a 1D length up to 2^24,
+    // 2D axes up to 65536
+    const bool pow2 = is_pow2(nx) && is_pow2(ny);
+    const bool oned = nx == 1 || ny == 1;
+    const bool large1d = pow2 && oned && (nx > 8192 || ny > 8192);
+    const int cap = pow2 ? (large1d ? (1 << 26) : 8192) : (oned ? (1 << 24) : 65536);
+    if (nx < 1 || ny < 1 || batch < 1 || nx > cap || ny > cap) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
     }
@@ -595,9 +735,15 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
     }
-    if (large1d && precision != FFT_PREC_FP32) {
+    if ((large1d || !pow2) && precision != FFT_PREC_FP32) {
         fail(FFT_ERR_UNSUPPORTED);
         return nullptr;
+    }
+    if (!pow2) {
+        int rc = FFT_OK;
+        fft_plan_s *p = create_any(nx, ny, batch, dir, &rc);
+        if (!p) fail(rc);
+        return p;
     }
     Schedule sc = default_schedule(nx, ny);
     const bool cached = precision == FFT_PREC_FP32 && tune_cache_lookup(nx, ny, batch, precision, &sc);
@@ -682,7 +828,7 @@ int fft_plan_set_pass_events(fft_plan_t p, void *ev_start, void *ev_mid, void *e
 
 int fft_plan_autotune(fft_plan_t p, void *stream) {
     if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
-    if (p->prec != FFT_PREC_FP32 || p->fs.n1 > 0) return FFT_OK;  // one schedule only
+    if (p->prec != FFT_PREC_FP32 || p->fs.n1 > 0 || p->any) return FFT_OK;  // one schedule only
     cudaSetDevice(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long total = (long long)p->nx * p->ny * p->batch;
@@ -791,6 +937,12 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
     };
     if (p->kind == 1) {
         k = snprintf(tmp, sizeof tmp, "{\"kind\": \"ragged\", \"kernel\": \"k_ragged\"}");
+    } else if (p->any) {
+        const gb300fft::AnyPlan &ap = *p->any;
+        k = snprintf(tmp, sizeof tmp,
+                     "{\"kind\": \"any\", \"precision\": \"fp32\", \"x\": {\"n\": %d, \"bluestein_m\": %d}, "
+                     "\"y\": {\"n\": %d, \"bluestein_m\": %d}, \"transposes\": %d}",
+                     ap.x.n, ap.x.M, ap.y.n, ap.y.M, ap.y.sub ? 2 : 0);
     } else if (p->fs.n1 > 0) {
         const gb300fft::FourStepPlan &fs = p->fs;
         char ra[96], rb[96];

@@ -45,3 +45,27 @@ def digit_reversal(n: int, radices) -> np.ndarray:
         out += d * mult
         mult *= R
     return out
+
+
+def bluestein_m(n: int) -> int:
+    """Power-of-two length of the circular convolution for a length-n axis."""
+    m = 1
+    while m < 2 * n - 1:
+        m <<= 1
+    return m
+
+
+def tol_any_axis(n: int) -> float:
+    """FP32 bound for one axis of any length.  A power of two is the plain
+    path (2e-7 * log2 n); any other n goes through Bluestein: two transforms
+    of length M = bluestein_m(n), the filter transform (a third one, computed
+    once in FP32) and three roundings by unit-modulus factors, so
+    2e-7 * (3 * log2 M + 3)."""
+    if n & (n - 1) == 0:
+        return 2e-7 * max(1.0, math.log2(n))
+    return 2e-7 * (3 * math.log2(bluestein_m(n)) + 3)
+
+
+def tol_any(nx: int, ny: int) -> float:
+    """Errors of the two axes add (a transpose is exact)."""
+    return tol_any_axis(nx) + (tol_any_axis(ny) if ny > 1 else 0.0)

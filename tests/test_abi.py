@@ -55,19 +55,22 @@ def test_error_strings(lib):
     assert b"timed out" in lib.fft_error_string(-6)
 
 
-@pytest.mark.parametrize("nx,ny,batch", [(3, 4, 1), (4, 6, 1), (0, 8, 1), (8, 8, 0),
+@pytest.mark.parametrize("nx,ny,batch", [(0, 3, 1), (3, 0, 1), (0, 8, 1), (8, 8, 0),
                                          (16384, 2, 1), (2, 16384, 1), (-4, 4, 1),
-                                         (1 << 27, 1, 1), (1, 1 << 27, 1), (3 << 14, 1, 1),
-                                         (1 << 26, 1, 64)])
+                                         (1 << 27, 1, 1), (1, 1 << 27, 1), (3 << 23, 1, 1),
+                                         (70000, 3, 1), (1 << 26, 1, 64)])
 def test_invalid_sizes_rejected_without_touching_the_gpu(lib, nx, ny, batch):
     assert lib.fft_plan_create(nx, ny, batch, -1, 0) is None
     assert lib.fft_last_error() == -1
 
 
-def test_long_1d_is_fp32_only(lib):
-    # the four-step path (1D lengths above 8192) has no split-FP16 form; the
-    # request is refused before any device call
+def test_long_1d_and_any_size_are_fp32_only(lib):
+    # the four-step path (1D lengths above 8192) and sizes that are not
+    # powers of two (Bluestein) have no split-FP16 form; the request is
+    # refused before any device call
     assert lib.fft_plan_create(1 << 16, 1, 1, -1, 1) is None
+    assert lib.fft_last_error() == -5
+    assert lib.fft_plan_create(1000, 3, 1, -1, 1) is None
     assert lib.fft_last_error() == -5
 
 
