@@ -302,6 +302,7 @@ def forms(torch, g, steps, warmup, dev):
                                  "HBM_GB/s_algorithmic": 16.0 * 4096 * 16384 / ms / 1e6}
     del x, y
     out.update(fourstep_form(torch, g, steps, dev))
+    out.update(any_size_form(torch, g, steps, dev))
     out.update(energy_form(torch, g, dev))
     out.update(ragged_form(torch, g, steps, dev))
     out.update(diff_form(torch, g, steps, dev))
@@ -331,6 +332,28 @@ def energy_form(torch, g, dev):
         return out
     except (NVMLError, AttributeError) as e:
         return {"energy": {"unavailable": str(e)}}
+
+
+def any_size_form(torch, g, steps, dev):
+    """Sizes that are not powers of two (Bluestein over the power-of-two
+    path): 1000 x 1000 (beside the paper's 1024 x 1024), 10^6 points in 1D,
+    and 16384 signals of 4095 points.  GFLOP/s uses the nominal 5 N log2 N
+    of the transform's own size."""
+    import math
+    import synth
+    out = {}
+    for nx, ny, b in ((1000, 1000, 1), (1_000_000, 1, 1), (4095, 1, 16384)):
+        x = torch.from_numpy(synth.uniform_complex((b, ny, nx), seed=SEED)).to(dev)
+        y = torch.empty_like(x)
+        plan = g.get_plan(nx, ny, b, False, "fp32", dev)
+        ms, _ = time_plan(torch, plan, x, y, max(10, steps // 4), 3)
+        n = nx * ny
+        d = plan.describe()
+        out[f"fp32_any_{nx}x{ny}x{b}"] = {
+            "ms": ms, "GFLOP/s_nominal": 5.0 * n * math.log2(n) * b / ms / 1e6,
+            "bluestein_m": [d["x"]["bluestein_m"], d["y"]["bluestein_m"]], "transposes": d["transposes"]}
+        del x, y
+    return out
 
 
 def fourstep_form(torch, g, steps, dev):
