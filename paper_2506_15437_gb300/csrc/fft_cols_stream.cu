@@ -25,7 +25,9 @@
 //
 // Rows of a block are P apart (the row pass's column pre-split) and the
 // output goes to the same rows it came from in natural order, so the pass is
-// in place on the intermediate.
+// in place on the intermediate; or (planar) the row pass wrote each block as
+// a plane of its own in a workspace, read here through a P = 1 map, and the
+// output goes to the interleaved rows of the destination.
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -58,7 +60,7 @@ struct StreamShape {
 template <int N, int E, int W, int S>
 __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
     k_cols_stream(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw, int nx,
-                  int batch, int P, int conj_out, int *status) {
+                  int batch, int P, int conj_out, int *status, int planar) {
     using Sh = StreamShape<N, E, W, S>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
@@ -92,8 +94,10 @@ __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
     auto issue = [&](long long m, int w) {
         const long long id = blockIdx.x + m * (long long)gridDim.x;
         const int x = (int)(id % groups_x) * 2 * W;
-        const int kp = (int)((id / groups_x) % P);
-        const int z0 = (int)((id / groups_x) / P) * N + w * Sh::SEG_ROWS;
+        // block b*P + kp: rows kp + P*i of slice b (map over the output), or
+        // planar, rows (b*P + kp)*N + i of a workspace whose map has P = 1
+        const int kp = planar ? 0 : (int)((id / groups_x) % P);
+        const int z0 = (int)(planar ? (id / groups_x) : (id / groups_x) / P) * N + w * Sh::SEG_ROWS;
         float2 *dst = seg_buf(w);
         mbar_expect_tx(full + w, Sh::SEG_BYTES);
 #pragma unroll
@@ -218,12 +222,12 @@ const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g) {
 }
 
 cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw, int nx,
-                               int batch, int split, int conj_out, int *status, int grid, cudaStream_t s) {
+                               int batch, int split, int conj_out, int *status, int grid, int planar, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     if (e != cudaSuccess) return e;
     CUtensorMap m = map;
-    void *args[] = {(void *)&m,     (void *)&out,      (void *)&tw,     (void *)&nx,
-                    (void *)&batch, (void *)&split,    (void *)&conj_out, (void *)&status};
+    void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&nx,     (void *)&batch,
+                    (void *)&split, (void *)&conj_out, (void *)&status, (void *)&planar};
     return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 

@@ -55,7 +55,7 @@ cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s);
 cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw,
                         const float2 *twp, long long nrows, int ny, int split, int conj_in,
                         int conj_out, const float *weight, float wscale, int grid, int pf_dist,
-                        int perm_t, int perm_g, cudaStream_t s);
+                        int perm_t, int perm_g, int planar, cudaStream_t s);
 int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, int split, bool persistent);
 // Long-row pass with a TMA landing ring (fft_rows_ring.cu), n in 2048..8192.
 bool ring_rows_available(int n);
@@ -121,7 +121,7 @@ cudaError_t build_roots_strided(float2 *t, int count, long long n, long long str
 // apply (perm_t = stage-0 butterflies T, perm_g = butterflies per warp G).
 const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g);
 cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw, int nx,
-                               int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+                               int batch, int split, int conj_out, int *status, int grid, int planar, cudaStream_t s);
 
 // Reorder-map debug launchers: write map[i] = output position of input i.
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s);
@@ -150,6 +150,7 @@ struct Schedule {
     int col_c = 2;         // cluster size of the DSMEM column kernel
     int col_pf = 0;        // TMA column pass: L2 prefetch distance (tiles)
     int col_stream = 1;    // out-of-place calls: streaming column pass over row-permuted rows, where compiled
+    int planar = 1;        // pre-split plans with the streaming pass: blocks as planes of a workspace
 };
 
 // One axis of a dense plan: a row-pass length (contiguous) or a column-pass
@@ -234,6 +235,11 @@ struct fft_plan_s {
     gb300fft::AxisPlan cols_split;  // length ny / split, for out-of-place calls when split > 1
     gb300fft::FourStepPlan fs;      // large 1D plans (n > 8192)
     gb300fft::AnyPlan *any = nullptr;  // sizes that are not all powers of two
+    // pre-split plans: the row pass writes each column block as a plane of
+    // this workspace (batch*ny*nx), read by the streaming column pass through
+    // planar_map; any call, in place or not, then runs the split path
+    float2 *planar_work = nullptr;
+    CUtensorMap planar_map;
     int split = 1;        // column pre-split P done by the row pass (out of place only)
     float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
     int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]

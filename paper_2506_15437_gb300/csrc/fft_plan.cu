@@ -92,6 +92,7 @@ void apply_env_overrides(Schedule *sc) {
     geti("GB300FFT_COL_W", &sc->col_w);
     geti("GB300FFT_COL_PF", &sc->col_pf);
     geti("GB300FFT_COL_STREAM", &sc->col_stream);
+    geti("GB300FFT_PLANAR", &sc->planar);
     if (const char *ev = getenv("GB300FFT_COL_CLUSTER")) {
         const int c = atoi(ev);
         if (c == 2 || c == 4) {
@@ -153,6 +154,7 @@ bool tune_cache_lookup(int nx, int ny, int batch, int prec, Schedule *sc) {
         sc->col_w = json_int(l, "col_w", sc->col_w);
         sc->col_c = json_int(l, "col_c", sc->col_c);
         sc->col_stream = json_int(l, "col_stream", sc->col_stream);
+        sc->planar = json_int(l, "planar", sc->planar);
         found = true;  // the last matching line wins
     }
     fclose(f);
@@ -172,9 +174,10 @@ void tune_cache_store(int nx, int ny, int batch, int prec, const Schedule &sc, f
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"row_e\": %d, \"row_persist\": %d, \"row_pf\": %d, \"split\": %d, "
-            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"ms\": %.5f}\n",
+            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"planar\": %d, "
+            "\"ms\": %.5f}\n",
             tune_key(nx, ny, batch, prec).c_str(), sc.row_e, sc.row_persist, sc.row_pf, sc.split, sc.col_kind,
-            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, ms);
+            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, sc.planar, ms);
     fclose(f);
 }
 
@@ -387,6 +390,16 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
                 else if (build_roots(p->twp, ny, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
             }
             if (rc == FFT_OK) p->split = split;
+            // planar blocks in a workspace for the streaming column pass (FP32)
+            const AxisPlan &cs = p->cols_split;
+            if (rc == FFT_OK && sc.planar && precision == FFT_PREC_FP32 && cs.stream && cs.cl_c == 0 &&
+                cs.pair_e == 0 && !p->ring) {
+                p->planar_work = dev_alloc<float2>(p, (size_t)nx * ny * batch);
+                if (!p->planar_work) rc = FFT_ERR_ALLOC;
+                else if (encode_col_map(&p->planar_map, p->planar_work, nx, (long long)ny * batch, 1, cs.stream->w,
+                                        cs.stream->box_rows) != 0)
+                    rc = FFT_ERR_CUDA;
+            }
         }
     }
     if (rc == FFT_OK) {
@@ -592,8 +605,10 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         return FFT_OK;
     }
     const bool two_pass = p->cols.col != nullptr;
-    // the pre-split pairs rows across CTAs, so an in-place call must not use it
-    const int P = (two_pass && src != dst) ? p->split : 1;
+    // the pre-split pairs rows across CTAs, so an in-place call must not use
+    // it -- unless the blocks go through the planar workspace
+    const bool planar = two_pass && p->planar_work != nullptr && p->prec == FFT_PREC_FP32;
+    const int P = (two_pass && (src != dst || planar)) ? p->split : 1;
     AxisPlan &cp = (P > 1) ? p->cols_split : p->cols;
     const long long nrows = total / p->rows.n;
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
@@ -620,7 +635,9 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     // out of place: the row pass may store its rows permuted for the
     // streaming column pass (in place it must not: rows would overwrite rows
     // other CTAs have yet to read)
-    const bool stream = two_pass && src != dst && cp.stream && !p->ring && cp.cl_c == 0 && cp.pair_e == 0;
+    const bool stream =
+        planar || (two_pass && src != dst && cp.stream && !p->ring && cp.cl_c == 0 && cp.pair_e == 0);
+    float2 *row_dst = planar ? p->planar_work : dst;
     int &grid = p->row_grid[weight ? 1 : 0][P > 1 ? 1 : 0];
     if (grid == 0)
         grid = p->ring ? ring_rows_grid(p->rows.n, nrows, P, p->num_sms, weight != nullptr)
@@ -630,9 +647,9 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     const cudaError_t er =
         p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                                    (inv && !two_pass) ? 1 : 0, weight, wscale, p->status, grid, s)
-                : launch_rows(*p->rows.row, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
+                : launch_rows(*p->rows.row, src, row_dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                               (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, stream ? cp.perm_t : 0,
-                              stream ? cp.perm_g : 0, s);
+                              stream ? cp.perm_g : 0, planar ? 1 : 0, s);
     if (er != cudaSuccess) return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
     if (!two_pass) {
@@ -659,14 +676,14 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
-    if (cp.map_base != out) {
+    if (!planar && cp.map_base != out) {
         if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.col->w, cp.col->box_rows) != 0)
             return FFT_ERR_CUDA;
         cp.map_base = out;
     }
     const cudaError_t ec =
-        stream ? launch_cols_stream(*cp.stream, cp.map, dst, cp.stream_tw, p->nx, p->batch, P, inv ? 1 : 0, p->status,
-                                    cp.stream_grid, s)
+        stream ? launch_cols_stream(*cp.stream, planar ? p->planar_map : cp.map, dst, cp.stream_tw, p->nx, p->batch, P,
+                                    inv ? 1 : 0, p->status, cp.stream_grid, planar ? 1 : 0, s)
                : launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid,
                              p->col_pf, s);
     if (ec != cudaSuccess) return FFT_ERR_CUDA;
@@ -867,6 +884,11 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                     Schedule d = c;
                     d.col_stream = 0;
                     cands.push_back(d);
+                    if (split == 2) {
+                        Schedule e = c;
+                        e.planar = 0;
+                        cands.push_back(e);
+                    }
                 }
                 for (int ce : {16, 64}) {
                     if (!col_variant(ilog2(cn), ce, default_col_w(cn, p->nx)) || ce == preferred_col_e(cn, default_col_w(cn, p->nx)))

@@ -50,7 +50,7 @@ template <int N, int E, bool WEIGHTED, int P>
 __global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
     k_rows(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
            const float2 *__restrict__ twp, long long nrows, int ny, int conj_in, int conj_out,
-           const float *__restrict__ weight, float wscale, int pf_dist, int perm_t, int perm_g) {
+           const float *__restrict__ weight, float wscale, int pf_dist, int perm_t, int perm_g, int planar) {
     using Sh = RowShape<N, E>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
@@ -152,15 +152,20 @@ __global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
             }
         }
         long long orow = row;
-        if (perm_t) {
-            // streaming column pass: column-block element i = j + r*perm_t
-            // goes to block row (j / G)*G*R0 + r*G + j % G (G = perm_g)
+        if (perm_t || planar) {
+            // column block kq, element i: with perm_t (streaming column pass)
+            // at block row (j / G)*G*R0 + r*G + j % G for i = j + r*perm_t
+            // (G = perm_g), else at block row i; the block's rows are P apart
+            // (kq + P*row) or, planar, a plane of its own (kq*Q + row)
             const long long bb = row / ny;
             const int y = (int)(row - bb * ny);
             const int i = y / P, kq = y - (y / P) * P;
-            const int j = i & (perm_t - 1), r = i / perm_t;
-            const int si = (j / perm_g) * perm_g * (Q / perm_t) + r * perm_g + (j & (perm_g - 1));
-            orow = bb * ny + kq + (long long)P * si;
+            int pos = i;
+            if (perm_t) {
+                const int j = i & (perm_t - 1), r = i / perm_t;
+                pos = (j / perm_g) * perm_g * (Q / perm_t) + r * perm_g + (j & (perm_g - 1));
+            }
+            orow = bb * ny + (planar ? (long long)kq * Q + pos : kq + (long long)P * pos);
         }
         float2 *dst = out + orow * N;
         auto store = [&](int i, int, float2 x) {
@@ -314,7 +319,7 @@ int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, i
 
 cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                         long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
-                        float wscale, int grid, int pf_dist, int perm_t, int perm_g, cudaStream_t s) {
+                        float wscale, int grid, int pf_dist, int perm_t, int perm_g, int planar, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
     if (split != 1 && split != 2) return cudaErrorInvalidValue;
     const void *fn = row_fn(v, weight != nullptr, split);
@@ -329,7 +334,7 @@ cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, cons
         return cudaErrorInvalidValue;
     void *args[] = {(void *)&in,      (void *)&out,     (void *)&tw,       (void *)&twp,    (void *)&nrows,
                     (void *)&ny,      (void *)&conj_in, (void *)&conj_out, (void *)&weight, (void *)&wscale,
-                    (void *)&pf_dist, (void *)&perm_t,  (void *)&perm_g};
+                    (void *)&pf_dist, (void *)&perm_t,  (void *)&perm_g,   (void *)&planar};
     return cudaLaunchKernel(fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 
