@@ -115,6 +115,13 @@ cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2
 // t[k] = exp(-2*pi*i*(k*stride mod n)/n), k < count, built in FP64.
 cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s);
 
+// Pre-split row pass from a landed pair of rows (fft_rows_land.cu): one CTA
+// per pair q, both output rows kp = 0, 1, stored like launch_rows stores them.
+bool land_rows_available(int n, int e);
+cudaError_t launch_rows_land(const float2 *in, float2 *out, const float2 *tw, const float2 *twp, int ny, int batch,
+                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms,
+                             cudaStream_t s);
+
 // Streaming column pass (fft_cols_stream.cu) over a row-permuted
 // intermediate: the variant for column length n and row length nx, or
 // nullptr; *perm_t / *perm_g receive the row permutation launch_rows must
@@ -151,6 +158,7 @@ struct Schedule {
     int col_pf = 0;        // TMA column pass: L2 prefetch distance (tiles)
     int col_stream = 1;    // out-of-place calls: streaming column pass over row-permuted rows, where compiled
     int planar = 1;        // pre-split plans with the streaming pass: blocks as planes of a workspace
+    int row_land = 1;      // pre-split 8192-point rows: one CTA per landed pair of input rows
 };
 
 // One axis of a dense plan: a row-pass length (contiguous) or a column-pass

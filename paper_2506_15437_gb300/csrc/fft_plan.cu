@@ -93,6 +93,7 @@ void apply_env_overrides(Schedule *sc) {
     geti("GB300FFT_COL_PF", &sc->col_pf);
     geti("GB300FFT_COL_STREAM", &sc->col_stream);
     geti("GB300FFT_PLANAR", &sc->planar);
+    geti("GB300FFT_ROW_LAND", &sc->row_land);
     if (const char *ev = getenv("GB300FFT_COL_CLUSTER")) {
         const int c = atoi(ev);
         if (c == 2 || c == 4) {
@@ -155,6 +156,7 @@ bool tune_cache_lookup(int nx, int ny, int batch, int prec, Schedule *sc) {
         sc->col_c = json_int(l, "col_c", sc->col_c);
         sc->col_stream = json_int(l, "col_stream", sc->col_stream);
         sc->planar = json_int(l, "planar", sc->planar);
+        sc->row_land = json_int(l, "row_land", sc->row_land);
         found = true;  // the last matching line wins
     }
     fclose(f);
@@ -175,9 +177,9 @@ void tune_cache_store(int nx, int ny, int batch, int prec, const Schedule &sc, f
     fprintf(f,
             "{\"key\": \"%s\", \"row_e\": %d, \"row_persist\": %d, \"row_pf\": %d, \"split\": %d, "
             "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"planar\": %d, "
-            "\"ms\": %.5f}\n",
+            "\"row_land\": %d, \"ms\": %.5f}\n",
             tune_key(nx, ny, batch, prec).c_str(), sc.row_e, sc.row_persist, sc.row_pf, sc.split, sc.col_kind,
-            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, sc.planar, ms);
+            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, sc.planar, sc.row_land, ms);
     fclose(f);
 }
 
@@ -644,8 +646,13 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                        : row_grid(*p->rows.row, nrows, p->num_sms, weight != nullptr, P,
                                   p->row_persist < 0 ? P > 1 : p->row_persist != 0);
     if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    const bool land = P == 2 && !weight && !p->ring && p->sched.row_land &&
+                      land_rows_available(p->rows.n, p->rows.row->e);
     const cudaError_t er =
-        p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
+        land ? launch_rows_land(src, row_dst, p->rows.tw, p->twp, p->ny, p->batch, inv ? 1 : 0,
+                                stream ? cp.perm_t : 0, stream ? cp.perm_g : 0, planar ? 1 : 0, p->status,
+                                p->num_sms, s)
+        : p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                                    (inv && !two_pass) ? 1 : 0, weight, wscale, p->status, grid, s)
                 : launch_rows(*p->rows.row, src, row_dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                               (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, stream ? cp.perm_t : 0,
@@ -888,6 +895,9 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                         Schedule e = c;
                         e.planar = 0;
                         cands.push_back(e);
+                        Schedule f = c;
+                        f.row_land = 0;
+                        cands.push_back(f);
                     }
                 }
                 for (int ce : {16, 64}) {
@@ -1000,7 +1010,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
                      "\"grid\": %d}, \"split\": %d}",
-                     tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : "k_rows"), p->rows.n, re,
+                     tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
                      !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
                      cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,

@@ -319,14 +319,20 @@ def test_column_pass_elements_per_thread(g, monkeypatch, e, ny, nx, batch, inver
 @pytest.mark.parametrize("inverse", [False, True])
 def test_streaming_column_pass_is_bit_identical(g, monkeypatch, ny, nx, batch, inverse):
     """The streaming column pass (row pass storing rows permuted, segments
-    landing per warp) runs the same butterflies in the same order as the
-    plain TMA column pass, so out-of-place results agree bit for bit; both
-    meet the oracle bound."""
+    landing per warp) and the landed-pair row pass run the same operations in
+    the same order as the plain row and column passes, so results agree bit
+    for bit; both meet the oracle bound."""
     monkeypatch.setenv("GB300FFT_COL_STREAM", "1")
+    monkeypatch.setenv("GB300FFT_ROW_LAND", "1")
     ps = g.Plan(nx, ny, batch, inverse=inverse)
     monkeypatch.setenv("GB300FFT_COL_STREAM", "0")
+    monkeypatch.setenv("GB300FFT_ROW_LAND", "0")
     pp = g.Plan(nx, ny, batch, inverse=inverse)
     monkeypatch.delenv("GB300FFT_COL_STREAM")
+    monkeypatch.delenv("GB300FFT_ROW_LAND")
+    if ny >= 8192 and nx == 8192:  # the landed-pair kernel serves 8192-point rows
+        assert ps.describe()["rows"]["kernel"].startswith("k_rows_land<")
+        assert pp.describe()["rows"]["kernel"].startswith("k_rows<")
     assert ps.describe()["cols"]["kernel"].startswith("k_cols_stream<")
     assert pp.describe()["cols"]["kernel"].startswith("k_cols<")
     x = synth.uniform_complex((batch, ny, nx), seed=7 * ny + nx)
