@@ -95,6 +95,26 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision);
 int fft_execute(fft_plan_t p, const void *in, void *out, void *stream);
 
 /*
+ * fft_execute_host -- fft_execute from and to host memory: host_in is copied
+ * to a plan-owned device buffer, transformed, and the result copied back to
+ * host_out.  Work issued on `stream` after this call sees host_out complete
+ * (the stream waits for the device-to-host copy).  The copies run on the
+ * plan's own copy streams through two staging buffers per direction, so
+ * successive calls pipeline: a call's host-to-device copy starts at once and
+ * overlaps the previous call's device-to-host copy (the host link carries
+ * both directions at the same time).  Hence host_in is read from the moment
+ * of the call on and must already hold the input then: it may not be the
+ * output of earlier work on `stream`.
+ *   host_in, host_out  batch*ny*nx complex64 each; page-locked memory
+ *                      (cudaHostAlloc, or torch's pin_memory) keeps the
+ *                      copies asynchronous.  They may not overlap.
+ * The first call allocates the staging buffers (four times the transform's
+ * size) and the copy streams; later calls allocate nothing.  Not for ragged
+ * plans (FFT_ERR_INVALID_ARG).
+ */
+int fft_execute_host(fft_plan_t p, const void *host_in, void *host_out, void *stream);
+
+/*
  * fft_backward -- the adjoint (conjugate transpose) of the plan's transform:
  * grad_in = F^H grad_out, i.e. the unnormalised transform with the opposite
  * exponent sign.  This is the vector-Jacobian product of fft_execute for a

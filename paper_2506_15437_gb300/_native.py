@@ -32,6 +32,7 @@ _LL = ctypes.c_longlong
 SIGNATURES = [
     ("fft_plan_create", _P, [_I, _I, _I, _I, _I]),
     ("fft_execute", _I, [_P, _P, _P, _P]),
+    ("fft_execute_host", _I, [_P, _P, _P, _P]),
     ("fft_backward", _I, [_P, _P, _P, _P]),
     ("fft_backward_weighted", _I, [_P, _P, _P, _F, _P, _P]),
     ("fft_weighted_power", _I, [_P, _P, _P, _P, _P]),

@@ -226,6 +226,17 @@ cudaError_t launch_blu_post(const float2 *A, float2 *out, const float2 *c, int n
                             cudaStream_t s);
 cudaError_t launch_transpose(const float2 *in, float2 *out, int rows, int cols, long long batch, cudaStream_t s);
 
+// Host-buffer execution (fft_execute_host): two staging buffers per
+// direction, one copy stream per direction, events linking them to the
+// caller's stream.
+struct HostStage {
+    float2 *din[2] = {nullptr, nullptr}, *dout[2] = {nullptr, nullptr};
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, computed[2] = {nullptr, nullptr},
+                out_done[2] = {nullptr, nullptr};
+    unsigned long long calls = 0;
+};
+
 struct RaggedState;
 void ragged_destroy(RaggedState *r);
 
@@ -248,6 +259,7 @@ struct fft_plan_s {
     // planar_map; any call, in place or not, then runs the split path
     float2 *planar_work = nullptr;
     CUtensorMap planar_map;
+    gb300fft::HostStage *host = nullptr;  // fft_execute_host staging (first use)
     int split = 1;        // column pre-split P done by the row pass (out of place only)
     float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
     int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]

@@ -524,6 +524,17 @@ namespace gb300fft {
 void free_plan(fft_plan_s *p) {
     if (!p) return;
     if (p->ragged) ragged_destroy(p->ragged);
+    if (p->host) {
+        HostStage &h = *p->host;
+        for (int i = 0; i < 2; ++i) {
+            if (h.in_ready[i]) cudaEventDestroy(h.in_ready[i]);
+            if (h.computed[i]) cudaEventDestroy(h.computed[i]);
+            if (h.out_done[i]) cudaEventDestroy(h.out_done[i]);
+        }
+        if (h.cin) cudaStreamDestroy(h.cin);
+        if (h.cout) cudaStreamDestroy(h.cout);
+        delete p->host;  // the staging buffers are in p->allocations
+    }
     if (p->any) {
         free_plan(p->any->x.sub);
         free_plan(p->any->y.sub);
@@ -793,6 +804,53 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
 int fft_execute(fft_plan_t p, const void *in, void *out, void *stream) {
     if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
     return run_dense(p, in, out, p->dir, nullptr, 1.f, static_cast<cudaStream_t>(stream));
+}
+
+int fft_execute_host(fft_plan_t p, const void *host_in, void *host_out, void *stream) {
+    if (!p || p->kind != 0 || !host_in || !host_out || host_in == host_out) return FFT_ERR_INVALID_ARG;
+    cudaSetDevice(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)p->nx * p->ny * p->batch * sizeof(float2);
+    if (!p->host) {
+        HostStage *h = new (std::nothrow) HostStage();
+        if (!h) return FFT_ERR_ALLOC;
+        p->host = h;
+        const size_t count = bytes / sizeof(float2);
+        for (int i = 0; i < 2; ++i) {
+            h->din[i] = dev_alloc<float2>(p, count);
+            h->dout[i] = dev_alloc<float2>(p, count);
+            if (!h->din[i] || !h->dout[i]) return FFT_ERR_ALLOC;
+            if (cudaEventCreateWithFlags(&h->in_ready[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->computed[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->out_done[i], cudaEventDisableTiming) != cudaSuccess)
+                return FFT_ERR_CUDA;
+        }
+        if (cudaStreamCreateWithFlags(&h->cin, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->cout, cudaStreamNonBlocking) != cudaSuccess)
+            return FFT_ERR_CUDA;
+    }
+    HostStage &h = *p->host;
+    const int i = (int)(h.calls & 1);
+    // input staging buffer i is free once the transform of two calls ago ran
+    if (cudaStreamWaitEvent(h.cin, h.computed[i], 0) != cudaSuccess ||
+        cudaMemcpyAsync(h.din[i], host_in, bytes, cudaMemcpyHostToDevice, h.cin) != cudaSuccess ||
+        cudaEventRecord(h.in_ready[i], h.cin) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    // the transform: after its input arrived and after the copy-out of two
+    // calls ago left output staging buffer i
+    if (cudaStreamWaitEvent(s, h.in_ready[i], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h.out_done[i], 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    const int rc = run_dense(p, h.din[i], h.dout[i], p->dir, nullptr, 1.f, s);
+    if (rc != FFT_OK) return rc;
+    if (cudaEventRecord(h.computed[i], s) != cudaSuccess ||
+        cudaStreamWaitEvent(h.cout, h.computed[i], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_out, h.dout[i], bytes, cudaMemcpyDeviceToHost, h.cout) != cudaSuccess ||
+        cudaEventRecord(h.out_done[i], h.cout) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h.out_done[i], 0) != cudaSuccess)  // the caller's stream sees host_out
+        return FFT_ERR_CUDA;
+    h.calls += 1;
+    return FFT_OK;
 }
 
 int fft_backward(fft_plan_t p, const void *grad_out, void *grad_in, void *stream) {

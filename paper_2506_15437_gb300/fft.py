@@ -68,6 +68,25 @@ class Plan:
                                       _stream_handle(x.device)), "fft_execute")
         return out
 
+    def execute_host(self, x: torch.Tensor, out: torch.Tensor | None = None, device=None) -> torch.Tensor:
+        """The transform of a host (CPU) complex64 tensor into a host tensor,
+        through the plan's device staging buffers (fft_execute_host).  Pinned
+        tensors keep the copies asynchronous; successive calls overlap one
+        call's upload with the previous call's download.  Ordered on the
+        current stream of `device` (default: the current CUDA device)."""
+        if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.complex64 or not x.is_contiguous():
+            raise ValueError("execute_host takes a contiguous complex64 CPU tensor")
+        if x.numel() != self.numel:
+            raise ValueError(f"input has {x.numel()} elements, plan expects {self.numel}")
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        elif out.is_cuda or out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != self.numel:
+            raise ValueError("out must be a contiguous complex64 CPU tensor of the plan's size")
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        N.check(self._lib.fft_execute_host(self._p, x.data_ptr(), out.data_ptr(), _stream_handle(dev)),
+                "fft_execute_host")
+        return out
+
     def backward(self, g: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         out = self._io(g, out)
         N.check(self._lib.fft_backward(self._p, g.data_ptr(), out.data_ptr(),
