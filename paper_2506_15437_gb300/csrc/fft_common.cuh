@@ -202,7 +202,7 @@ struct SyncWarp {
 // SRC_IN_SMEM: stage-0 inputs were read from `sm` itself, so the first
 // shared-memory write must wait for every thread's reads.
 // ---------------------------------------------------------------------------
-template <int N, int E, int W, int PADSH>
+template <int N, int E, int W, int PADSH, int PADSH1 = PADSH>
 struct Engine {
     using Sc = Sched<N, E>;
     static constexpr int T = N / E;   // threads per column
@@ -210,8 +210,12 @@ struct Engine {
     static constexpr int R0 = Sc::R0;
     static constexpr int S = Sc::S;
     static constexpr int RL = (S == 1) ? R0 : E;  // radix of the last stage
+    // padded index of the exchange after stage s - 1: the first exchange may
+    // use its own shift (PADSH1), since its write pattern follows radix R0
     __host__ __device__ static constexpr int pad(int f) { return f + (f >> PADSH); }
-    static constexpr int SMEM_ELEMS = (S > 1) ? pad(N * W - 1) + 1 : 0;
+    __host__ __device__ static constexpr int pad_s(int f, int s) { return f + (f >> (s == 1 ? PADSH1 : PADSH)); }
+    static constexpr int SMEM_ELEMS =
+        (S > 1) ? (pad_s(N * W - 1, 1) > pad(N * W - 1) ? pad_s(N * W - 1, 1) : pad(N * W - 1)) + 1 : 0;
 
     template <class Pol, bool SRC_IN_SMEM, class Sync, class AfterReads, class Store>
     __device__ static __forceinline__ void run(typename Pol::T (&v)[E], typename Pol::T *sm,
@@ -242,13 +246,13 @@ struct Engine {
                     const int j = tt + b * T;
                     const int m = j & (Nsp - 1);
 #pragma unroll
-                    for (int k = 0; k < Rp; ++k) sm[pad(((j - m) * Rp + m + k * Nsp) * W + c)] = v[b * Rp + k];
+                    for (int k = 0; k < Rp; ++k) sm[pad_s(((j - m) * Rp + m + k * Nsp) * W + c, s)] = v[b * Rp + k];
                 }
                 sync();
                 const int Ns = Sc::ns(s);
                 const int m = tt & (Ns - 1);
 #pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = sm[pad((tt + r * T) * W + c)];
+                for (int r = 0; r < E; ++r) v[r] = sm[pad_s((tt + r * T) * W + c, s)];
                 if (s == S - 1) after_reads();
                 if constexpr (Pol::kUsesTwiddles) {
                     // twiddles r = 2k+1, 2k+2 of this butterfly in one 16-byte load
@@ -279,6 +283,14 @@ struct Engine {
 template <int E>
 struct PadShift {
     static constexpr int value = (E >= 64) ? 6 : (E >= 32) ? 5 : 4;
+};
+// First-exchange shift of the one-row engines (W = 1): with E = 32 the write
+// after the radix-4/8 first stage puts 16 lanes 8 or 4 float2 apart, which
+// a shift of 4 spreads over all banks (half-warp bank model; shift 5 leaves
+// 2-way conflicts there).
+template <int E>
+struct RowPadShift1 {
+    static constexpr int value = (E == 32) ? 4 : PadShift<E>::value;
 };
 
 // ---------------------------------------------------------------------------

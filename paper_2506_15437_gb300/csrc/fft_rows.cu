@@ -28,7 +28,7 @@ struct RowShape {
     // for 512-thread CTAs with E <= 16, at most 85 for 256-thread ones
     static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS
                                                : (THREADS >= 256 ? (E < 32 ? 3 : ROWMINB32) : 1);
-    using Eng = Engine<N, E, 1, PadShift<E>::value>;
+    using Eng = Engine<N, E, 1, PadShift<E>::value, RowPadShift1<E>::value>;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
 };
 
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
 // identity butterflies, identical addresses.  map[tag] = final position.
 template <int N, int E>
 __global__ void __launch_bounds__(N / E) k_rows_movemap(int *map) {
-    using Eng = Engine<N, E, 1, PadShift<E>::value>;
+    using Eng = Engine<N, E, 1, PadShift<E>::value, RowPadShift1<E>::value>;
     constexpr int T = N / E;
     constexpr int R0 = Eng::R0;
     extern __shared__ __align__(16) float2 smem[];

@@ -22,7 +22,7 @@ template <int N, int E>
 struct LandShape {
     static constexpr int T = N / E;        // threads per output row
     static constexpr int THREADS = 2 * T;  // one half per output row kp
-    using Eng = Engine<N, E, 1, PadShift<E>::value>;
+    using Eng = Engine<N, E, 1, PadShift<E>::value, RowPadShift1<E>::value>;
     static constexpr size_t LAND_BYTES = 2 * (size_t)N * sizeof(float2);
     static constexpr size_t XBYTES = 2 * (size_t)Eng::SMEM_ELEMS * sizeof(float2);
     static constexpr size_t BUF = XBYTES > LAND_BYTES ? XBYTES : LAND_BYTES;
