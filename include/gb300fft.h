@@ -99,12 +99,15 @@ int fft_execute(fft_plan_t p, const void *in, void *out, void *stream);
  * to a plan-owned device buffer, transformed, and the result copied back to
  * host_out.  Work issued on `stream` after this call sees host_out complete
  * (the stream waits for the device-to-host copy).  The copies run on the
- * plan's own copy streams through two staging buffers per direction, so
- * successive calls pipeline: a call's host-to-device copy starts at once and
- * overlaps the previous call's device-to-host copy (the host link carries
- * both directions at the same time).  Hence host_in is read from the moment
- * of the call on and must already hold the input then: it may not be the
- * output of earlier work on `stream`.
+ * plan's own copy streams through two staging buffers per direction and the
+ * transform on the plan's own compute stream, so successive calls pipeline:
+ * a call's host-to-device copy starts at once and overlaps the previous
+ * call's device-to-host copy (the host link carries both directions at the
+ * same time), and its transform overlaps that copy too.  Hence host_in is
+ * read from the moment of the call on and must already hold the input then:
+ * it may not be the output of earlier work on `stream`.  The plan's shared
+ * workspaces stay ordered: after fft_execute / fft_backward on `stream` the
+ * next host call's transform waits for that work.
  *   host_in, host_out  batch*ny*nx complex64 each; page-locked memory
  *                      (cudaHostAlloc, or torch's pin_memory) keeps the
  *                      copies asynchronous.  They may not overlap.

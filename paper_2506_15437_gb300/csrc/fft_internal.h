@@ -231,9 +231,9 @@ cudaError_t launch_transpose(const float2 *in, float2 *out, int rows, int cols, 
 // caller's stream.
 struct HostStage {
     float2 *din[2] = {nullptr, nullptr}, *dout[2] = {nullptr, nullptr};
-    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaStream_t cin = nullptr, cout = nullptr, comp = nullptr;
     cudaEvent_t in_ready[2] = {nullptr, nullptr}, computed[2] = {nullptr, nullptr},
-                out_done[2] = {nullptr, nullptr};
+                out_done[2] = {nullptr, nullptr}, entry = nullptr;
     unsigned long long calls = 0;
 };
 
@@ -260,6 +260,7 @@ struct fft_plan_s {
     float2 *planar_work = nullptr;
     CUtensorMap planar_map;
     gb300fft::HostStage *host = nullptr;  // fft_execute_host staging (first use)
+    bool last_use_host = false;           // the plan's latest work was an fft_execute_host call
     int split = 1;        // column pre-split P done by the row pass (out of place only)
     float2 *twp = nullptr;  // exp(-2*pi*i*k/ny), k < ny: the pre-split twiddles
     int row_grid[2][2] = {{0, 0}, {0, 0}};  // persistent row grid [weighted][split > 1]

@@ -531,8 +531,10 @@ void free_plan(fft_plan_s *p) {
             if (h.computed[i]) cudaEventDestroy(h.computed[i]);
             if (h.out_done[i]) cudaEventDestroy(h.out_done[i]);
         }
+        if (h.entry) cudaEventDestroy(h.entry);
         if (h.cin) cudaStreamDestroy(h.cin);
         if (h.cout) cudaStreamDestroy(h.cout);
+        if (h.comp) cudaStreamDestroy(h.comp);
         delete p->host;  // the staging buffers are in p->allocations
     }
     if (p->any) {
@@ -803,6 +805,7 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
 
 int fft_execute(fft_plan_t p, const void *in, void *out, void *stream) {
     if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
+    p->last_use_host = false;
     return run_dense(p, in, out, p->dir, nullptr, 1.f, static_cast<cudaStream_t>(stream));
 }
 
@@ -826,7 +829,9 @@ int fft_execute_host(fft_plan_t p, const void *host_in, void *host_out, void *st
                 return FFT_ERR_CUDA;
         }
         if (cudaStreamCreateWithFlags(&h->cin, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&h->cout, cudaStreamNonBlocking) != cudaSuccess)
+            cudaStreamCreateWithFlags(&h->cout, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->comp, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->entry, cudaEventDisableTiming) != cudaSuccess)
             return FFT_ERR_CUDA;
     }
     HostStage &h = *p->host;
@@ -836,14 +841,23 @@ int fft_execute_host(fft_plan_t p, const void *host_in, void *host_out, void *st
         cudaMemcpyAsync(h.din[i], host_in, bytes, cudaMemcpyHostToDevice, h.cin) != cudaSuccess ||
         cudaEventRecord(h.in_ready[i], h.cin) != cudaSuccess)
         return FFT_ERR_CUDA;
-    // the transform: after its input arrived and after the copy-out of two
-    // calls ago left output staging buffer i
-    if (cudaStreamWaitEvent(s, h.in_ready[i], 0) != cudaSuccess ||
-        cudaStreamWaitEvent(s, h.out_done[i], 0) != cudaSuccess)
+    // The transform runs on the plan's compute stream, so it can overlap the
+    // previous call's copy-out.  It reads and writes only staging buffers and
+    // the plan's workspaces; the workspaces were last used by a host call
+    // (already ordered on this stream) unless the plan ran on the caller's
+    // stream since, in which case the compute stream waits for that first.
+    if (!p->last_use_host &&
+        (cudaEventRecord(h.entry, s) != cudaSuccess || cudaStreamWaitEvent(h.comp, h.entry, 0) != cudaSuccess))
         return FFT_ERR_CUDA;
-    const int rc = run_dense(p, h.din[i], h.dout[i], p->dir, nullptr, 1.f, s);
+    // after its input arrived and after the copy-out of two calls ago left
+    // output staging buffer i
+    if (cudaStreamWaitEvent(h.comp, h.in_ready[i], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(h.comp, h.out_done[i], 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    const int rc = run_dense(p, h.din[i], h.dout[i], p->dir, nullptr, 1.f, h.comp);
     if (rc != FFT_OK) return rc;
-    if (cudaEventRecord(h.computed[i], s) != cudaSuccess ||
+    p->last_use_host = true;
+    if (cudaEventRecord(h.computed[i], h.comp) != cudaSuccess ||
         cudaStreamWaitEvent(h.cout, h.computed[i], 0) != cudaSuccess ||
         cudaMemcpyAsync(host_out, h.dout[i], bytes, cudaMemcpyDeviceToHost, h.cout) != cudaSuccess ||
         cudaEventRecord(h.out_done[i], h.cout) != cudaSuccess ||
@@ -855,11 +869,13 @@ int fft_execute_host(fft_plan_t p, const void *host_in, void *host_out, void *st
 
 int fft_backward(fft_plan_t p, const void *grad_out, void *grad_in, void *stream) {
     if (!p || p->kind != 0) return FFT_ERR_INVALID_ARG;
+    p->last_use_host = false;
     return run_dense(p, grad_out, grad_in, -p->dir, nullptr, 1.f, static_cast<cudaStream_t>(stream));
 }
 
 int fft_backward_weighted(fft_plan_t p, const void *X, const void *w, float scale, void *grad_in, void *stream) {
     if (!p || p->kind != 0 || !w || !aligned16(w)) return FFT_ERR_INVALID_ARG;
+    p->last_use_host = false;
     return run_dense(p, X, grad_in, -p->dir, static_cast<const float *>(w), scale,
                      static_cast<cudaStream_t>(stream));
 }

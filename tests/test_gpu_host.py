@@ -45,3 +45,24 @@ def test_host_rejects_device_and_aliased_buffers(g):
     lib = _native.load()
     assert lib.fft_execute_host(plan._p, h.data_ptr(), h.data_ptr(), 0) == -2
     plan.close()
+
+
+def test_host_calls_interleaved_with_device_calls(g):
+    """Host calls (plan compute stream) and device calls (caller's stream)
+    on one plan share its workspaces; interleaved, every result stays
+    correct."""
+    plan = g.Plan(8192, 8192, 1)
+    xs = [synth.uniform_complex((8192, 8192), seed=60 + k) for k in range(4)]
+    refs = []
+    for k in range(4):
+        hin = torch.from_numpy(xs[k]).pin_memory()
+        if k % 2 == 0:
+            hout = plan.execute_host(hin, torch.empty_like(hin).pin_memory())
+        else:
+            hout = plan.execute(hin.cuda()).cpu()
+        refs.append(hout)
+    torch.cuda.synchronize()
+    for k in range(4):
+        want = plan.execute(torch.from_numpy(xs[k]).cuda()).cpu()
+        assert torch.equal(torch.view_as_real(refs[k]), torch.view_as_real(want)), k
+    plan.close()
