@@ -13,6 +13,9 @@
 // j^2 mod 2n is reduced in integers and evaluated in FP64 (sincospi), then
 // rounded once to FP32.
 //
+// For M <= 8192 the chirp and filter products are fused into the two
+// transforms (k_blu below): two HBM passes over the padded rows.
+//
 // A 2D transform whose sizes are not both powers of two runs axis by axis:
 // the x axis over all rows, a tiled transpose, the y axis over the rows of
 // the transposed array, and the transpose back.
@@ -107,13 +110,133 @@ __global__ void __launch_bounds__(256) k_transpose(const float2 *__restrict__ in
     }
 }
 
+// Fused Bluestein for padded lengths M <= 8192 (one row per thread group, as
+// in the row pass).  Phase 0: A[r] = F(a) . H with a[j] = x[r][j] c[j] for
+// j < n and 0 up to M, the chirp product applied as the rows are loaded and
+// the filter product as the transform is stored.  Phase 1: out[r][k] =
+// c[k] * F^-1(A[r])[k] for k < n, the inverse as conj(F(conj(.))) and the
+// chirp product and truncation applied as it is stored.  Two HBM passes over
+// the padded rows instead of five.
+template <int N, int E>
+struct BluShape {
+    static constexpr int T = N / E;
+    static constexpr int ROWS = (T >= 256) ? 1 : 256 / T;
+    static constexpr int THREADS = ROWS * T;
+    using Eng = Engine<N, E, 1, PadShift<E>::value, RowPadShift1<E>::value>;
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
+    static constexpr int MINB = THREADS >= 512 ? (E >= 32 ? 512 : 1024) / THREADS : (THREADS >= 256 ? 2 : 1);
+};
+
+template <int N, int E, int PHASE>
+__global__ void __launch_bounds__(BluShape<N, E>::THREADS, BluShape<N, E>::MINB)
+    k_blu(const float2 *__restrict__ src, float2 *__restrict__ dst, const float2 *__restrict__ tw,
+          const float2 *__restrict__ chirp, const float2 *__restrict__ H, int n, long long rows) {
+    using Sh = BluShape<N, E>;
+    using Eng = typename Sh::Eng;
+    constexpr int T = Sh::T;
+    constexpr int R0 = Eng::R0;
+    extern __shared__ __align__(16) float2 smem[];
+    const int g = threadIdx.x / T;
+    const int tt = threadIdx.x - g * T;
+    float2 *sm = smem + g * Eng::SMEM_ELEMS;
+    const long long row = (long long)blockIdx.x * Sh::ROWS + g;
+    const bool active = row < rows;
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < E / R0; ++b) {
+        const int j = tt + b * T;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+            const int i = j + r * (N / R0);
+            float2 x = make_float2(0.f, 0.f);
+            if constexpr (PHASE == 0) {
+                if (active && i < n) x = cmul(__ldg(src + row * n + i), __ldg(chirp + i));
+            } else {
+                if (active) {
+                    x = __ldg(src + row * N + i);
+                    x.y = -x.y;
+                }
+            }
+            v[b * R0 + r] = x;
+        }
+    }
+    auto store = [&](int i, int, float2 x) {
+        if constexpr (PHASE == 0) {
+            if (active) dst[row * N + i] = cmul(x, __ldg(H + i));
+        } else {
+            if (active && i < n) {
+                x.y = -x.y;
+                dst[row * n + i] = cmul(x, __ldg(chirp + i));
+            }
+        }
+    };
+    auto none = [] {};
+    if constexpr (Eng::NT >= 32)
+        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncBlock{}, none, store);
+    else
+        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncWarp{}, none, store);
+}
+
 namespace {
+BluVariant g_blu[kMaxLog2 + 1];
+bool g_blu_init = false;
+
+template <int N>
+void reg_blu() {
+    constexpr int E = N >= 8192 ? 32 : N >= 16 ? 16 : (N >= 8 ? 8 : N);  // the row pass's default E
+    using Sh = BluShape<N, E>;
+    BluVariant &v = g_blu[ilog2(N)];
+    v.fn[0] = (const void *)k_blu<N, E, 0>;
+    v.fn[1] = (const void *)k_blu<N, E, 1>;
+    v.n = N;
+    v.e = E;
+    v.threads = Sh::THREADS;
+    v.rows_per_cta = Sh::ROWS;
+    v.smem = Sh::SMEM;
+}
+void init_blu() {
+    if (g_blu_init) return;
+    reg_blu<4>();
+    reg_blu<8>();
+    reg_blu<16>();
+    reg_blu<32>();
+    reg_blu<64>();
+    reg_blu<128>();
+    reg_blu<256>();
+    reg_blu<512>();
+    reg_blu<1024>();
+    reg_blu<2048>();
+    reg_blu<4096>();
+    reg_blu<8192>();
+    g_blu_init = true;
+}
+
 int blocks_for(long long count) {
     long long b = (count + 255) / 256;
     if (b > 152LL * 16) b = 152LL * 16;
     return (int)(b < 1 ? 1 : b);
 }
 }  // namespace
+
+const BluVariant *blu_variant(int M) {
+    init_blu();
+    if (M < 4 || M > 8192 || (M & (M - 1))) return nullptr;
+    const BluVariant *v = &g_blu[ilog2(M)];
+    return v->fn[0] ? v : nullptr;
+}
+
+cudaError_t launch_blu(const BluVariant &v, int phase, const float2 *src, float2 *dst, const float2 *tw,
+                       const float2 *chirp, const float2 *H, int n, long long rows, cudaStream_t s) {
+    if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
+    if (v.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn[phase], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (e != cudaSuccess) return e;
+    }
+    const long long grid = (rows + v.rows_per_cta - 1) / v.rows_per_cta;
+    if (grid < 1 || grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    void *args[] = {(void *)&src, (void *)&dst, (void *)&tw, (void *)&chirp, (void *)&H, (void *)&n, (void *)&rows};
+    return cudaLaunchKernel(v.fn[phase], dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+}
 
 cudaError_t build_chirp(float2 *c, int n, int sgn, cudaStream_t s) {
     k_chirp<<<(n + 255) / 256, 256, 0, s>>>(c, n, sgn);

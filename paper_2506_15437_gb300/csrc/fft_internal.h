@@ -203,7 +203,18 @@ struct FourStepPlan {
 // Any-size transforms (fft_bluestein.cu kernels, fft_plan.cu logic).  One
 // axis: `rows` transforms of length n along contiguous rows, by a
 // power-of-two sub-plan (M == 0) or by Bluestein over a length-M sub-plan.
+// Fused Bluestein kernels for one padded length M (fft_bluestein.cu).
+struct BluVariant {
+    const void *fn[2] = {nullptr, nullptr};  // phase 0 (forward, chirp in, filter out), 1 (inverse, chirp out)
+    int n = 0, e = 0, threads = 0, rows_per_cta = 0;
+    size_t smem = 0;
+};
+const BluVariant *blu_variant(int M);
+cudaError_t launch_blu(const BluVariant &v, int phase, const float2 *src, float2 *dst, const float2 *tw,
+                       const float2 *chirp, const float2 *H, int n, long long rows, cudaStream_t s);
+
 struct AnyAxis {
+    const BluVariant *fused = nullptr;  // M <= 8192: fused kernels (same E as the sub-plan's row pass)
     int n = 1, M = 0;
     long long rows = 0;
     fft_plan_s *sub = nullptr;           // (n or M, 1, rows), run forward and inverse

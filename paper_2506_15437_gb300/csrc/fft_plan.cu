@@ -461,6 +461,13 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
     }
     if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
     free_plan(one);
+    // fused kernels when the padded length is one row pass with the same E
+    // (so they share the sub-plan's twiddle table)
+    const char *ev = getenv("GB300FFT_BLUESTEIN_FUSED");  // 0: the five-pass form (tests, experiments)
+    const BluVariant *fv = (ev && atoi(ev) == 0) ? nullptr : blu_variant(ax.M);
+    if (rc == FFT_OK && fv && ax.sub->rows.row && ax.sub->fs.n1 == 0 && !ax.sub->any &&
+        fv->e == ax.sub->rows.row->e && (ax.sub->rows.tw || ax.sub->rows.row->tw_size == 0))
+        ax.fused = fv;
     return rc;
 }
 
@@ -550,6 +557,12 @@ void free_plan(fft_plan_s *p) {
 int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStream_t s) {
     if (!ax.M) return run_dense(ax.sub, in, out, sign, nullptr, 1.f, s);
     const int d = sign > 0 ? 1 : 0;
+    if (ax.fused) {
+        if (launch_blu(*ax.fused, 0, in, ax.A, ax.sub->rows.tw, ax.chirp[d], ax.H[d], ax.n, ax.rows, s) != cudaSuccess ||
+            launch_blu(*ax.fused, 1, ax.A, out, ax.sub->rows.tw, ax.chirp[d], nullptr, ax.n, ax.rows, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
     if (launch_blu_pre(in, ax.A, ax.chirp[d], ax.n, ax.M, ax.rows, s) != cudaSuccess) return FFT_ERR_CUDA;
     int rc = run_dense(ax.sub, ax.A, ax.A, FFT_FORWARD, nullptr, 1.f, s);
     if (rc != FFT_OK) return rc;
@@ -1046,9 +1059,9 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
     } else if (p->any) {
         const gb300fft::AnyPlan &ap = *p->any;
         k = snprintf(tmp, sizeof tmp,
-                     "{\"kind\": \"any\", \"precision\": \"fp32\", \"x\": {\"n\": %d, \"bluestein_m\": %d}, "
-                     "\"y\": {\"n\": %d, \"bluestein_m\": %d}, \"transposes\": %d}",
-                     ap.x.n, ap.x.M, ap.y.n, ap.y.M, ap.y.sub ? 2 : 0);
+                     "{\"kind\": \"any\", \"precision\": \"fp32\", \"x\": {\"n\": %d, \"bluestein_m\": %d, "
+                     "\"fused\": %d}, \"y\": {\"n\": %d, \"bluestein_m\": %d, \"fused\": %d}, \"transposes\": %d}",
+                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.y.n, ap.y.M, ap.y.fused ? 1 : 0, ap.y.sub ? 2 : 0);
     } else if (p->fs.n1 > 0) {
         const gb300fft::FourStepPlan &fs = p->fs;
         char ra[96], rb[96];

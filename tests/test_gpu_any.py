@@ -91,6 +91,28 @@ def test_long_1d_million_points(g):
     assert worst_rel_l2(got, ref, n) <= tol_any(n, 1)
 
 
+@pytest.mark.parametrize("n", [5, 100, 1000, 4095])
+def test_fused_and_unfused_bluestein_agree(g, monkeypatch, n):
+    """Padded lengths up to 8192 run the fused kernels (chirp and filter
+    products inside the two transforms); both forms meet the bound and agree
+    closely (the same arithmetic in a different grouping of passes)."""
+    x = synth.uniform_complex((3, n), seed=77 + n)
+    fused = g.Plan(n, 1, 3)
+    assert fused.describe()["x"]["fused"] == 1
+    monkeypatch.setenv("GB300FFT_BLUESTEIN_FUSED", "0")
+    plain = g.Plan(n, 1, 3)
+    monkeypatch.delenv("GB300FFT_BLUESTEIN_FUSED")
+    assert plain.describe()["x"]["fused"] == 0
+    d = torch.from_numpy(x).cuda()
+    a = fused.execute(d).cpu().numpy()
+    b = plain.execute(d).cpu().numpy()
+    ref = oracle.fft1d_any(x, threads=ORACLE_THREADS)
+    assert worst_rel_l2(a, ref, n) <= tol_any(n, 1)
+    assert worst_rel_l2(b, ref, n) <= tol_any(n, 1)
+    fused.close()
+    plain.close()
+
+
 def test_describe_and_unsupported(g):
     plan = g.get_plan(1000, 3, 1, False, "fp32", "cuda")
     d = plan.describe()
