@@ -38,6 +38,7 @@ struct ColVariant {
 const RowVariant *row_variant(int log2n, int e);           // nullptr if not compiled
 const ColVariant *col_variant(int log2n, int e, int w);    // nullptr if not compiled
 int default_row_e(int n);
+bool row_split_available(int n, int e);  // a column pre-split (P = 2) row kernel exists
 int default_col_e(int n);
 int preferred_col_e(int n, int w);
 int default_col_w(int n, int nx);

@@ -382,8 +382,10 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         Schedule plain = sc;
         if (rc == FFT_OK) rc = setup_col_axis(p, p->cols, ny, nx, (long long)nx * batch, plain);
         // Column pre-split: a length-8192 column needs a 128 KiB tile (one CTA
-        // per SM); splitting it as 2 x 4096 halves the tile.
-        const int split = (sc.split == 2 && ny >= 4) ? 2 : 1;
+        // per SM); splitting it as 2 x 4096 halves the tile.  Only row
+        // schedules compiled with the pre-split take it.
+        const int split =
+            (sc.split == 2 && ny >= 4 && p->rows.row && row_split_available(p->rows.n, p->rows.row->e)) ? 2 : 1;
         if (rc == FFT_OK && split > 1) {
             rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split, sc);
             if (rc == FFT_OK) {
@@ -966,7 +968,7 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                 continue;
             }
             for (int split : {1, 2}) {
-                if (split == 2 && p->ny < 4) continue;
+                if (split == 2 && (p->ny < 4 || !row_split_available(rown, re))) continue;
                 Schedule c;
                 c.row_e = re;
                 c.row_persist = persist;

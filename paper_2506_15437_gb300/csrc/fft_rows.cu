@@ -303,6 +303,11 @@ static const void *row_fn(const RowVariant &v, bool weighted, int split) {
     return k.fn;
 }
 
+bool row_split_available(int n, int e) {
+    const RowEntry *en = row_entry(ilog2(n), e);
+    return en && en->split2.fn && en->split2_weighted.fn;
+}
+
 int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, int split, bool persistent) {
     const void *fn = row_fn(v, weighted, split);
     if (!fn) return 0;
