@@ -214,7 +214,32 @@ const BluVariant *blu_variant(int M);
 cudaError_t launch_blu(const BluVariant &v, int phase, const float2 *src, float2 *dst, const float2 *tw,
                        const float2 *chirp, const float2 *H, int n, long long rows, cudaStream_t s);
 
+// Mixed-radix stages of a 7-smooth length n <= kMixedMaxN (fft_mixed.cu).
+constexpr int kMixedMaxN = 14336;           // two float2 buffers of n in one CTA's shared memory
+constexpr size_t kMixedMaxSmem = 227 * 1024;
+constexpr int kMixedMaxStages = 16;
+struct MixedStages {
+    int n = 0, S = 0, tw_size = 0;
+    int wlog = 0;                      // log2 of the columns per CTA (column kernel)
+    int radix[kMixedMaxStages] = {};
+    int ns[kMixedMaxStages] = {};      // product of the radices before stage s
+    int nb[kMixedMaxStages] = {};      // butterflies per transform, n / radix
+    uint32_t mag_nb[kMixedMaxStages] = {}, mag_ns[kMixedMaxStages] = {};  // ceil(2^32 / d) divisors
+    int tw_off[kMixedMaxStages] = {};  // stage s's twiddles w_{Ns R}^{k r} at tw_off[s] + k (R - 1) + r - 1
+};
+bool mixed_factor(int n, MixedStages *st);  // false unless n = 2^a 3^b 5^c 7^d <= kMixedMaxN
+cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s);
+int mixed_rows_per_cta(int n);
+int mixed_cols_width(int n, int nx);
+cudaError_t launch_mixed_rows(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out,
+                              long long rows, int conj, cudaStream_t s);
+cudaError_t launch_mixed_cols(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out, int nx,
+                              long long slices, int conj, cudaStream_t s);
+
 struct AnyAxis {
+    bool mixed = false;                 // 7-smooth n: the mixed-radix kernel, no padding
+    MixedStages mst;
+    float2 *mtw = nullptr;              // mixed-radix twiddles (forward)
     const BluVariant *fused = nullptr;  // M <= 8192: fused kernels (same E as the sub-plan's row pass)
     int n = 1, M = 0;
     long long rows = 0;
@@ -227,6 +252,7 @@ struct AnyAxis {
 // (2D) transpose, y axis over the rows of the transposed array, transpose back.
 struct AnyPlan {
     AnyAxis x, y;                // y.n == 1: a 1D batch
+    bool y_cols = false;         // y axis by the mixed-radix column kernel, in place, no transposes
     float2 *t = nullptr;         // [batch][nx][ny] transposed workspace
 };
 cudaError_t build_chirp(float2 *c, int n, int sgn, cudaStream_t s);

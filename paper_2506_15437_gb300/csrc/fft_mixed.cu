@@ -1,0 +1,349 @@
+// Mixed-radix transforms for lengths of the form 2^a 3^b 5^c 7^d.
+//
+// The paper's kernels take powers of two only and name uneven sizes as
+// further work (Sections 6 and 7).  Smooth lengths up to kMixedMaxN run here
+// as a Stockham autosort transform whose stages have radix 8, 4, 2, 3, 5 or 7,
+// chosen at plan time: stage s of radix R, with Ns the product of the radices
+// before it, takes butterfly j (k = j mod Ns) from elements j + r n/R,
+// multiplies leg r by w_{Ns R}^{k r}, runs an R-point DFT and writes leg r to
+// element (j - k) R + k + r Ns.  After the last stage the output is in natural
+// order, so no reorder pass exists.  One CTA owns whole transforms: the first
+// stage reads global memory, the last writes it, and the stages between
+// ping-pong through two shared-memory buffers.
+//
+// Two layouts: rows (transforms along contiguous rows, W rows per CTA when
+// they are short) and columns (the transforms of W adjacent columns of an
+// [ny][nx] slice, element i of column x at i*nx + x), which serves the y axis
+// of a 2D plan without a transpose.
+#include "fft_common.cuh"
+#include "fft_internal.h"
+
+namespace gb300fft {
+
+namespace {
+
+// cos(2 pi j / R) and sin(2 pi j / R) for 1 <= j <= (R-1)/2, R in {3, 5, 7}
+__host__ __device__ constexpr float cos_r(int R, int j) {
+    return R == 3   ? -0.5f
+           : R == 5 ? (j == 1 ? 0.30901699437494742f : -0.80901699437494742f)
+                    : (j == 1 ? 0.62348980185873353f : j == 2 ? -0.22252093395631440f : -0.90096886790241913f);
+}
+__host__ __device__ constexpr float sin_r(int R, int j) {
+    return R == 3   ? 0.86602540378443865f
+           : R == 5 ? (j == 1 ? 0.95105651629515357f : 0.58778525229247313f)
+                    : (j == 1 ? 0.78183148246802981f : j == 2 ? 0.97492791218182361f : 0.43388373911755812f);
+}
+
+// Forward R-point DFT for odd prime R, legs paired as (k, R - k):
+//   y_m     = a_0 + sum_k t_k cos(2 pi k m / R) - i sum_k d_k sin(2 pi k m / R)
+//   y_{R-m} = a_0 + sum_k t_k cos(2 pi k m / R) + i sum_k d_k sin(2 pi k m / R)
+// with t_k = a_k + a_{R-k}, d_k = a_k - a_{R-k}, k, m = 1 .. (R-1)/2.
+template <int R>
+__device__ __forceinline__ void dft_odd(float2 *a) {
+    constexpr int H = (R - 1) / 2;
+    float2 t[H], d[H];
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        t[k - 1] = cadd(a[k], a[R - k]);
+        d[k - 1] = csub(a[k], a[R - k]);
+    }
+    float2 y0 = a[0];
+#pragma unroll
+    for (int k = 0; k < H; ++k) y0 = cadd(y0, t[k]);
+    float2 y[R];
+    y[0] = y0;
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+        float2 A = a[0], B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            const int q = (k * m) % R;  // angle index, folded into 1 .. H
+            const int j = q <= H ? q : R - q;
+            const float c = cos_r(R, j);
+            const float sn = q <= H ? sin_r(R, j) : -sin_r(R, j);
+            A = make_float2(fmaf(c, t[k - 1].x, A.x), fmaf(c, t[k - 1].y, A.y));
+            B = make_float2(fmaf(sn, d[k - 1].x, B.x), fmaf(sn, d[k - 1].y, B.y));
+        }
+        // -i B = (B.y, -B.x)
+        y[m] = make_float2(A.x + B.y, A.y - B.x);
+        y[R - m] = make_float2(A.x - B.y, A.y + B.x);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) a[k] = y[k];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_any(float2 *a) {
+    if constexpr ((R & (R - 1)) == 0) dft<R>(a);
+    else dft_odd<R>(a);
+}
+
+struct MixedGeom {
+    int n;        // transform length
+    int W;        // transforms per CTA
+    int nv;       // valid transforms in this CTA (rows: the last CTA may hold fewer)
+    int estride;  // element stride within a transform (1 for rows, nx for columns)
+    int tstride;  // offset between the CTA's transforms (n for rows, 1 for columns)
+};
+
+// x / d for x * d < 2^32 by a multiply-high with m = ceil(2^32 / d) (d >= 2);
+// d = 1 passes x through
+__device__ __forceinline__ int fdiv(int x, int d, uint32_t m) {
+    return d == 1 ? x : (int)__umulhi((uint32_t)x, m);
+}
+
+struct StageArgs {
+    int nb, Ns;  // butterflies per transform, product of the earlier radices
+    uint32_t mag_nb, mag_ns;
+    int wlog;
+};
+
+// One stage of radix R over the CTA's W transforms, `src` to `dst` (global
+// memory in place of `src` in the first stage, of `dst` in the last).  Rows:
+// butterfly index fastest within a transform (coalesced rows); columns:
+// transform fastest (W adjacent columns of a row together).  Local layout:
+// rows [c][i], columns [i][c].  `gin` and `gout` point at the CTA's first
+// transform, so every offset within the group fits 32 bits.
+template <int R, bool COLS, bool FIRST, bool LAST>
+__device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs a, const float2 *src, float2 *dst,
+                                            const float2 *gin, float2 *gout, const float2 *__restrict__ tws,
+                                            float si) {
+    const int nb = a.nb, Ns = a.Ns;
+    const int total = g.nv * nb;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int c, j;
+        if (COLS) {
+            c = idx & (g.W - 1);
+            j = idx >> a.wlog;
+        } else {
+            c = fdiv(idx, nb, a.mag_nb);
+            j = idx - c * nb;
+        }
+        const int k = j - fdiv(j, Ns, a.mag_ns) * Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = j + r * nb;
+            if (FIRST) {
+                float2 x = gin[c * g.tstride + i * g.estride];
+                x.y *= si;
+                v[r] = x;
+            } else {
+                v[r] = src[COLS ? i * g.W + c : c * g.n + i];
+            }
+        }
+        if (!FIRST) {
+            const float2 *w = tws + k * (R - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(w + r - 1));
+        }
+        dft_any<R>(v);
+        const int o0 = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int o = o0 + r * Ns;
+            if (LAST) {
+                float2 x = v[r];
+                x.y *= si;
+                gout[c * g.tstride + o * g.estride] = x;
+            } else {
+                dst[COLS ? o * g.W + c : c * g.n + o] = v[r];
+            }
+        }
+    }
+}
+
+template <bool COLS, bool FIRST, bool LAST>
+__device__ __forceinline__ void mixed_dispatch(int R, const MixedGeom &g, const StageArgs a, const float2 *src,
+                                               float2 *dst, const float2 *gin, float2 *gout, const float2 *tws,
+                                               float si) {
+    switch (R) {
+        case 2: mixed_stage<2, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 3: mixed_stage<3, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 4: mixed_stage<4, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 5: mixed_stage<5, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 7: mixed_stage<7, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        default: mixed_stage<8, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+    }
+}
+
+template <bool COLS>
+__global__ void __launch_bounds__(512) k_mixed(const float2 *in, float2 *out, const float2 *__restrict__ tw,
+                                               const MixedStages st, long long ntrans, int W, int nx, int conj) {
+    extern __shared__ __align__(16) float2 mbuf[];
+    MixedGeom g;
+    g.n = st.n;
+    g.W = W;
+    const long long t0 = (long long)blockIdx.x * W;  // first transform of this CTA
+    long long base;
+    if (COLS) {
+        // transform t: column t % nx of slice t / nx; W divides nx
+        const long long b = t0 / nx;
+        const int x0 = (int)(t0 - b * nx);
+        g.nv = W;
+        base = b * (long long)nx * st.n + x0;
+        g.estride = nx;
+        g.tstride = 1;
+    } else {
+        g.nv = (int)(ntrans - t0 < W ? ntrans - t0 : W);
+        base = t0 * st.n;
+        g.estride = 1;
+        g.tstride = st.n;
+    }
+    const float2 *gin = in + base;
+    float2 *gout = out + base;
+    const float si = conj ? -1.f : 1.f;
+    float2 *A = mbuf, *B = mbuf + (size_t)W * st.n;
+    for (int s = 0; s < st.S; ++s) {
+        StageArgs a;
+        a.nb = st.nb[s];
+        a.Ns = st.ns[s];
+        a.mag_nb = st.mag_nb[s];
+        a.mag_ns = st.mag_ns[s];
+        a.wlog = st.wlog;
+        const float2 *tws = tw + st.tw_off[s];
+        const int R = st.radix[s];
+        if (st.S == 1) mixed_dispatch<COLS, true, true>(R, g, a, A, B, gin, gout, tws, si);
+        else if (s == 0) mixed_dispatch<COLS, true, false>(R, g, a, A, B, gin, gout, tws, si);
+        else if (s == st.S - 1) mixed_dispatch<COLS, false, true>(R, g, a, A, B, gin, gout, tws, si);
+        else mixed_dispatch<COLS, false, false>(R, g, a, A, B, gin, gout, tws, si);
+        __syncthreads();
+        float2 *tmp = A;
+        A = B;
+        B = tmp;
+    }
+}
+
+// stage s's table: entry k (R - 1) + r - 1 = w_{Ns R}^{k r}, k < Ns, 1 <= r < R,
+// from the FP64 root, rounded once
+__global__ void k_mixed_twiddles(float2 *t, int Ns, int R) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Ns * (R - 1)) return;
+    const int k = e / (R - 1), r = e % (R - 1) + 1;
+    const int L = Ns * R;
+    double sv, cv;
+    sincospi(2.0 * (double)((k * r) % L) / (double)L, &sv, &cv);
+    t[e] = make_float2((float)cv, (float)(-sv));
+}
+
+bool smem_ok(const void *fn, size_t smem) {
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                                cudaSuccess)
+        return false;
+    return true;
+}
+
+uint32_t magic(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d - 1) / (uint64_t)d); }
+
+// Threads for a group of W transforms of total length W n.
+int mixed_threads(int elems) { return elems > 4096 ? 512 : 256; }
+
+// the stage constants the kernel reads for a group of W transforms
+MixedStages with_group(const MixedStages &st, int W) {
+    MixedStages m = st;
+    m.wlog = ilog2(W);
+    for (int s = 0; s < st.S; ++s) {
+        m.mag_nb[s] = magic(st.nb[s]);
+        m.mag_ns[s] = magic(st.ns[s]);
+    }
+    return m;
+}
+
+}  // namespace
+
+bool mixed_factor(int n, MixedStages *st) {
+    if (n < 2 || n > kMixedMaxN) return false;
+    MixedStages m;
+    m.n = n;
+    int rest = n, S = 0;
+    auto push = [&](int R) {
+        if (S >= kMixedMaxStages) return false;
+        m.radix[S++] = R;
+        rest /= R;
+        return true;
+    };
+    while (rest % 8 == 0)
+        if (!push(8)) return false;
+    if (rest % 4 == 0 && !push(4)) return false;
+    if (rest % 2 == 0 && !push(2)) return false;
+    for (int R : {3, 5, 7})
+        while (rest % R == 0)
+            if (!push(R)) return false;
+    if (rest != 1) return false;
+    m.S = S;
+    int off = 0, Ns = 1;
+    for (int s = 0; s < S; ++s) {
+        m.tw_off[s] = off;
+        m.ns[s] = Ns;
+        m.nb[s] = n / m.radix[s];
+        off += Ns * (m.radix[s] - 1);
+        Ns *= m.radix[s];
+    }
+    m.tw_size = off;
+    if (st) *st = m;
+    return true;
+}
+
+cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s) {
+    int Ns = 1;
+    for (int i = 0; i < st.S; ++i) {
+        const int R = st.radix[i], count = Ns * (R - 1);
+        k_mixed_twiddles<<<(count + 255) / 256, 256, 0, s>>>(tw + st.tw_off[i], Ns, R);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        Ns *= R;
+    }
+    return cudaSuccess;
+}
+
+int mixed_rows_per_cta(int n) {
+    int W = 1;
+    while (W < 64 && (long long)2 * W * n <= 4096) W *= 2;
+    return W;
+}
+
+int mixed_cols_width(int n, int nx) {
+    // widest group of adjacent columns (a divisor of nx) whose two buffers
+    // leave room for three CTAs per SM, else the widest that fits at all
+    for (int W : {8, 4, 2})
+        if (nx % W == 0 && (size_t)2 * W * n * sizeof(float2) <= 72 * 1024) return W;
+    for (int W : {8, 4, 2})
+        if (nx % W == 0 && (size_t)2 * W * n * sizeof(float2) <= kMixedMaxSmem) return W;
+    return 1;
+}
+
+cudaError_t launch_mixed_rows(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out,
+                              long long rows, int conj, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const int W = mixed_rows_per_cta(st.n);
+    const size_t smem = (size_t)2 * W * st.n * sizeof(float2);
+    if (smem > kMixedMaxSmem) return cudaErrorInvalidValue;
+    const void *fn = (const void *)k_mixed<false>;
+    if (!smem_ok(fn, smem)) return cudaErrorInvalidValue;
+    const long long grid = (rows + W - 1) / W;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const MixedStages m = with_group(st, W);
+    const int nx = 0;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&m, (void *)&rows, (void *)&W, (void *)&nx,
+                    (void *)&conj};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(mixed_threads(W * st.n)), args, smem, s);
+}
+
+cudaError_t launch_mixed_cols(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out, int nx,
+                              long long slices, int conj, cudaStream_t s) {
+    if (slices <= 0 || nx <= 0) return cudaSuccess;
+    const int W = mixed_cols_width(st.n, nx);
+    const size_t smem = (size_t)2 * W * st.n * sizeof(float2);
+    if (nx % W || smem > kMixedMaxSmem) return cudaErrorInvalidValue;
+    const void *fn = (const void *)k_mixed<true>;
+    if (!smem_ok(fn, smem)) return cudaErrorInvalidValue;
+    long long ntrans = slices * nx;
+    const long long grid = ntrans / W;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const MixedStages m = with_group(st, W);
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&m, (void *)&ntrans, (void *)&W, (void *)&nx,
+                    (void *)&conj};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(mixed_threads(W * st.n)), args, smem, s);
+}
+
+}  // namespace gb300fft

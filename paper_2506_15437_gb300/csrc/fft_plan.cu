@@ -428,10 +428,18 @@ long long next_pow2(long long v) {
     return m;
 }
 
+// mixed-radix stages for this length, unless GB300FFT_MIXED=0 (tests and
+// experiments compare against Bluestein)
+bool use_mixed(int n, MixedStages *st) {
+    const char *ev = getenv("GB300FFT_MIXED");
+    if (ev && atoi(ev) == 0) return false;
+    return !is_pow2(n) && mixed_factor(n, st);
+}
+
 // One axis of an any-size plan: rows transforms of length n.  A power of two
-// gets a dense sub-plan of its own; any other n gets Bluestein over a
-// length-M power-of-two sub-plan, M >= 2n - 1, with the chirps and the
-// filter transforms built here.
+// gets a dense sub-plan of its own; a 7-smooth n up to kMixedMaxN the
+// mixed-radix kernel; any other n Bluestein over a length-M power-of-two
+// sub-plan, M >= 2n - 1, with the chirps and the filter transforms built here.
 int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
     ax.n = n;
     ax.rows = rows;
@@ -439,6 +447,12 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
     if (is_pow2(n)) {
         ax.sub = create_dense(n, 1, (int)rows, FFT_FORWARD, FFT_PREC_FP32, default_schedule(n, 1), &rc);
         return ax.sub ? FFT_OK : rc;
+    }
+    if (use_mixed(n, &ax.mst)) {
+        ax.mixed = true;
+        ax.mtw = dev_alloc<float2>(p, ax.mst.tw_size > 0 ? ax.mst.tw_size : 1);
+        if (!ax.mtw) return FFT_ERR_ALLOC;
+        return build_mixed_twiddles(ax.mtw, ax.mst, 0) == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
     }
     ax.M = (int)next_pow2(2LL * n - 1);
     if (rows * ax.M > (1LL << 31)) return FFT_ERR_INVALID_SIZE;
@@ -500,7 +514,9 @@ fft_plan_s *create_any(int nx, int ny, int batch, int dir, int *rc_out) {
         } else {
             rc = setup_any_axis(p, ap->x, nx, (long long)ny * batch);
             if (rc == FFT_OK) rc = setup_any_axis(p, ap->y, ny, (long long)nx * batch);
-            if (rc == FFT_OK) {
+            // a mixed-radix y axis runs down the columns in place
+            ap->y_cols = rc == FFT_OK && ap->y.mixed;
+            if (rc == FFT_OK && !ap->y_cols) {
                 ap->t = dev_alloc<float2>(p, (size_t)nx * ny * batch);
                 if (!ap->t) rc = FFT_ERR_ALLOC;
             }
@@ -557,6 +573,10 @@ void free_plan(fft_plan_s *p) {
 
 // rows transforms of length ax.n along contiguous rows, in -> out (may alias)
 int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStream_t s) {
+    if (ax.mixed)
+        return launch_mixed_rows(ax.mst, ax.mtw, in, out, ax.rows, sign > 0 ? 1 : 0, s) == cudaSuccess
+                   ? FFT_OK
+                   : FFT_ERR_CUDA;
     if (!ax.M) return run_dense(ax.sub, in, out, sign, nullptr, 1.f, s);
     const int d = sign > 0 ? 1 : 0;
     if (ax.fused) {
@@ -582,7 +602,10 @@ int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_
     int rc = run_any_axis(ap.x, src, dst, sign, s);
     if (rc != FFT_OK) return rc;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (ap.y.sub) {
+    if (ap.y_cols) {
+        if (launch_mixed_cols(ap.y.mst, ap.y.mtw, dst, dst, p->nx, p->batch, sign > 0 ? 1 : 0, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+    } else if (p->nx > 1 && p->ny > 1) {
         const long long batch = p->batch;
         if (launch_transpose(dst, ap.t, p->ny, p->nx, batch, s) != cudaSuccess) return FFT_ERR_CUDA;
         rc = run_any_axis(ap.y, ap.t, ap.t, sign, s);
@@ -1062,8 +1085,10 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
         const gb300fft::AnyPlan &ap = *p->any;
         k = snprintf(tmp, sizeof tmp,
                      "{\"kind\": \"any\", \"precision\": \"fp32\", \"x\": {\"n\": %d, \"bluestein_m\": %d, "
-                     "\"fused\": %d}, \"y\": {\"n\": %d, \"bluestein_m\": %d, \"fused\": %d}, \"transposes\": %d}",
-                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.y.n, ap.y.M, ap.y.fused ? 1 : 0, ap.y.sub ? 2 : 0);
+                     "\"fused\": %d, \"mixed\": %d}, \"y\": {\"n\": %d, \"bluestein_m\": %d, \"fused\": %d, "
+                     "\"mixed\": %d}, \"transposes\": %d}",
+                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.x.mixed ? 1 : 0, ap.y.n, ap.y.M, ap.y.fused ? 1 : 0,
+                     ap.y.mixed ? 1 : 0, (p->nx > 1 && p->ny > 1 && !ap.y_cols) ? 2 : 0);
     } else if (p->fs.n1 > 0) {
         const gb300fft::FourStepPlan &fs = p->fs;
         char ra[96], rb[96];

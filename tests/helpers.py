@@ -55,17 +55,54 @@ def bluestein_m(n: int) -> int:
     return m
 
 
-def tol_any_axis(n: int) -> float:
-    """FP32 bound for one axis of any length.  A power of two is the plain
-    path (2e-7 * log2 n); any other n goes through Bluestein: two transforms
-    of length M = bluestein_m(n), the filter transform (a third one, computed
-    once in FP32) and three roundings by unit-modulus factors, so
-    2e-7 * (3 * log2 M + 3)."""
-    if n & (n - 1) == 0:
-        return 2e-7 * max(1.0, math.log2(n))
+MIXED_MAX_N = 14336  # longest mixed-radix length (two float2 buffers in one CTA's shared memory)
+
+
+def odd_factors(n: int) -> int:
+    """Number of prime factors 3, 5, 7 of n (with multiplicity) if n is
+    7-smooth, else -1."""
+    k = 0
+    for p in (3, 5, 7):
+        while n % p == 0:
+            n //= p
+            k += 1
+    while n % 2 == 0:
+        n //= 2
+    return k if n == 1 else -1
+
+
+def mixed_eligible(n: int) -> bool:
+    """Lengths the mixed-radix kernel takes: 7-smooth, not a power of two,
+    at most MIXED_MAX_N."""
+    return n & (n - 1) != 0 and n <= MIXED_MAX_N and odd_factors(n) >= 0
+
+
+def tol_bluestein_axis(n: int) -> float:
+    """Bluestein: two transforms of length M = bluestein_m(n), the filter
+    transform (a third one, computed once in FP32) and three roundings by
+    unit-modulus factors, so 2e-7 * (3 * log2 M + 3)."""
     return 2e-7 * (3 * math.log2(bluestein_m(n)) + 3)
 
 
-def tol_any(nx: int, ny: int) -> float:
+def tol_mixed_axis(n: int) -> float:
+    """Mixed radix: the power-of-two bound per radix-2-equivalent level
+    (2e-7 * log2 n) plus one level for each odd-radix stage, whose DFT folds
+    the legs into sums and differences before its multiply-adds."""
+    return 2e-7 * (math.log2(n) + odd_factors(n))
+
+
+def tol_any_axis(n: int, mixed: bool = True) -> float:
+    """FP32 bound for one axis of any length: a power of two is the plain
+    path (2e-7 * log2 n); a 7-smooth length up to MIXED_MAX_N the mixed-radix
+    kernel (unless `mixed` is False: the plan was made with it switched off);
+    any other length Bluestein."""
+    if n & (n - 1) == 0:
+        return 2e-7 * max(1.0, math.log2(n))
+    if mixed and mixed_eligible(n):
+        return tol_mixed_axis(n)
+    return tol_bluestein_axis(n)
+
+
+def tol_any(nx: int, ny: int, mixed: bool = True) -> float:
     """Errors of the two axes add (a transpose is exact)."""
-    return tol_any_axis(nx) + (tol_any_axis(ny) if ny > 1 else 0.0)
+    return tol_any_axis(nx, mixed) + (tol_any_axis(ny, mixed) if ny > 1 else 0.0)

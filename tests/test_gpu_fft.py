@@ -315,13 +315,15 @@ def test_column_pass_elements_per_thread(g, monkeypatch, e, ny, nx, batch, inver
     plan.close()
 
 
-@pytest.mark.parametrize("ny,nx,batch", [(4096, 4, 2), (4096, 256, 1), (8192, 64, 1), (8192, 8192, 1)])
+@pytest.mark.parametrize("ny,nx,batch", [(4096, 4, 2), (4096, 256, 1), (8192, 64, 1), (8192, 8192, 1),
+                                         (8192, 8192, 2)])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_streaming_column_pass_is_bit_identical(g, monkeypatch, ny, nx, batch, inverse):
     """The streaming column pass (row pass storing rows permuted, segments
     landing per warp) and the landed-pair row pass run the same operations in
     the same order as the plain row and column passes, so results agree bit
-    for bit; both meet the oracle bound."""
+    for bit; both meet the oracle bound.  The batch of two 8192 x 8192
+    transforms has pairs on both sides of the slice boundary."""
     monkeypatch.setenv("GB300FFT_COL_STREAM", "1")
     monkeypatch.setenv("GB300FFT_ROW_LAND", "1")
     ps = g.Plan(nx, ny, batch, inverse=inverse)

@@ -68,11 +68,13 @@ def test_host_calls_interleaved_with_device_calls(g):
     plan.close()
 
 
-@pytest.mark.parametrize("nx,ny,batch", [(8192, 8192, 1), (1 << 24, 1, 1), (1000, 1000, 1), (4096, 4096, 2)])
+@pytest.mark.parametrize("nx,ny,batch", [(8192, 8192, 1), (1 << 24, 1, 1), (1001, 1001, 1), (1000, 1000, 1),
+                                         (4096, 4096, 2)])
 def test_execute_is_graph_capturable(g, nx, ny, batch):
     """fft_execute allocates and synchronises nothing, so a CUDA graph can
     capture it: the landed-pair rows with the streaming planar columns, the
-    four-step path, and the fused Bluestein path with its transposes.  A
+    four-step path, the fused Bluestein path with its transposes and the
+    mixed-radix path with its in-place column kernel.  A
     replay on new input gives the eager result bit for bit."""
     plan = g.Plan(nx, ny, batch)
     x0 = torch.from_numpy(synth.uniform_complex((batch, ny, nx), seed=81)).cuda()
