@@ -457,6 +457,12 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(n, n, b)
         X = torch.empty_like(x)
         run = lambda: (plan.execute(x, out=X), plan.backward_weighted(X, w, 2.0))  # noqa: E731
+    elif name == "mixed_3000":
+        # 8192 signals of 3000 = 2^3 3 5^3 points (mixed radix, 196 MB each way)
+        x = torch.from_numpy(synth.uniform_complex((8192, 3000), seed=SEED)).to(dev)
+        plan = g.Plan(3000, 1, 8192)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     elif name.startswith("fourstep"):
         n, b = (1 << 24, 4) if name == "fourstep_2p24" else (1 << 26, 1)
         x = torch.from_numpy(synth.uniform_complex((b, n), seed=SEED)).to(dev)
@@ -491,7 +497,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
                     choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "ragged", "diff", "fourstep_2p24",
-                             "fourstep_2p26"],
+                             "fourstep_2p26", "mixed_3000"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

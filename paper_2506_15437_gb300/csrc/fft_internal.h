@@ -221,24 +221,36 @@ constexpr int kMixedMaxStages = 16;
 struct MixedStages {
     int n = 0, S = 0, tw_size = 0;
     int wlog = 0;                      // log2 of the columns per CTA (column kernel)
+    int buf_elems = 0;                 // elements of one padded shared-memory buffer
+    int pad[kMixedMaxStages] = {};     // padding shift of the buffer stage s writes (0: none)
     int radix[kMixedMaxStages] = {};
     int ns[kMixedMaxStages] = {};      // product of the radices before stage s
     int nb[kMixedMaxStages] = {};      // butterflies per transform, n / radix
     uint32_t mag_nb[kMixedMaxStages] = {}, mag_ns[kMixedMaxStages] = {};  // ceil(2^32 / d) divisors
     int tw_off[kMixedMaxStages] = {};  // stage s's twiddles w_{Ns R}^{k r} at tw_off[s] + k (R - 1) + r - 1
 };
+// Launch configuration of the mixed-radix kernel for one axis, fixed at
+// plan creation: transforms per CTA, threads, padded buffers.
+struct MixedLaunch {
+    MixedStages m;
+    bool cols = false;
+    int nx = 0;  // columns: row length of the [ny][nx] slices
+    int W = 1, T = 0;
+    size_t smem = 0;
+};
 bool mixed_factor(int n, MixedStages *st);  // false unless n = 2^a 3^b 5^c 7^d <= kMixedMaxN
 cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s);
 int mixed_rows_per_cta(int n);
 int mixed_cols_width(int n, int nx);
-cudaError_t launch_mixed_rows(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out,
-                              long long rows, int conj, cudaStream_t s);
-cudaError_t launch_mixed_cols(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out, int nx,
-                              long long slices, int conj, cudaStream_t s);
+int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out);  // 0 on success
+// rows: `count` transforms along contiguous rows; columns: `count` [n][nx] slices
+cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *in, float2 *out, long long count,
+                         int conj, cudaStream_t s);
 
 struct AnyAxis {
     bool mixed = false;                 // 7-smooth n: the mixed-radix kernel, no padding
     MixedStages mst;
+    MixedLaunch ml;                     // rows, or (the y axis of a 2D plan) columns
     float2 *mtw = nullptr;              // mixed-radix twiddles (forward)
     const BluVariant *fused = nullptr;  // M <= 8192: fused kernels (same E as the sub-plan's row pass)
     int n = 1, M = 0;

@@ -96,7 +96,12 @@ struct StageArgs {
     int nb, Ns;  // butterflies per transform, product of the earlier radices
     uint32_t mag_nb, mag_ns;
     int wlog;
+    int pin, pout;  // padding shifts of the buffer read and of the buffer written (31: none)
 };
+
+// padded shared-memory index: one spare slot after every 2^ps elements
+// (ps = 31: no padding, since every index is below 2^31)
+__device__ __forceinline__ int padx(int x, int ps) { return x + (x >> ps); }
 
 // One stage of radix R over the CTA's W transforms, `src` to `dst` (global
 // memory in place of `src` in the first stage, of `dst` in the last).  Rows:
@@ -129,7 +134,7 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
                 x.y *= si;
                 v[r] = x;
             } else {
-                v[r] = src[COLS ? i * g.W + c : c * g.n + i];
+                v[r] = src[padx(COLS ? i * g.W + c : c * g.n + i, a.pin)];
             }
         }
         if (!FIRST) {
@@ -147,7 +152,7 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
                 x.y *= si;
                 gout[c * g.tstride + o * g.estride] = x;
             } else {
-                dst[COLS ? o * g.W + c : c * g.n + o] = v[r];
+                dst[padx(COLS ? o * g.W + c : c * g.n + o, a.pout)] = v[r];
             }
         }
     }
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(512) k_mixed(const float2 *in, float2 *out, co
     const float2 *gin = in + base;
     float2 *gout = out + base;
     const float si = conj ? -1.f : 1.f;
-    float2 *A = mbuf, *B = mbuf + (size_t)W * st.n;
+    float2 *A = mbuf, *B = mbuf + st.buf_elems;
     for (int s = 0; s < st.S; ++s) {
         StageArgs a;
         a.nb = st.nb[s];
@@ -201,6 +206,8 @@ __global__ void __launch_bounds__(512) k_mixed(const float2 *in, float2 *out, co
         a.mag_nb = st.mag_nb[s];
         a.mag_ns = st.mag_ns[s];
         a.wlog = st.wlog;
+        a.pin = (s > 0 && st.pad[s - 1]) ? st.pad[s - 1] : 31;
+        a.pout = st.pad[s] ? st.pad[s] : 31;
         const float2 *tws = tw + st.tw_off[s];
         const int R = st.radix[s];
         if (st.S == 1) mixed_dispatch<COLS, true, true>(R, g, a, A, B, gin, gout, tws, si);
@@ -238,14 +245,84 @@ uint32_t magic(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (
 // Threads for a group of W transforms of total length W n.
 int mixed_threads(int elems) { return elems > 4096 ? 512 : 256; }
 
-// the stage constants the kernel reads for a group of W transforms
-MixedStages with_group(const MixedStages &st, int W) {
+// Shared-memory wavefronts of one access pattern under the half-warp model
+// for 8-byte words: the 16 lanes of a half-warp form one wavefront per
+// distinct word sharing a bank pair, so the cost of a half-warp is the
+// largest number of distinct words on one pair (1 when conflict free).
+// `addr(lane)` gives the padded word index or -1 for an idle lane.
+template <class F>
+long long half_warp_cost(int lanes, F addr) {
+    long long cost = 0;
+    for (int h = 0; h < lanes; h += 16) {
+        int words[16][16];
+        int cnt[16] = {};
+        for (int l = h; l < h + 16 && l < lanes; ++l) {
+            const int a = addr(l);
+            if (a < 0) continue;
+            const int b = a & 15;
+            bool seen = false;
+            for (int q = 0; q < cnt[b]; ++q) seen = seen || words[b][q] == a;
+            if (!seen) words[b][cnt[b]++] = a;
+        }
+        int worst = 0;
+        for (int b = 0; b < 16; ++b) worst = cnt[b] > worst ? cnt[b] : worst;
+        cost += worst;
+    }
+    return cost;
+}
+
+// Cost of the buffer written by stage s (with shift ps) and read by stage
+// s + 1 (same shift), over the first warps of every round (the patterns
+// repeat with the butterfly index).
+long long boundary_cost(const MixedStages &st, int s, int W, bool cols, int T, int ps) {
+    auto pad = [ps](int x) { return ps ? x + (x >> ps) : x; };
+    long long cost = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int t = s + side;  // stage that writes (side 0) or reads (side 1)
+        const int R = st.radix[t], nb = st.nb[t], Ns = st.ns[t];
+        const int total = W * nb;
+        for (int base = 0; base < total; base += T)
+            for (int w0 = base; w0 < base + T && w0 < total && w0 < base + 4 * 32; w0 += 32)
+                for (int r = 0; r < R; ++r)
+                    cost += half_warp_cost(32, [&](int l) {
+                        const int idx = w0 + l;
+                        if (idx >= total || idx >= base + T) return -1;
+                        const int c = cols ? idx % W : idx / nb;
+                        const int j = cols ? idx / W : idx % nb;
+                        const int k = j % Ns;
+                        const int e = side ? j + r * nb : (j - k) * R + k + r * Ns;
+                        return pad(cols ? e * W + c : c * st.n + e);
+                    });
+    }
+    return cost;
+}
+
+// the stage constants the kernel reads for a group of W transforms, with a
+// padding shift per stage boundary chosen by the bank model
+MixedStages with_group(const MixedStages &st, int W, bool cols, int T) {
     MixedStages m = st;
     m.wlog = ilog2(W);
+    int elems = W * st.n;
     for (int s = 0; s < st.S; ++s) {
         m.mag_nb[s] = magic(st.nb[s]);
         m.mag_ns[s] = magic(st.ns[s]);
+        m.pad[s] = 0;
+        if (s + 1 < st.S) {
+            long long best = boundary_cost(st, s, W, cols, T, 0);
+            for (int ps : {5, 4, 3}) {
+                // both buffers, padded, within one CTA's shared memory
+                if ((size_t)2 * (W * st.n + ((W * st.n - 1) >> ps)) * sizeof(float2) > kMixedMaxSmem) continue;
+                const long long c = boundary_cost(st, s, W, cols, T, ps);
+                if (c < best) {
+                    best = c;
+                    m.pad[s] = ps;
+                }
+            }
+            const int e = W * st.n + ((W * st.n - 1) >> (m.pad[s] ? m.pad[s] : 31));
+            if (m.pad[s] && e > elems) elems = e;
+        }
     }
+    m.buf_elems = elems;
     return m;
 }
 
@@ -312,38 +389,35 @@ int mixed_cols_width(int n, int nx) {
     return 1;
 }
 
-cudaError_t launch_mixed_rows(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out,
-                              long long rows, int conj, cudaStream_t s) {
-    if (rows <= 0) return cudaSuccess;
-    const int W = mixed_rows_per_cta(st.n);
-    const size_t smem = (size_t)2 * W * st.n * sizeof(float2);
-    if (smem > kMixedMaxSmem) return cudaErrorInvalidValue;
-    const void *fn = (const void *)k_mixed<false>;
-    if (!smem_ok(fn, smem)) return cudaErrorInvalidValue;
-    const long long grid = (rows + W - 1) / W;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const MixedStages m = with_group(st, W);
-    const int nx = 0;
-    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&m, (void *)&rows, (void *)&W, (void *)&nx,
-                    (void *)&conj};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(mixed_threads(W * st.n)), args, smem, s);
+int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out) {
+    MixedLaunch L;
+    L.cols = cols;
+    L.nx = cols ? nx : 0;
+    L.W = cols ? mixed_cols_width(st.n, nx) : mixed_rows_per_cta(st.n);
+    if (cols && (nx <= 0 || nx % L.W)) return -1;
+    L.T = mixed_threads(L.W * st.n);
+    L.m = with_group(st, L.W, cols, L.T);
+    L.smem = (size_t)2 * L.m.buf_elems * sizeof(float2);
+    if (L.smem > kMixedMaxSmem) return -1;
+    const void *fn = cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>;
+    if (!smem_ok(fn, L.smem)) return -1;
+    *out = L;
+    return 0;
 }
 
-cudaError_t launch_mixed_cols(const MixedStages &st, const float2 *tw, const float2 *in, float2 *out, int nx,
-                              long long slices, int conj, cudaStream_t s) {
-    if (slices <= 0 || nx <= 0) return cudaSuccess;
-    const int W = mixed_cols_width(st.n, nx);
-    const size_t smem = (size_t)2 * W * st.n * sizeof(float2);
-    if (nx % W || smem > kMixedMaxSmem) return cudaErrorInvalidValue;
-    const void *fn = (const void *)k_mixed<true>;
-    if (!smem_ok(fn, smem)) return cudaErrorInvalidValue;
-    long long ntrans = slices * nx;
-    const long long grid = ntrans / W;
+cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *in, float2 *out, long long count,
+                         int conj, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (L.T <= 0) return cudaErrorInvalidValue;
+    // rows: count transforms; columns: count slices of nx columns
+    long long ntrans = L.cols ? count * L.nx : count;
+    const long long grid = (ntrans + L.W - 1) / L.W;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const MixedStages m = with_group(st, W);
-    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&m, (void *)&ntrans, (void *)&W, (void *)&nx,
-                    (void *)&conj};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(mixed_threads(W * st.n)), args, smem, s);
+    const void *fn = L.cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>;
+    int W = L.W, nx = L.nx;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&L.m, (void *)&ntrans, (void *)&W,
+                    (void *)&nx, (void *)&conj};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(L.T), args, L.smem, s);
 }
 
 }  // namespace gb300fft

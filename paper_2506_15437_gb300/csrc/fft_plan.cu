@@ -429,7 +429,8 @@ long long next_pow2(long long v) {
 }
 
 // mixed-radix stages for this length, unless GB300FFT_MIXED=0 (tests and
-// experiments compare against Bluestein)
+// experiments compare against Bluestein).  A mixed-radix axis given
+// `cols_nx` > 0 runs down the columns of [n][cols_nx] slices.
 bool use_mixed(int n, MixedStages *st) {
     const char *ev = getenv("GB300FFT_MIXED");
     if (ev && atoi(ev) == 0) return false;
@@ -440,7 +441,7 @@ bool use_mixed(int n, MixedStages *st) {
 // gets a dense sub-plan of its own; a 7-smooth n up to kMixedMaxN the
 // mixed-radix kernel; any other n Bluestein over a length-M power-of-two
 // sub-plan, M >= 2n - 1, with the chirps and the filter transforms built here.
-int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
+int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_nx = 0) {
     ax.n = n;
     ax.rows = rows;
     int rc = FFT_OK;
@@ -452,6 +453,7 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows) {
         ax.mixed = true;
         ax.mtw = dev_alloc<float2>(p, ax.mst.tw_size > 0 ? ax.mst.tw_size : 1);
         if (!ax.mtw) return FFT_ERR_ALLOC;
+        if (mixed_prepare(ax.mst, cols_nx > 0, cols_nx, &ax.ml) != 0) return FFT_ERR_UNSUPPORTED;
         return build_mixed_twiddles(ax.mtw, ax.mst, 0) == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
     }
     ax.M = (int)next_pow2(2LL * n - 1);
@@ -513,8 +515,8 @@ fft_plan_s *create_any(int nx, int ny, int batch, int dir, int *rc_out) {
             rc = setup_any_axis(p, ap->x, nx == 1 ? ny : nx, batch);
         } else {
             rc = setup_any_axis(p, ap->x, nx, (long long)ny * batch);
-            if (rc == FFT_OK) rc = setup_any_axis(p, ap->y, ny, (long long)nx * batch);
             // a mixed-radix y axis runs down the columns in place
+            if (rc == FFT_OK) rc = setup_any_axis(p, ap->y, ny, (long long)nx * batch, nx);
             ap->y_cols = rc == FFT_OK && ap->y.mixed;
             if (rc == FFT_OK && !ap->y_cols) {
                 ap->t = dev_alloc<float2>(p, (size_t)nx * ny * batch);
@@ -574,9 +576,8 @@ void free_plan(fft_plan_s *p) {
 // rows transforms of length ax.n along contiguous rows, in -> out (may alias)
 int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStream_t s) {
     if (ax.mixed)
-        return launch_mixed_rows(ax.mst, ax.mtw, in, out, ax.rows, sign > 0 ? 1 : 0, s) == cudaSuccess
-                   ? FFT_OK
-                   : FFT_ERR_CUDA;
+        return launch_mixed(ax.ml, ax.mtw, in, out, ax.rows, sign > 0 ? 1 : 0, s) == cudaSuccess ? FFT_OK
+                                                                                                : FFT_ERR_CUDA;
     if (!ax.M) return run_dense(ax.sub, in, out, sign, nullptr, 1.f, s);
     const int d = sign > 0 ? 1 : 0;
     if (ax.fused) {
@@ -603,7 +604,7 @@ int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_
     if (rc != FFT_OK) return rc;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
     if (ap.y_cols) {
-        if (launch_mixed_cols(ap.y.mst, ap.y.mtw, dst, dst, p->nx, p->batch, sign > 0 ? 1 : 0, s) != cudaSuccess)
+        if (launch_mixed(ap.y.ml, ap.y.mtw, dst, dst, p->batch, sign > 0 ? 1 : 0, s) != cudaSuccess)
             return FFT_ERR_CUDA;
     } else if (p->nx > 1 && p->ny > 1) {
         const long long batch = p->batch;
