@@ -2,8 +2,9 @@
 //
 // The paper's kernels take powers of two only and name uneven sizes as
 // further work (Sections 6 and 7).  Smooth lengths up to kMixedMaxN run here
-// as a Stockham autosort transform whose stages have radix 8, 4, 2, 3, 5 or 7,
-// chosen at plan time: stage s of radix R, with Ns the product of the radices
+// as a Stockham autosort transform whose stages have radix 16, 8, 4, 2, 15,
+// 9, 3, 5 or 7, chosen at plan time (15 and 9 are two-level DFTs in
+// registers with compile-time inner twiddles): stage s of radix R, with Ns the product of the radices
 // before it, takes butterfly j (k = j mod Ns) from elements j + r n/R,
 // multiplies leg r by w_{Ns R}^{k r}, runs an R-point DFT and writes leg r to
 // element (j - k) R + k + r Ns.  After the last stage the output is in natural
@@ -22,16 +23,36 @@ namespace gb300fft {
 
 namespace {
 
-// cos(2 pi j / R) and sin(2 pi j / R) for 1 <= j <= (R-1)/2, R in {3, 5, 7}
-__host__ __device__ constexpr float cos_r(int R, int j) {
-    return R == 3   ? -0.5f
-           : R == 5 ? (j == 1 ? 0.30901699437494742f : -0.80901699437494742f)
-                    : (j == 1 ? 0.62348980185873353f : j == 2 ? -0.22252093395631440f : -0.90096886790241913f);
+// cos and sin of 2 pi m / R, evaluated by the compiler: the angle is split
+// in integers into a quadrant k (multiples of pi/2) and a remainder phi in
+// [0, pi/2), whose sine and cosine are Taylor series summed in double (error
+// below 1e-15; exactly 0 and +-1 on the axes), then rounded once to float.
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
 }
-__host__ __device__ constexpr float sin_r(int R, int j) {
-    return R == 3   ? 0.86602540378443865f
-           : R == 5 ? (j == 1 ? 0.95105651629515357f : 0.58778525229247313f)
-                    : (j == 1 ? 0.78183148246802981f : j == 2 ? 0.97492791218182361f : 0.43388373911755812f);
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double cos_2pi(int m, int R) {
+    const long long q = ((long long)(m % R) + R) % R, t = 4 * q, k = t / R, rem = t - k * R;
+    const double phi = (kPiD / 2) * (double)rem / (double)R;
+    return k == 0 ? taylor_cos(phi) : k == 1 ? -taylor_sin(phi) : k == 2 ? -taylor_cos(phi) : taylor_sin(phi);
+}
+__host__ __device__ constexpr double sin_2pi(int m, int R) {
+    const long long q = ((long long)(m % R) + R) % R, t = 4 * q, k = t / R, rem = t - k * R;
+    const double phi = (kPiD / 2) * (double)rem / (double)R;
+    return k == 0 ? taylor_sin(phi) : k == 1 ? taylor_cos(phi) : k == 2 ? -taylor_sin(phi) : -taylor_cos(phi);
 }
 
 // Forward R-point DFT for odd prime R, legs paired as (k, R - k):
@@ -59,8 +80,8 @@ __device__ __forceinline__ void dft_odd(float2 *a) {
         for (int k = 1; k <= H; ++k) {
             const int q = (k * m) % R;  // angle index, folded into 1 .. H
             const int j = q <= H ? q : R - q;
-            const float c = cos_r(R, j);
-            const float sn = q <= H ? sin_r(R, j) : -sin_r(R, j);
+            const float c = (float)cos_2pi(j, R);
+            const float sn = q <= H ? (float)sin_2pi(j, R) : -(float)sin_2pi(j, R);
             A = make_float2(fmaf(c, t[k - 1].x, A.x), fmaf(c, t[k - 1].y, A.y));
             B = make_float2(fmaf(sn, d[k - 1].x, B.x), fmaf(sn, d[k - 1].y, B.y));
         }
@@ -72,9 +93,66 @@ __device__ __forceinline__ void dft_odd(float2 *a) {
     for (int k = 0; k < R; ++k) a[k] = y[k];
 }
 
+// x * w_R^M with w_R = exp(-2 pi i / R); powers of -i are exact swaps
+template <int M, int R>
+__device__ __forceinline__ float2 mul_w(float2 x) {
+    if constexpr ((4 * M) % R == 0) {
+        constexpr int k = ((4 * M) / R) % 4;
+        if constexpr (k == 0) return x;
+        else if constexpr (k == 1) return make_float2(x.y, -x.x);
+        else if constexpr (k == 2) return make_float2(-x.x, -x.y);
+        else return make_float2(-x.y, x.x);
+    } else {
+        constexpr float wr = (float)cos_2pi(M, R), wi = (float)-sin_2pi(M, R);
+        return make_float2(fmaf(x.x, wr, -x.y * wi), fmaf(x.x, wi, x.y * wr));
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void dft_any(float2 *a);
+
+// R = R1 R2 points in registers, natural order in and out: with input index
+// i2 + R2 i1 and output index k1 + R1 k2, w_R^{ik} = w_R1^{i1 k1} w_R^{i2 k1}
+// w_R2^{i2 k2}, so: R2 transforms of length R1 (over i1), the inner twiddles
+// w_R^{i2 k1} (compile-time constants), R1 transforms of length R2 (over i2).
+template <int R1, int R2, int I2, int K1>
+__device__ __forceinline__ void dft_2lvl_tw(const float2 *t, float2 *b) {
+    if constexpr (K1 < R1) {
+        b[I2 * R1 + K1] = mul_w<I2 * K1, R1 * R2>(t[K1]);
+        dft_2lvl_tw<R1, R2, I2, K1 + 1>(t, b);
+    }
+}
+template <int R1, int R2, int I2 = 0>
+__device__ __forceinline__ void dft_2lvl_cols(const float2 *a, float2 *b) {
+    if constexpr (I2 < R2) {
+        float2 t[R1];
+#pragma unroll
+        for (int i1 = 0; i1 < R1; ++i1) t[i1] = a[I2 + R2 * i1];
+        dft_any<R1>(t);
+        dft_2lvl_tw<R1, R2, I2, 0>(t, b);
+        dft_2lvl_cols<R1, R2, I2 + 1>(a, b);
+    }
+}
+template <int R1, int R2>
+__device__ __forceinline__ void dft_2lvl(float2 *a) {
+    float2 b[R1 * R2];
+    dft_2lvl_cols<R1, R2>(a, b);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 t[R2];
+#pragma unroll
+        for (int i2 = 0; i2 < R2; ++i2) t[i2] = b[i2 * R1 + k1];
+        dft_any<R2>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = t[k2];
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void dft_any(float2 *a) {
     if constexpr ((R & (R - 1)) == 0) dft<R>(a);
+    else if constexpr (R == 9) dft_2lvl<3, 3>(a);
+    else if constexpr (R == 15) dft_2lvl<3, 5>(a);
     else dft_odd<R>(a);
 }
 
@@ -168,12 +246,15 @@ __device__ __forceinline__ void mixed_dispatch(int R, const MixedGeom &g, const 
         case 4: mixed_stage<4, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
         case 5: mixed_stage<5, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
         case 7: mixed_stage<7, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        default: mixed_stage<8, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 8: mixed_stage<8, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 9: mixed_stage<9, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 15: mixed_stage<15, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        default: mixed_stage<16, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
     }
 }
 
 template <bool COLS>
-__global__ void __launch_bounds__(512) k_mixed(const float2 *in, float2 *out, const float2 *__restrict__ tw,
+__global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, const float2 *__restrict__ tw,
                                                const MixedStages st, long long ntrans, int W, int nx, int conj) {
     extern __shared__ __align__(16) float2 mbuf[];
     MixedGeom g;
@@ -233,6 +314,8 @@ __global__ void k_mixed_twiddles(float2 *t, int Ns, int R) {
     t[e] = make_float2((float)cv, (float)(-sv));
 }
 
+const void *mixed_fn(bool cols) { return cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>; }
+
 bool smem_ok(const void *fn, size_t smem) {
     if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                                 cudaSuccess)
@@ -242,8 +325,10 @@ bool smem_ok(const void *fn, size_t smem) {
 
 uint32_t magic(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d - 1) / (uint64_t)d); }
 
-// Threads for a group of W transforms of total length W n.
-int mixed_threads(int elems) { return elems > 4096 ? 512 : 256; }
+// Threads for a group of W transforms of total length W n: a group longer
+// than 8192 points fills one SM's shared memory alone, so it brings the
+// most threads it can.
+int mixed_threads(int elems) { return elems > 8192 ? 1024 : elems > 4096 ? 512 : 256; }
 
 // Shared-memory wavefronts of one access pattern under the half-warp model
 // for 8-byte words: the 16 lanes of a half-warp form one wavefront per
@@ -339,13 +424,29 @@ bool mixed_factor(int n, MixedStages *st) {
         rest /= R;
         return true;
     };
-    while (rest % 8 == 0)
-        if (!push(8)) return false;
-    if (rest % 4 == 0 && !push(4)) return false;
-    if (rest % 2 == 0 && !push(2)) return false;
-    for (int R : {3, 5, 7})
-        while (rest % R == 0)
-            if (!push(R)) return false;
+    // powers of two: 16s, then one 8, 4 or 2; odd part: 3 * 5 and 3 * 3 in
+    // one register stage each, then single 3, 5, 7 (a 25-point stage needs
+    // twice the registers of a 16-point one and halves the CTAs per SM:
+    // measured slower than two 5-point stages)
+    int e3 = 0, e5 = 0;
+    for (int t = rest; t % 3 == 0; t /= 3) ++e3;
+    for (int t = rest; t % 5 == 0; t /= 5) ++e5;
+    while (rest % 16 == 0)
+        if (!push(16)) return false;
+    for (int R : {8, 4, 2})
+        if (rest % R == 0 && !push(R)) return false;
+    if (e5 >= 1 && e3 >= 1) {
+        if (!push(15)) return false;
+        --e5;
+        --e3;
+    }
+    for (; e3 >= 2; e3 -= 2)
+        if (!push(9)) return false;
+    if (e3 == 1 && !push(3)) return false;
+    for (; e5 >= 1; --e5)
+        if (!push(5)) return false;
+    while (rest % 7 == 0)
+        if (!push(7)) return false;
     if (rest != 1) return false;
     m.S = S;
     int off = 0, Ns = 1;
@@ -399,8 +500,7 @@ int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out) {
     L.m = with_group(st, L.W, cols, L.T);
     L.smem = (size_t)2 * L.m.buf_elems * sizeof(float2);
     if (L.smem > kMixedMaxSmem) return -1;
-    const void *fn = cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>;
-    if (!smem_ok(fn, L.smem)) return -1;
+    if (!smem_ok(mixed_fn(cols), L.smem)) return -1;
     *out = L;
     return 0;
 }
@@ -413,7 +513,7 @@ cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *i
     long long ntrans = L.cols ? count * L.nx : count;
     const long long grid = (ntrans + L.W - 1) / L.W;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const void *fn = L.cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>;
+    const void *fn = mixed_fn(L.cols);
     int W = L.W, nx = L.nx;
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&L.m, (void *)&ntrans, (void *)&W,
                     (void *)&nx, (void *)&conj};
