@@ -337,26 +337,27 @@ def energy_form(torch, g, dev):
 def any_size_form(torch, g, steps, dev):
     """Sizes that are not powers of two.  7-smooth lengths take the
     mixed-radix kernel (one HBM pass per axis: 1000 x 1000 beside the
-    paper's 1024 x 1024, 1920 x 1080, 16384 signals of 3000 points); other
-    lengths Bluestein over the power-of-two path (10^6 points in 1D, which
-    is smooth but longer than one CTA holds, and 16384 signals of 4095
-    points).  GFLOP/s uses the nominal 5 N log2 N of the transform's own
-    size; the HBM figure counts one read and one write per axis."""
+    paper's 1024 x 1024, 1920 x 1080, 16384 signals of 3000 points), or,
+    longer than one CTA holds, its four-step form (two passes: 32 signals
+    of 10^6 points); other lengths Bluestein over the power-of-two path
+    (16384 signals of 4095 = 3^2 5 7 13 points).  GFLOP/s uses the nominal
+    5 N log2 N of the transform's own size; the HBM figure counts one read
+    and one write per axis or pass."""
     import math
     import synth
     out = {}
-    for nx, ny, b in ((1000, 1000, 1), (1920, 1080, 1), (3000, 1, 16384), (1_000_000, 1, 1), (4095, 1, 16384)):
+    for nx, ny, b in ((1000, 1000, 1), (1920, 1080, 1), (3000, 1, 16384), (1_000_000, 1, 32), (4095, 1, 16384)):
         x = torch.from_numpy(synth.uniform_complex((b, ny, nx), seed=SEED)).to(dev)
         y = torch.empty_like(x)
         plan = g.get_plan(nx, ny, b, False, "fp32", dev)
         ms, _ = time_plan(torch, plan, x, y, max(10, steps // 4), 3)
         n = nx * ny
         d = plan.describe()
-        axes = 2 if ny > 1 else 1
+        axes = 2 if ny > 1 or d["x"]["mixed_fourstep"][0] else 1
         out[f"fp32_any_{nx}x{ny}x{b}"] = {
             "ms": ms, "GFLOP/s_nominal": 5.0 * n * math.log2(n) * b / ms / 1e6,
             "HBM_GB/s_algorithmic": 16.0 * axes * n * b / ms / 1e6,
-            "mixed": [d["x"]["mixed"], d["y"]["mixed"]],
+            "mixed": [d["x"]["mixed"], d["y"]["mixed"]], "mixed_fourstep": d["x"]["mixed_fourstep"],
             "bluestein_m": [d["x"]["bluestein_m"], d["y"]["bluestein_m"]], "transposes": d["transposes"]}
         del x, y
     return out

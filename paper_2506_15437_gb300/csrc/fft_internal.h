@@ -229,6 +229,17 @@ struct MixedStages {
     uint32_t mag_nb[kMixedMaxStages] = {}, mag_ns[kMixedMaxStages] = {};  // ceil(2^32 / d) divisors
     int tw_off[kMixedMaxStages] = {};  // stage s's twiddles w_{Ns R}^{k r} at tw_off[s] + k (R - 1) + r - 1
 };
+// Second pass of a mixed-radix four-step transform (n = n1 n2): row k1 of
+// the first pass's output is multiplied by w_n^{i2 k1} as it is loaded and
+// its outputs k2 are stored at k1 + n1 k2.
+struct FourStepB {
+    const float2 *hi = nullptr, *lo = nullptr;  // w_n^{t 2^lshift}, w_n^u (u < 2^lshift)
+    int n1 = 0;      // rows per transform (0: not a four-step pass)
+    int k1 = 0;      // set per CTA in the kernel
+    int lshift = 0, lmask = 0;
+    int stride = 0;  // staged row stride in shared memory (n2 rounded up to odd)
+};
+
 // Launch configuration of the mixed-radix kernel for one axis, fixed at
 // plan creation: transforms per CTA, threads, padded buffers.
 struct MixedLaunch {
@@ -237,12 +248,18 @@ struct MixedLaunch {
     int nx = 0;  // columns: row length of the [ny][nx] slices
     int W = 1, T = 0;
     size_t smem = 0;
+    FourStepB fs;
 };
 bool mixed_factor(int n, MixedStages *st);  // false unless n = 2^a 3^b 5^c 7^d <= kMixedMaxN
 cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s);
 int mixed_rows_per_cta(int n);
 int mixed_cols_width(int n, int nx);
-int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out);  // 0 on success
+// 0 on success; fs_n1 > 0: the second pass of a four-step transform with
+// n1 rows per transform (rows layout)
+int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, int fs_n1 = 0);
+// n = n1 n2 with both factors mixed-radix lengths (<= kMixedMaxN), n1 and
+// n2 as close as possible; false if none
+bool mixed_split(int n, int *n1, int *n2);
 // rows: `count` transforms along contiguous rows; columns: `count` [n][nx] slices
 cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *in, float2 *out, long long count,
                          int conj, cudaStream_t s);
@@ -251,6 +268,10 @@ struct AnyAxis {
     bool mixed = false;                 // 7-smooth n: the mixed-radix kernel, no padding
     MixedStages mst;
     MixedLaunch ml;                     // rows, or (the y axis of a 2D plan) columns
+    bool mfs = false;                   // 7-smooth n > kMixedMaxN: mixed-radix four-step
+    int n1 = 0, n2 = 0;                 // n = n1 n2: columns of length n1, then rows of n2
+    MixedLaunch mla, mlb;               // the two passes
+    float2 *mtwa = nullptr, *mtwb = nullptr, *fs_hi = nullptr, *fs_lo = nullptr, *fs_work = nullptr;
     float2 *mtw = nullptr;              // mixed-radix twiddles (forward)
     const BluVariant *fused = nullptr;  // M <= 8192: fused kernels (same E as the sub-plan's row pass)
     int n = 1, M = 0;

@@ -16,6 +16,8 @@
 // they are short) and columns (the transforms of W adjacent columns of an
 // [ny][nx] slice, element i of column x at i*nx + x), which serves the y axis
 // of a 2D plan without a transpose.
+#include <math.h>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -187,10 +189,10 @@ __device__ __forceinline__ int padx(int x, int ps) { return x + (x >> ps); }
 // transform fastest (W adjacent columns of a row together).  Local layout:
 // rows [c][i], columns [i][c].  `gin` and `gout` point at the CTA's first
 // transform, so every offset within the group fits 32 bits.
-template <int R, bool COLS, bool FIRST, bool LAST>
+template <int R, bool COLS, bool FIRST, bool LAST, bool FS>
 __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs a, const float2 *src, float2 *dst,
                                             const float2 *gin, float2 *gout, const float2 *__restrict__ tws,
-                                            float si) {
+                                            float si, const FourStepB &fs) {
     const int nb = a.nb, Ns = a.Ns;
     const int total = g.nv * nb;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -210,6 +212,12 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
             if (FIRST) {
                 float2 x = gin[c * g.tstride + i * g.estride];
                 x.y *= si;
+                if (FS) {
+                    // four-step: element i2 = i of row k1 times w_n^{i2 k1}, from
+                    // the two factor tables w_n^a = hi[a >> L] lo[a & (2^L - 1)]
+                    const int e = i * (fs.k1 + c);
+                    x = cmul(x, cmul(__ldg(fs.hi + (e >> fs.lshift)), __ldg(fs.lo + (e & fs.lmask))));
+                }
                 v[r] = x;
             } else {
                 v[r] = src[padx(COLS ? i * g.W + c : c * g.n + i, a.pin)];
@@ -225,7 +233,9 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int o = o0 + r * Ns;
-            if (LAST) {
+            if (LAST && FS) {
+                dst[c * fs.stride + o] = v[r];  // staged: the CTA stores its rows transposed afterwards
+            } else if (LAST) {
                 float2 x = v[r];
                 x.y *= si;
                 gout[c * g.tstride + o * g.estride] = x;
@@ -236,26 +246,27 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
     }
 }
 
-template <bool COLS, bool FIRST, bool LAST>
+template <bool COLS, bool FIRST, bool LAST, bool FS>
 __device__ __forceinline__ void mixed_dispatch(int R, const MixedGeom &g, const StageArgs a, const float2 *src,
                                                float2 *dst, const float2 *gin, float2 *gout, const float2 *tws,
-                                               float si) {
+                                               float si, const FourStepB &fs) {
     switch (R) {
-        case 2: mixed_stage<2, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 3: mixed_stage<3, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 4: mixed_stage<4, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 5: mixed_stage<5, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 7: mixed_stage<7, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 8: mixed_stage<8, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 9: mixed_stage<9, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        case 15: mixed_stage<15, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
-        default: mixed_stage<16, COLS, FIRST, LAST>(g, a, src, dst, gin, gout, tws, si); break;
+        case 2: mixed_stage<2, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 3: mixed_stage<3, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 4: mixed_stage<4, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 5: mixed_stage<5, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 7: mixed_stage<7, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 8: mixed_stage<8, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 9: mixed_stage<9, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 15: mixed_stage<15, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        default: mixed_stage<16, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
     }
 }
 
-template <bool COLS>
+template <bool COLS, bool FS>
 __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, const float2 *__restrict__ tw,
-                                               const MixedStages st, long long ntrans, int W, int nx, int conj) {
+                                                const MixedStages st, long long ntrans, int W, int nx, int conj,
+                                                FourStepB fs) {
     extern __shared__ __align__(16) float2 mbuf[];
     MixedGeom g;
     g.n = st.n;
@@ -278,6 +289,13 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
     }
     const float2 *gin = in + base;
     float2 *gout = out + base;
+    long long fs_out = 0;
+    if (FS) {
+        // rows t0 .. t0 + W - 1 are rows k1 of one transform b (W divides n1)
+        const long long b = t0 / fs.n1;
+        fs.k1 = (int)(t0 - b * fs.n1);
+        fs_out = b * (long long)fs.n1 * st.n + fs.k1;
+    }
     const float si = conj ? -1.f : 1.f;
     float2 *A = mbuf, *B = mbuf + st.buf_elems;
     for (int s = 0; s < st.S; ++s) {
@@ -291,14 +309,25 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
         a.pout = st.pad[s] ? st.pad[s] : 31;
         const float2 *tws = tw + st.tw_off[s];
         const int R = st.radix[s];
-        if (st.S == 1) mixed_dispatch<COLS, true, true>(R, g, a, A, B, gin, gout, tws, si);
-        else if (s == 0) mixed_dispatch<COLS, true, false>(R, g, a, A, B, gin, gout, tws, si);
-        else if (s == st.S - 1) mixed_dispatch<COLS, false, true>(R, g, a, A, B, gin, gout, tws, si);
-        else mixed_dispatch<COLS, false, false>(R, g, a, A, B, gin, gout, tws, si);
+        if (st.S == 1) mixed_dispatch<COLS, true, true, FS>(R, g, a, A, B, gin, gout, tws, si, fs);
+        else if (s == 0) mixed_dispatch<COLS, true, false, FS>(R, g, a, A, B, gin, gout, tws, si, fs);
+        else if (s == st.S - 1) mixed_dispatch<COLS, false, true, FS>(R, g, a, A, B, gin, gout, tws, si, fs);
+        else mixed_dispatch<COLS, false, false, FS>(R, g, a, A, B, gin, gout, tws, si, fs);
         __syncthreads();
         float2 *tmp = A;
         A = B;
         B = tmp;
+    }
+    if (FS) {
+        // output k2 of row k1 goes to k1 + n1 k2: the W rows' outputs k2 are
+        // W adjacent elements, so a warp stores 32 / W runs of W elements
+        float2 *dstb = out + fs_out;
+        for (int idx = threadIdx.x; idx < W * st.n; idx += blockDim.x) {
+            const int c = idx & (W - 1), k2 = idx >> st.wlog;
+            float2 x = A[c * fs.stride + k2];
+            x.y *= si;
+            dstb[c + (long long)fs.n1 * k2] = x;
+        }
     }
 }
 
@@ -314,7 +343,10 @@ __global__ void k_mixed_twiddles(float2 *t, int Ns, int R) {
     t[e] = make_float2((float)cv, (float)(-sv));
 }
 
-const void *mixed_fn(bool cols) { return cols ? (const void *)k_mixed<true> : (const void *)k_mixed<false>; }
+const void *mixed_fn(bool cols, bool fs) {
+    return cols ? (const void *)k_mixed<true, false>
+                : fs ? (const void *)k_mixed<false, true> : (const void *)k_mixed<false, false>;
+}
 
 bool smem_ok(const void *fn, size_t smem) {
     if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -490,19 +522,51 @@ int mixed_cols_width(int n, int nx) {
     return 1;
 }
 
-int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out) {
+int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, int fs_n1) {
     MixedLaunch L;
     L.cols = cols;
     L.nx = cols ? nx : 0;
-    L.W = cols ? mixed_cols_width(st.n, nx) : mixed_rows_per_cta(st.n);
+    const bool fs = !cols && fs_n1 > 0;
+    if (fs) {
+        // W rows of one transform per CTA (W divides n1), staged with an odd
+        // row stride so the transposed reads spread over the banks
+        L.fs.n1 = fs_n1;
+        L.fs.stride = st.n | 1;
+        L.W = 1;
+        for (int W : {8, 4, 2})
+            if (fs_n1 % W == 0 && (size_t)2 * W * L.fs.stride * sizeof(float2) <= 72 * 1024) {
+                L.W = W;
+                break;
+            }
+    } else {
+        L.W = cols ? mixed_cols_width(st.n, nx) : mixed_rows_per_cta(st.n);
+    }
     if (cols && (nx <= 0 || nx % L.W)) return -1;
     L.T = mixed_threads(L.W * st.n);
     L.m = with_group(st, L.W, cols, L.T);
+    if (fs && L.m.buf_elems < L.W * L.fs.stride) L.m.buf_elems = L.W * L.fs.stride;
     L.smem = (size_t)2 * L.m.buf_elems * sizeof(float2);
     if (L.smem > kMixedMaxSmem) return -1;
-    if (!smem_ok(mixed_fn(cols), L.smem)) return -1;
+    if (!smem_ok(mixed_fn(cols, fs), L.smem)) return -1;
     *out = L;
     return 0;
+}
+
+bool mixed_split(int n, int *n1, int *n2) {
+    int best = 0;
+    double bd = 1e30;
+    for (int d = 2; d <= kMixedMaxN && d < n; ++d) {
+        if (n % d || n / d > kMixedMaxN || !mixed_factor(d, nullptr) || !mixed_factor(n / d, nullptr)) continue;
+        const double dist = fabs(log((double)d) - 0.5 * log((double)n));
+        if (dist < bd) {
+            bd = dist;
+            best = d;
+        }
+    }
+    if (!best) return false;
+    *n2 = best;
+    *n1 = n / best;
+    return true;
 }
 
 cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *in, float2 *out, long long count,
@@ -513,10 +577,11 @@ cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *i
     long long ntrans = L.cols ? count * L.nx : count;
     const long long grid = (ntrans + L.W - 1) / L.W;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const void *fn = mixed_fn(L.cols);
+    const void *fn = mixed_fn(L.cols, L.fs.n1 > 0);
     int W = L.W, nx = L.nx;
+    FourStepB fs = L.fs;
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&L.m, (void *)&ntrans, (void *)&W,
-                    (void *)&nx, (void *)&conj};
+                    (void *)&nx, (void *)&conj, (void *)&fs};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(L.T), args, L.smem, s);
 }
 

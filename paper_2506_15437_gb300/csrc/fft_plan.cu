@@ -437,6 +437,14 @@ bool use_mixed(int n, MixedStages *st) {
     return !is_pow2(n) && mixed_factor(n, st);
 }
 
+// a 7-smooth length beyond one CTA that splits into two mixed-radix lengths,
+// unless GB300FFT_MIXED=0
+bool use_mixed_fourstep(int n, int *n1, int *n2) {
+    const char *ev = getenv("GB300FFT_MIXED");
+    if (ev && atoi(ev) == 0) return false;
+    return !is_pow2(n) && n > kMixedMaxN && mixed_split(n, n1, n2);
+}
+
 // One axis of an any-size plan: rows transforms of length n.  A power of two
 // gets a dense sub-plan of its own; a 7-smooth n up to kMixedMaxN the
 // mixed-radix kernel; any other n Bluestein over a length-M power-of-two
@@ -455,6 +463,34 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_n
         if (!ax.mtw) return FFT_ERR_ALLOC;
         if (mixed_prepare(ax.mst, cols_nx > 0, cols_nx, &ax.ml) != 0) return FFT_ERR_UNSUPPORTED;
         return build_mixed_twiddles(ax.mtw, ax.mst, 0) == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+    }
+    // a longer smooth length: four-step over two mixed-radix passes (columns
+    // of length n1 into a workspace, then rows of length n2 with the
+    // inter-pass twiddle on load and a transposed store)
+    if (use_mixed_fourstep(n, &ax.n1, &ax.n2)) {
+        MixedStages sa, sb;
+        if (!mixed_factor(ax.n1, &sa) || !mixed_factor(ax.n2, &sb)) return FFT_ERR_UNSUPPORTED;
+        if (mixed_prepare(sa, true, ax.n2, &ax.mla) != 0 || mixed_prepare(sb, false, 0, &ax.mlb, ax.n1) != 0)
+            return FFT_ERR_UNSUPPORTED;
+        int lshift = 0;
+        while ((1LL << (2 * lshift)) < n) ++lshift;  // 2^lshift >= sqrt(n)
+        const int nlo = 1 << lshift, nhi = (int)((n + nlo - 1) / nlo);
+        ax.mtwa = dev_alloc<float2>(p, sa.tw_size > 0 ? sa.tw_size : 1);
+        ax.mtwb = dev_alloc<float2>(p, sb.tw_size > 0 ? sb.tw_size : 1);
+        ax.fs_lo = dev_alloc<float2>(p, nlo);
+        ax.fs_hi = dev_alloc<float2>(p, nhi);
+        ax.fs_work = dev_alloc<float2>(p, (size_t)rows * n);
+        if (!ax.mtwa || !ax.mtwb || !ax.fs_lo || !ax.fs_hi || !ax.fs_work) return FFT_ERR_ALLOC;
+        if (build_mixed_twiddles(ax.mtwa, sa, 0) != cudaSuccess || build_mixed_twiddles(ax.mtwb, sb, 0) != cudaSuccess ||
+            build_roots_strided(ax.fs_lo, nlo, n, 1, 0) != cudaSuccess ||
+            build_roots_strided(ax.fs_hi, nhi, n, nlo, 0) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        ax.mlb.fs.hi = ax.fs_hi;
+        ax.mlb.fs.lo = ax.fs_lo;
+        ax.mlb.fs.lshift = lshift;
+        ax.mlb.fs.lmask = nlo - 1;
+        ax.mfs = true;
+        return FFT_OK;
     }
     ax.M = (int)next_pow2(2LL * n - 1);
     if (rows * ax.M > (1LL << 31)) return FFT_ERR_INVALID_SIZE;
@@ -575,6 +611,13 @@ void free_plan(fft_plan_s *p) {
 
 // rows transforms of length ax.n along contiguous rows, in -> out (may alias)
 int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStream_t s) {
+    if (ax.mfs) {
+        const int cj = sign > 0 ? 1 : 0;  // conj(F(conj x)): each pass conjugates its loads and stores
+        if (launch_mixed(ax.mla, ax.mtwa, in, ax.fs_work, ax.rows, cj, s) != cudaSuccess ||
+            launch_mixed(ax.mlb, ax.mtwb, ax.fs_work, out, ax.rows * ax.n1, cj, s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
     if (ax.mixed)
         return launch_mixed(ax.ml, ax.mtw, in, out, ax.rows, sign > 0 ? 1 : 0, s) == cudaSuccess ? FFT_OK
                                                                                                 : FFT_ERR_CUDA;
@@ -1086,10 +1129,12 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
         const gb300fft::AnyPlan &ap = *p->any;
         k = snprintf(tmp, sizeof tmp,
                      "{\"kind\": \"any\", \"precision\": \"fp32\", \"x\": {\"n\": %d, \"bluestein_m\": %d, "
-                     "\"fused\": %d, \"mixed\": %d}, \"y\": {\"n\": %d, \"bluestein_m\": %d, \"fused\": %d, "
-                     "\"mixed\": %d}, \"transposes\": %d}",
-                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.x.mixed ? 1 : 0, ap.y.n, ap.y.M, ap.y.fused ? 1 : 0,
-                     ap.y.mixed ? 1 : 0, (p->nx > 1 && p->ny > 1 && !ap.y_cols) ? 2 : 0);
+                     "\"fused\": %d, \"mixed\": %d, \"mixed_fourstep\": [%d, %d]}, \"y\": {\"n\": %d, "
+                     "\"bluestein_m\": %d, \"fused\": %d, \"mixed\": %d, \"mixed_fourstep\": [%d, %d]}, "
+                     "\"transposes\": %d}",
+                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.x.mixed ? 1 : 0, ap.x.n1, ap.x.n2, ap.y.n, ap.y.M,
+                     ap.y.fused ? 1 : 0, ap.y.mixed ? 1 : 0, ap.y.n1, ap.y.n2,
+                     (p->nx > 1 && p->ny > 1 && !ap.y_cols) ? 2 : 0);
     } else if (p->fs.n1 > 0) {
         const gb300fft::FourStepPlan &fs = p->fs;
         char ra[96], rb[96];

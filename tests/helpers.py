@@ -91,15 +91,26 @@ def tol_mixed_axis(n: int) -> float:
     return 2e-7 * (math.log2(n) + odd_factors(n))
 
 
+def mixed_fourstep_eligible(n: int) -> bool:
+    """Longer 7-smooth lengths (not powers of two): two mixed-radix passes
+    of a four-step split (every such length up to 2^24 has a divisor
+    between n / MIXED_MAX_N and MIXED_MAX_N)."""
+    return n & (n - 1) != 0 and MIXED_MAX_N < n <= (1 << 24) and odd_factors(n) >= 0
+
+
 def tol_any_axis(n: int, mixed: bool = True) -> float:
     """FP32 bound for one axis of any length: a power of two is the plain
     path (2e-7 * log2 n); a 7-smooth length up to MIXED_MAX_N the mixed-radix
-    kernel (unless `mixed` is False: the plan was made with it switched off);
-    any other length Bluestein."""
+    kernel, a longer one its four-step form (two more levels: the inter-pass
+    twiddle is the product of two rounded table entries), unless `mixed` is
+    False (the plan was made with it switched off); any other length
+    Bluestein."""
     if n & (n - 1) == 0:
         return 2e-7 * max(1.0, math.log2(n))
     if mixed and mixed_eligible(n):
         return tol_mixed_axis(n)
+    if mixed and mixed_fourstep_eligible(n):
+        return tol_mixed_axis(n) + 2 * 2e-7
     return tol_bluestein_axis(n)
 
 

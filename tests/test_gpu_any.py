@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from tests.helpers import ORACLE_THREADS, mixed_eligible, tol_any, worst_rel_l2
+from tests.helpers import ORACLE_THREADS, mixed_eligible, mixed_fourstep_eligible, tol_any, worst_rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,14 +83,51 @@ def test_fft2_autograd_any_shape(g):
     assert worst_rel_l2(x.grad.cpu().numpy(), ref, nx * ny) <= 2 * tol_any(nx, ny)
 
 
-def test_long_1d_million_points(g):
-    n = 1_000_000  # 2^6 * 5^6: Bluestein over the four-step path (M = 2^21)
+def test_long_1d_million_points(g, monkeypatch):
+    """10^6 = 2^6 5^6: the mixed-radix four-step (1000 x 1000); with mixed
+    radix switched off, Bluestein over the power-of-two four-step path
+    (M = 2^21)."""
+    n = 1_000_000
     x = synth.uniform_complex((1, n), seed=2506)
-    plan = g.get_plan(n, 1, 1, False, "fp32", "cuda")
-    assert plan.describe()["x"]["bluestein_m"] == 1 << 21
-    got = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.fft1d_any(x, threads=ORACLE_THREADS)
+    plan = g.Plan(n, 1, 1)
+    assert plan.describe()["x"]["mixed_fourstep"] == [1000, 1000]
+    got = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
     assert worst_rel_l2(got, ref, n) <= tol_any(n, 1)
+    monkeypatch.setenv("GB300FFT_MIXED", "0")
+    blu = g.Plan(n, 1, 1)
+    monkeypatch.delenv("GB300FFT_MIXED")
+    assert blu.describe()["x"]["bluestein_m"] == 1 << 21
+    got = blu.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert worst_rel_l2(got, ref, n) <= tol_any(n, 1, mixed=False)
+    plan.close()
+    blu.close()
+
+
+# Smooth lengths beyond one CTA: the mixed-radix four-step.  Prime powers
+# (5^7, 7^6, 3^10), a power of two times 3, 15 and 9 stages, and the
+# longest balanced case below 2^24.
+MIXED_FS = [(15360, 3), (20000, 2), (78125, 2), (117649, 1), (59049, 1), (3 << 20, 1), (2 ** 9 * 3 ** 9, 1)]
+
+
+@pytest.mark.parametrize("n,batch", MIXED_FS, ids=[f"{a}x{b}" for a, b in MIXED_FS])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_mixed_radix_fourstep(g, n, batch, inverse):
+    assert mixed_fourstep_eligible(n)
+    x = synth.uniform_complex((batch, n), seed=n % 9973)
+    plan = g.Plan(n, 1, batch, inverse=inverse)
+    n1, n2 = plan.describe()["x"]["mixed_fourstep"]
+    assert n1 * n2 == n and max(n1, n2) <= 14336
+    d = torch.from_numpy(x).cuda()
+    got = plan.execute(d).cpu().numpy()
+    ref = oracle.fft1d_any(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    err = worst_rel_l2(got, ref, n)
+    print(f"mixedfs n={n} ({n1}x{n2}) inverse={inverse} err={err:.3e} tol={tol_any(n, 1):.3e}")
+    assert err <= tol_any(n, 1), n
+    plan.execute(d, out=d)  # in place: the first pass reads the input, the second writes it
+    assert np.array_equal(d.cpu().numpy(), got)
+    assert plan.status() == 0
+    plan.close()
 
 
 @pytest.mark.parametrize("n", [5, 100, 1000, 4095])
