@@ -198,9 +198,10 @@ def test_mixed_radix_1d(g, n, inverse):
 
 
 # (ny, nx): y by the column kernel with 8, 4, 2 or 1 adjacent columns (odd
-# nx), x mixed or a power of two or Bluestein, y longest at 14336
+# nx), x mixed or a power of two or Bluestein, y longest at 14336; axes
+# longer than 14336 by the four-step form (x directly, y between transposes)
 MIXED_2D = [(1000, 1000), (1080, 1920), (7, 1024), (100, 61), (61, 100), (1024, 7), (14336, 8), (12, 14336),
-            (9, 6), (3, 5), (600, 2)]
+            (9, 6), (3, 5), (600, 2), (3, 20000), (15360, 2)]
 
 
 @pytest.mark.parametrize("ny,nx", MIXED_2D, ids=[f"{a}x{b}" for a, b in MIXED_2D])
