@@ -54,7 +54,7 @@ enum { FFT_PREC_FP32 = 0, FFT_PREC_SPLIT_FP16_TC = 1 };
 
 enum {
     FFT_OK = 0,
-    FFT_ERR_INVALID_SIZE = -1, /* n not a power of two in range, batch < 1, count < 1 */
+    FFT_ERR_INVALID_SIZE = -1, /* a length out of range, batch < 1, count < 1 */
     FFT_ERR_INVALID_ARG = -2,  /* NULL / misaligned pointer, bad dir or precision, bad index */
     FFT_ERR_ALLOC = -3,        /* device or host allocation failed at plan creation */
     FFT_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
@@ -64,16 +64,27 @@ enum {
 
 /*
  * fft_plan_create -- plan `batch` 2D transforms of size [ny][nx].
- *   nx, ny     powers of two, 1 <= n <= 8192 each (nx = 1 or ny = 1 gives a
- *              batch of 1D transforms along the other axis).  A 1D length
- *              (the other axis 1) may go up to 2^26: lengths above 8192 run
- *              as the four-step decomposition the paper leaves as its next
- *              step (Section 6) -- n = n1*n2, length-n1 FFTs down the columns
- *              of the [n1][n2] view, then the twiddle w_n^{i2*k1} applied as
- *              the rows are loaded and length-n2 FFTs along them, stored
- *              transposed -- two HBM passes through a plan-owned workspace of
- *              n*batch complex values.  Such plans are FFT_PREC_FP32 only
- *              (else FFT_ERR_UNSUPPORTED) and have no fft_backward_weighted.
+ *   nx, ny     >= 1 (nx = 1 or ny = 1 gives a batch of 1D transforms along
+ *              the other axis).  Powers of two up to 8192 per axis run the
+ *              dense two-pass path (Section 5).  A 1D length may go up to
+ *              2^26 for a power of two and 2^24 otherwise; 2D axes up to
+ *              65536.  Power-of-two 1D lengths above 8192 run as the
+ *              four-step decomposition the paper leaves as its next step
+ *              (Section 6) -- n = n1*n2, length-n1 FFTs down the columns of
+ *              the [n1][n2] view, then the twiddle w_n^{i2*k1} applied as the
+ *              rows are loaded and length-n2 FFTs along them, stored
+ *              transposed -- two HBM passes through a plan-owned workspace
+ *              of n*batch complex values.  Every other shape is planned axis
+ *              by axis (the paper's uneven sizes, Sections 6 and 7):
+ *              lengths 2^a 3^b 5^c 7^d up to 14336 by mixed-radix stages
+ *              (radices 16, 8, 4, 2, 15, 9, 3, 5, 7) in one pass, longer such
+ *              lengths by a mixed-radix four-step, powers of two by the
+ *              dense path, any other length by Bluestein's algorithm over a
+ *              power-of-two length M >= 2n - 1; the y axis of a 2D plan runs
+ *              down the columns in place when it is mixed-radix and between
+ *              two transposes otherwise.  Plans other than the dense 2D
+ *              ones are FFT_PREC_FP32 only (else FFT_ERR_UNSUPPORTED) and
+ *              have no fft_backward_weighted.
  *   batch      >= 1; slices are stored back to back, nx*ny elements apart;
  *              nx*ny*batch <= 2^31.
  *   dir        FFT_FORWARD or FFT_INVERSE: the exponent sign of fft_execute.

@@ -525,8 +525,10 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_n
     return rc;
 }
 
-// A plan for sizes that are not all powers of two (FP32): nx == 1 or ny == 1
-// is a 1D batch; otherwise x axis, transpose, y axis, transpose.
+// A plan axis by axis (FP32): sizes that are not all powers of two, and 2D
+// power-of-two shapes with an axis above 8192.  nx == 1 or ny == 1 is a 1D
+// batch; otherwise the x axis, then the y axis down the columns in place
+// (mixed radix) or between two transposes.
 fft_plan_s *create_any(int nx, int ny, int batch, int dir, int *rc_out) {
     fft_plan_s *p = new (std::nothrow) fft_plan_s();
     AnyPlan *ap = new (std::nothrow) AnyPlan();
@@ -831,13 +833,15 @@ const char *fft_error_string(int code) {
 
 fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
     t_last_error = FFT_OK;
-    // powers of two: up to 8192 per axis, a single axis (1D batch) up to 2^26
-    // by the four-step path; other sizes (Bluestein): a 1D length up to 2^24,
-    // 2D axes up to 65536
+    // a 1D length (the other axis 1) up to 2^26 for powers of two (the
+    // four-step path above 8192), 2^24 otherwise; 2D axes up to 65536.  Dense
+    // plans: powers of two, 2D axes up to 8192; everything else goes axis by
+    // axis (mixed radix, four-step or Bluestein per axis, FP32 only)
     const bool pow2 = is_pow2(nx) && is_pow2(ny);
     const bool oned = nx == 1 || ny == 1;
     const bool large1d = pow2 && oned && (nx > 8192 || ny > 8192);
-    const int cap = pow2 ? (large1d ? (1 << 26) : 8192) : (oned ? (1 << 24) : 65536);
+    const bool dense = pow2 && (oned || (nx <= 8192 && ny <= 8192));
+    const int cap = oned ? (pow2 ? (1 << 26) : (1 << 24)) : 65536;
     if (nx < 1 || ny < 1 || batch < 1 || nx > cap || ny > cap) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
@@ -854,11 +858,11 @@ fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
         fail(FFT_ERR_INVALID_SIZE);
         return nullptr;
     }
-    if ((large1d || !pow2) && precision != FFT_PREC_FP32) {
+    if ((large1d || !dense) && precision != FFT_PREC_FP32) {
         fail(FFT_ERR_UNSUPPORTED);
         return nullptr;
     }
-    if (!pow2) {
+    if (!dense) {
         int rc = FFT_OK;
         fft_plan_s *p = create_any(nx, ny, batch, dir, &rc);
         if (!p) fail(rc);

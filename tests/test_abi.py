@@ -56,7 +56,7 @@ def test_error_strings(lib):
 
 
 @pytest.mark.parametrize("nx,ny,batch", [(0, 3, 1), (3, 0, 1), (0, 8, 1), (8, 8, 0),
-                                         (16384, 2, 1), (2, 16384, 1), (-4, 4, 1),
+                                         (131072, 2, 1), (2, 131072, 1), (-4, 4, 1),
                                          (1 << 27, 1, 1), (1, 1 << 27, 1), (3 << 23, 1, 1),
                                          (70000, 3, 1), (1 << 26, 1, 64)])
 def test_invalid_sizes_rejected_without_touching_the_gpu(lib, nx, ny, batch):
@@ -65,12 +65,14 @@ def test_invalid_sizes_rejected_without_touching_the_gpu(lib, nx, ny, batch):
 
 
 def test_long_1d_and_any_size_are_fp32_only(lib):
-    # the four-step path (1D lengths above 8192) and sizes that are not
-    # powers of two (Bluestein) have no split-FP16 form; the request is
-    # refused before any device call
+    # the four-step path (1D lengths above 8192), sizes that are not
+    # powers of two and 2D axes above 8192 (planned axis by axis) have no
+    # split-FP16 form; the request is refused before any device call
     assert lib.fft_plan_create(1 << 16, 1, 1, -1, 1) is None
     assert lib.fft_last_error() == -5
     assert lib.fft_plan_create(1000, 3, 1, -1, 1) is None
+    assert lib.fft_last_error() == -5
+    assert lib.fft_plan_create(16384, 2, 1, -1, 1) is None  # 2D axis above 8192: axis by axis
     assert lib.fft_last_error() == -5
 
 

@@ -45,7 +45,7 @@ def test_1d_any_length(g, n, inverse):
 
 
 SHAPES_2D = [(3, 5), (12, 7), (100, 60), (60, 100), (1000, 3), (3, 1000), (480, 720), (256, 100), (100, 256),
-             (64, 6), (1, 1000), (1000, 1)]
+             (64, 6), (1, 1000), (1000, 1), (16384, 4), (4, 16384), (2, 32768), (16384, 3)]
 
 
 @pytest.mark.parametrize("ny,nx", SHAPES_2D, ids=[f"{a}x{b}" for a, b in SHAPES_2D])
