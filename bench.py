@@ -254,22 +254,47 @@ def time_plan(torch, plan, x, out, steps, warmup, pass_events=False):
     return ms, passes
 
 
+def time_plan_flushed(torch, plan, x, out, steps, scratch):
+    """Mean and median ms per execute with L2 cold: before each timed call a
+    scratch buffer twice the size of L2 is written, outside the timed events."""
+    plan.execute(x, out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for k in range(steps):
+        scratch.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.execute(x, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return sum(ts) / len(ts), statistics.median(ts)
+
+
 def forms(torch, g, steps, warmup, dev):
     """Secondary measurements (rank 0, N=1 only): other sizes, inverse, the
     split tensor-core path, the differentiation form and the ragged batch."""
     import synth
     out = {}
+    # 2 x the 129 MB L2, written before each L2-cold call of the sizes that fit L2
+    scratch = torch.empty(2 * 129 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for n in (1024, 2048, 4096, 8192):
         x = torch.from_numpy(synth.normal_complex((n, n), seed=SEED)).to(dev)
         y = torch.empty_like(x)
         for inv in (False, True):
             plan = g.get_plan(n, n, 1, inv, "fp32", dev)
             ms, _ = time_plan(torch, plan, x, y, max(10, steps // 4), 3)
-            out[f"fp32_{'inv' if inv else 'fwd'}_{n}"] = {
-                "ms": ms, "GFLOP/s": flops_2d(n, n) / ms / 1e6,
-                "HBM_GB/s_algorithmic": 32.0 * n * n / ms / 1e6,
-                "note": "fits L2 (hot)" if n <= 2048 else "larger than L2"}
+            entry = {"ms": ms, "GFLOP/s": flops_2d(n, n) / ms / 1e6,
+                     "HBM_GB/s_algorithmic": 32.0 * n * n / ms / 1e6,
+                     "note": "fits L2 (hot)" if n <= 2048 else "larger than L2"}
+            if n <= 2048:
+                cold, cold_med = time_plan_flushed(torch, plan, x, y, 20, scratch)
+                entry.update({"ms_l2_flushed": cold, "ms_l2_flushed_median": cold_med,
+                              "HBM_GB/s_algorithmic_l2_flushed": 32.0 * n * n / cold / 1e6})
+            out[f"fp32_{'inv' if inv else 'fwd'}_{n}"] = entry
         del x, y
+    del scratch
     # split-FP16 tensor-core form on the precision workloads (noise + 8
     # exponentials), beside the FP32 path; relative difference of the two
     # results (the error against FP64 comes from the parity tests)
