@@ -4,18 +4,23 @@
 // further work (Sections 6 and 7).  Smooth lengths up to kMixedMaxN run here
 // as a Stockham autosort transform whose stages have radix 16, 8, 4, 2, 15,
 // 9, 3, 5 or 7, chosen at plan time (15 and 9 are two-level DFTs in
-// registers with compile-time inner twiddles): stage s of radix R, with Ns the product of the radices
-// before it, takes butterfly j (k = j mod Ns) from elements j + r n/R,
-// multiplies leg r by w_{Ns R}^{k r}, runs an R-point DFT and writes leg r to
-// element (j - k) R + k + r Ns.  After the last stage the output is in natural
-// order, so no reorder pass exists.  One CTA owns whole transforms: the first
-// stage reads global memory, the last writes it, and the stages between
-// ping-pong through two shared-memory buffers.
+// registers with compile-time inner twiddles).  Stage s of radix R, with Ns
+// the product of the radices before it, takes butterfly j (k = j mod Ns)
+// from elements j + r n/R, multiplies leg r by w_{Ns R}^{k r}, runs an
+// R-point DFT and writes leg r to element (j - k) R + k + r Ns.  After the
+// last stage the output is in natural order, so no reorder pass exists.
+// One CTA owns whole transforms: the first stage reads global memory, the
+// last writes it, and the stages between ping-pong through two padded
+// shared-memory buffers.
 //
 // Two layouts: rows (transforms along contiguous rows, W rows per CTA when
 // they are short) and columns (the transforms of W adjacent columns of an
 // [ny][nx] slice, element i of column x at i*nx + x), which serves the y axis
-// of a 2D plan without a transpose.
+// of a 2D plan without a transpose.  Longer smooth lengths run as a
+// four-step split n = n1 n2 over both layouts: columns of length n1 into a
+// workspace, then rows of length n2 whose first stage multiplies by the
+// inter-pass twiddle and whose last stage is staged in shared memory and
+// stored transposed (FourStepB).
 #include <math.h>
 
 #include "fft_common.cuh"
