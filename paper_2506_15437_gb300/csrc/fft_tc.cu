@@ -55,6 +55,12 @@ cudaError_t build_w16_table(void *t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// the two halves of h as one 32-bit word (low half first)
+__device__ __forceinline__ uint32_t h2bits(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
 __device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
     return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
@@ -135,14 +141,12 @@ struct TcPolicy {
                 for (int r = 0; r < 16; r += 2) {
                     const float xr0 = v[r].x * inv_s, xr1 = v[r + 1].x * inv_s;
                     const float xi0 = v[r].y * inv_s, xi1 = v[r + 1].y * inv_s;
-                    const __half hr0 = __float2half_rn(xr0), hr1 = __float2half_rn(xr1);
-                    const __half hi0 = __float2half_rn(xi0), hi1 = __float2half_rn(xi1);
-                    dst[r / 2] = pack_half2(hr0, hr1);
-                    dst[8 + r / 2] = pack_half2(hi0, hi1);
-                    dst[16 + r / 2] = pack_half2(__float2half_rn((xr0 - __half2float(hr0)) * 2048.f),
-                                                 __float2half_rn((xr1 - __half2float(hr1)) * 2048.f));
-                    dst[24 + r / 2] = pack_half2(__float2half_rn((xi0 - __half2float(hi0)) * 2048.f),
-                                                 __float2half_rn((xi1 - __half2float(hi1)) * 2048.f));
+                    const __half2 hr = __floats2half2_rn(xr0, xr1), hi = __floats2half2_rn(xi0, xi1);
+                    const float2 hrf = __half22float2(hr), hif = __half22float2(hi);
+                    dst[r / 2] = h2bits(hr);
+                    dst[8 + r / 2] = h2bits(hi);
+                    dst[16 + r / 2] = h2bits(__floats2half2_rn((xr0 - hrf.x) * 2048.f, (xr1 - hrf.y) * 2048.f));
+                    dst[24 + r / 2] = h2bits(__floats2half2_rn((xi0 - hif.x) * 2048.f, (xi1 - hif.y) * 2048.f));
                 }
             }
             __syncwarp();
@@ -345,10 +349,10 @@ struct TcgPolicy {
                 const int k0 = (c & 1) * 8 + 2 * q;
                 const float x0 = ((c & 2) ? v[k0].y : v[k0].x) * inv_s;
                 const float x1 = ((c & 2) ? v[k0 + 1].y : v[k0 + 1].x) * inv_s;
-                const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-                wh[q] = pack_half2(h0, h1);
-                wl[q] = pack_half2(__float2half_rn((x0 - __half2float(h0)) * 2048.f),
-                                   __float2half_rn((x1 - __half2float(h1)) * 2048.f));
+                const __half2 h = __floats2half2_rn(x0, x1);
+                const float2 hf = __half22float2(h);
+                wh[q] = h2bits(h);
+                wl[q] = h2bits(__floats2half2_rn((x0 - hf.x) * 2048.f, (x1 - hf.y) * 2048.f));
             }
             *reinterpret_cast<uint4 *>(row_hi + c * 128) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
             *reinterpret_cast<uint4 *>(row_lo + c * 128) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
