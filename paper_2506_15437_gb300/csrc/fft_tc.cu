@@ -408,8 +408,11 @@ struct TcRowShape {
     static constexpr size_t SMEM = STAGE_OFF + Pol::stage_bytes(THREADS);
 };
 
+// 256-thread CTAs are held to 128 registers so two fit an SM (the kernel
+// waits on its MMA groups and needs the second CTA's warps to cover them);
+// 512-thread CTAs would spill at 64 and stay one per SM
 template <int N, int P, class Pol>
-__global__ void __launch_bounds__(TcRowShape<N, Pol>::THREADS, 1)
+__global__ void __launch_bounds__(TcRowShape<N, Pol>::THREADS, TcRowShape<N, Pol>::THREADS <= 256 ? 2 : 1)
     k_rows_tc(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
               const float2 *__restrict__ twp, const __half *__restrict__ w16, long long nrows, int ny, int conj_in,
               int conj_out, int *status) {
