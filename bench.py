@@ -389,8 +389,10 @@ def any_size_form(torch, g, steps, dev):
 
 
 def fourstep_form(torch, g, steps, dev):
-    """Long 1D transforms beyond one CTA (four-step, two HBM passes):
-    4 x 2^24 and 1 x 2^26 points, both 512 MiB of input."""
+    """Long 1D transforms beyond one CTA: 4 x 2^24 points (four-step, two HBM
+    passes) and 1 x 2^26 (three passes: 4096-point columns, a 4-point middle
+    pass carrying the twiddles, 4096-point rows), both 512 MiB of input.  The
+    HBM figure counts the two-pass minimum, 32 B per point."""
     import synth
     out = {}
     for n, b in ((1 << 24, 4), (1 << 26, 1)):
@@ -403,8 +405,8 @@ def fourstep_form(torch, g, steps, dev):
             "ms": ms, "GFLOP/s": flops_2d(n, 1, b) / ms / 1e6,
             "HBM_GB/s_algorithmic": 32.0 * n * b / ms / 1e6,
             "passes_ms": {"cols": passes[0], "rows_twiddled_transposed": passes[1]},
-            "n1_x_n2": [d["fourstep"]["n1"], d["fourstep"]["n2"]],
-            "kernels": [d["cols"]["kernel"], d["rows"]["kernel"]]}
+            "n1_x_n2": [d["fourstep"]["n1"], d["fourstep"]["n2"]], "middle": d["fourstep"]["m"],
+            "kernels": [k for k in (d["cols"]["kernel"], d["fourstep"]["mid"], d["rows"]["kernel"]) if k]}
         del x, y
     return out
 

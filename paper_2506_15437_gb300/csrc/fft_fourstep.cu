@@ -23,6 +23,19 @@
 // per-row table G[c][e] = w_n^{k1*m_e} of W*E entries that the CTA builds in
 // shared memory; each value comes from two FP64-built tables,
 // w_n^a = hi[a >> 13] * lo[a & 8191] with lo[k] = w_n^k, hi[k] = w_n^{8192 k}.
+//
+// Three passes for n = 2^25, 2^26: a length-8192 axis allows only 16-byte
+// tiles (two columns or rows of 64 KiB in one CTA), which halves the DRAM
+// efficiency of both passes.  So the row length n / 4096 is split once more,
+// n = n1 * M * n3 with n1 = n3 = 4096 and M = 2 or 4 (i2 < M the middle
+// digit, i' = i2*n3 + i3):
+//   pass A   the length-4096 column FFTs, as above (32-byte tiles);
+//   pass M   per (k1, i3): u[i2] = Y[k1][i2][i3] w_n^{i' k1}, an M-point DFT
+//            over i2, then the twiddle w_n^{i3 k2 n1} (= w_{M n3}^{i3 k2}) --
+//            elementwise and in place, coalesced over i3 (k_fs_mid);
+//   pass B   length-4096 row FFTs of row (k1, k2) without twiddle, stored at
+//            k1 + n1 k2 + n1 M k3, W = 4 rows of adjacent k1 per CTA.
+// 48 bytes per point instead of 32, every pass with 32-byte tiles.
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -59,10 +72,13 @@ __device__ __forceinline__ float2 root_n(const float2 *__restrict__ lohi, int a)
 // there, and the buffer then serves as the Stockham exchange.  The next
 // tile's copies start as soon as every thread has read its last-stage
 // operands, so they overlap the last butterflies and the stores.
-template <int N, int E, int W>
+// MID: the last pass of the three-pass form (middle digit m, no twiddle);
+// otherwise pass B of the four-step form (m = 1, twiddle on load).
+template <int N, int E, int W, bool MID>
 __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E, W>::MINB)
     k_rows_fourstep(const float2 *__restrict__ work, float2 *__restrict__ out, const float2 *__restrict__ tw,
-                    const float2 *__restrict__ lohi, int n1, long long ntiles, int reverse, int *status) {
+                    const float2 *__restrict__ lohi, int n1, long long ntiles, int reverse, int *status,
+                    int m_arg) {
     using Sh = FsRowShape<N, E, W>;
     using Eng = typename Sh::Eng;
     constexpr int R0 = Eng::R0;
@@ -72,17 +88,24 @@ __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E,
     float2 *G = reinterpret_cast<float2 *>(raw + Sh::G_OFF);  // [W][E + 1]
     uint64_t *bar = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
     __shared__ int s_ok;
+    const int m = MID ? m_arg : 1;
     const int groups = n1 / W;
     const int t = threadIdx.x;
     const int c = t % W;
     const int tt = t / W;
-    const int mask = reverse ? n1 * N - 1 : -1;  // n = n1 * N is a power of two
+    const int mask = reverse ? n1 * m * N - 1 : -1;  // n = n1 * m * N is a power of two
     const int sgn = reverse ? -1 : 1;
+    // tile id: transform tr, middle digit k2 (m > 1: three passes), rows
+    // k1 = k10 .. k10 + W - 1; workspace row (k1, k2) of transform tr at
+    // ((tr * n1 + k1) * m + k2) * N
     auto issue = [&](long long id) {  // thread 0: the W row copies of tile `id`
         mbar_expect_tx(bar, Sh::TILE_BYTES);
-        const float2 *src = work + id * (long long)W * N;
+        const long long tb = id / groups, tr = tb / m;
+        const int k2 = (int)(tb - tr * m), k10 = (int)(id - tb * groups) * W;
+        const float2 *src = work + ((tr * n1 + k10) * m + k2) * (long long)N;
 #pragma unroll 1
-        for (int r = 0; r < W; ++r) bulk_load(tile + r * Sh::ROWP, src + (long long)r * N, N * sizeof(float2), bar);
+        for (int r = 0; r < W; ++r)
+            bulk_load(tile + r * Sh::ROWP, src + (long long)r * m * N, N * sizeof(float2), bar);
     };
     if (t == 0) {
         mbar_init(bar, 1);
@@ -94,14 +117,19 @@ __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E,
     uint32_t phase = 0;
     if (t == 0 && id < ntiles) issue(id);
     for (; id < ntiles; id += gridDim.x) {
-        const long long b = id / groups;  // transform within the batch
-        const int k10 = (int)(id - b * groups) * W;
-        for (int q = t; q < W * E; q += Sh::THREADS) {
-            const int cq = q / E, e = q % E;
-            const int me = (e / R0) * T + (e % R0) * (N / R0);
-            G[cq * Sh::GROW + e] = root_n(lohi, (k10 + cq) * me);  // k1 * m_e < n1 * n2
+        const long long tb = id / groups;  // transform and middle digit
+        const long long b = tb / m;        // transform within the batch
+        const int k2m = (int)(tb - b * m);
+        const int k10 = (int)(id - tb * groups) * W;
+        float2 base = make_float2(1.f, 0.f);
+        if constexpr (!MID) {
+            for (int q = t; q < W * E; q += Sh::THREADS) {
+                const int cq = q / E, e = q % E;
+                const int me = (e / R0) * T + (e % R0) * (N / R0);
+                G[cq * Sh::GROW + e] = root_n(lohi, (k10 + cq) * me);  // k1 * m_e < n1 * n2
+            }
+            base = root_n(lohi, (k10 + c) * tt);
         }
-        const float2 base = root_n(lohi, (k10 + c) * tt);
         if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
         __syncthreads();
         if (!s_ok) {
@@ -120,10 +148,13 @@ __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E,
 #pragma unroll
             for (int r = 0; r < R0; ++r) {
                 const int e = bb * R0 + r;
-                v[e] = cmul(tile[c * Sh::ROWP + j + r * (N / R0)], cmul(base, G[c * Sh::GROW + e]));
+                const float2 x = tile[c * Sh::ROWP + j + r * (N / R0)];
+                if constexpr (MID) v[e] = x;
+                else v[e] = cmul(x, cmul(base, G[c * Sh::GROW + e]));
             }
         }
-        float2 *dst = out + b * (long long)n1 * N;
+        float2 *dst = out + b * (long long)n1 * m * N;
+        const int off = k10 + n1 * k2m, ostride = n1 * m;
         auto after_reads = [&] {
             __syncthreads();
             if (t == 0 && next < ntiles) {
@@ -131,13 +162,14 @@ __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E,
                 issue(next);
             }
         };
-        auto store = [&](int i, int cc, float2 x) { dst[(sgn * (k10 + cc + i * n1)) & mask] = x; };
+        auto store = [&](int i, int cc, float2 x) { dst[(sgn * (off + cc + i * ostride)) & mask] = x; };
         Eng::template run<FftPolicy, true>(v, tile, tw, tt, c, SyncBlock{}, after_reads, store);
     }
 }
 
 namespace {
 ColVariant g_fs_rows[kMaxLog2 + 1][3][4];  // [log2 n2][E slot: 16, 32, 64][W slot: 2, 4, 8, 16]
+const void *g_fs_mid_fn = nullptr;         // the three-pass form's last pass (4096, E = 64, W = 4)
 bool g_fs_rows_init = false;
 
 int e_slot(int e) { return e == 16 ? 0 : e == 32 ? 1 : e == 64 ? 2 : -1; }
@@ -150,7 +182,7 @@ void reg_fs_row() {
     static_assert(N * W <= 16384, "exchange buffer");
     using Sh = FsRowShape<N, E, W>;
     ColVariant &v = g_fs_rows[ilog2(N)][e_slot(E)][w_slot(W)];
-    v.fn = (const void *)k_rows_fourstep<N, E, W>;
+    v.fn = (const void *)k_rows_fourstep<N, E, W, false>;
     v.n = N;
     v.e = E;
     v.w = W;
@@ -174,6 +206,7 @@ void init_fs_rows() {
     reg_fs_row_ws<2048>();
     reg_fs_row<4096, 16, 4>();
     reg_fs_row<4096, 64, 4>();
+    g_fs_mid_fn = (const void *)k_rows_fourstep<4096, 64, 4, true>;
     reg_fs_row<8192, 16, 2>();
     reg_fs_row<8192, 32, 2>();
     g_fs_rows_init = true;
@@ -198,25 +231,61 @@ const ColVariant *fourstep_row_variant(int log2n, int e, int w) {
 }
 
 cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2 *out, const float2 *tw,
-                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s) {
-    if (v.w < 1 || n1 % v.w) return cudaErrorInvalidValue;
-    const long long ntiles = (long long)batch * (n1 / v.w);
+                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s,
+                                 int m) {
+    if (v.w < 1 || n1 % v.w || m < 1) return cudaErrorInvalidValue;
+    init_fs_rows();
+    // m > 1: the three-pass form's last pass, compiled for 4096-point rows only
+    const void *fn = v.fn;
+    if (m > 1) {
+        if (v.n != 4096 || v.e != 64 || v.w != 4) return cudaErrorInvalidValue;
+        fn = g_fs_mid_fn;
+    }
+    const long long ntiles = (long long)batch * m * (n1 / v.w);
     if (ntiles < 1 || ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (v.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return e;
     }
     // persistent grid: every resident CTA slot once
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.threads, v.smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, v.threads, v.smem) != cudaSuccess)
         return cudaErrorInvalidConfiguration;
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > ntiles) grid = ntiles;
-    void *args[] = {(void *)&work, (void *)&out,    (void *)&tw,      (void *)&lohi,
-                    (void *)&n1,   (void *)&ntiles, (void *)&reverse, (void *)&status};
-    return cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+    void *args[] = {(void *)&work,   (void *)&out,     (void *)&tw,     (void *)&lohi, (void *)&n1,
+                    (void *)&ntiles, (void *)&reverse, (void *)&status, (void *)&m};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+}
+
+// Middle pass of the three-pass form: one thread per (transform, k1, i3).
+template <int M>
+__global__ void __launch_bounds__(256) k_fs_mid(float2 *work, const float2 *__restrict__ lohi, int n1, int n3,
+                                                long long groups) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= groups) return;
+    const long long tk = gid / n3;  // tr * n1 + k1
+    const int i3 = (int)(gid - tk * n3);
+    const int k1 = (int)(tk % n1);
+    float2 *p = work + tk * M * n3 + i3;  // element (tr, k1, i2, i3)
+    float2 v[M];
+#pragma unroll
+    for (int i2 = 0; i2 < M; ++i2) v[i2] = cmul(p[(long long)i2 * n3], root_n(lohi, (i2 * n3 + i3) * k1));
+    dft<M>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) p[(long long)k2 * n3] = k2 ? cmul(v[k2], root_n(lohi, i3 * k2 * n1)) : v[k2];
+}
+
+cudaError_t launch_fs_mid(float2 *work, const float2 *lohi, int n1, int m, int n3, int batch, cudaStream_t s) {
+    const long long groups = (long long)batch * n1 * n3;
+    const long long grid = (groups + 255) / 256;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (m == 2) k_fs_mid<2><<<(unsigned)grid, 256, 0, s>>>(work, lohi, n1, n3, groups);
+    else if (m == 4) k_fs_mid<4><<<(unsigned)grid, 256, 0, s>>>(work, lohi, n1, n3, groups);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace gb300fft

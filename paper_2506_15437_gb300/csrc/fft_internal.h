@@ -112,7 +112,10 @@ int fourstep_row_w(int n);
 // or at out[b][(n - k) mod n] if reverse (which turns the forward transform
 // into the inverse).
 cudaError_t launch_rows_fourstep(const ColVariant &v, const float2 *work, float2 *out, const float2 *tw,
-                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s);
+                                 const float2 *lohi, int n1, int batch, int reverse, int *status, cudaStream_t s,
+                                 int m = 1);  // m > 1: the three-pass form's last pass (no twiddle)
+// middle pass of the three-pass form (m = 2 or 4), in place on the workspace
+cudaError_t launch_fs_mid(float2 *work, const float2 *lohi, int n1, int m, int n3, int batch, cudaStream_t s);
 // t[k] = exp(-2*pi*i*(k*stride mod n)/n), k < count, built in FP64.
 cudaError_t build_roots_strided(float2 *t, int count, long long n, long long stride, cudaStream_t s);
 
@@ -191,6 +194,7 @@ struct AxisPlan {
 // (rows of work, stored transposed) into the output.
 struct FourStepPlan {
     int n = 0, n1 = 0, n2 = 0;  // n1 == 0: not a four-step plan
+    int m = 1;                  // > 1: three passes, rows of n2 / m after an m-point middle pass
     const ColVariant *a = nullptr;
     const ColVariant *b = nullptr;
     float2 *tw_a = nullptr, *tw_b = nullptr;  // stage twiddles of the two passes

@@ -312,22 +312,34 @@ int setup_fourstep(fft_plan_s *p, int n) {
         if (is_pow2(v) && v >= 128 && v <= 8192 && n / v >= 128 && n / v <= 8192) fs.n2 = v;
     }
     fs.n1 = n / fs.n2;
+    // 2^25 and 2^26: three passes (4096-point columns, an M-point middle pass,
+    // 4096-point rows), every pass on 32-byte tiles; GB300FFT_FS_THREE=0 keeps
+    // the two-pass split with its length-8192 axis
+    const char *e3 = getenv("GB300FFT_FS_THREE");
+    if (n >= (1 << 25) && !(e3 && atoi(e3) == 0)) {
+        fs.n1 = 4096;
+        fs.n2 = n / 4096;
+        fs.m = fs.n2 / 4096;
+    }
     // pass A tile width: 4 from 2048 up, 8 at 1024, 16 below (measured; the
     // 2D column pass's rule gives 8 at 2048, 0.31 vs 0.26 ms here)
     int wa = fs.n1 >= 8192 ? 2 : fs.n1 >= 2048 ? 4 : fs.n1 == 1024 ? 8 : 16;
     if (const char *ev = getenv("GB300FFT_FS_WA"))
         if (col_variant(ilog2(fs.n1), default_col_e(fs.n1), atoi(ev)) && atoi(ev) <= fs.n2) wa = atoi(ev);
     // E = 32 for the length-8192 column pass (measured 0.62 -> 0.52 ms at 2^26)
-    int ea = fs.n1 == 8192 ? 32 : preferred_col_e(fs.n1, wa), eb = fourstep_row_e(fs.n2);
-    int wb = fourstep_row_w(fs.n2);
+    const int rown = fs.n2 / fs.m;  // length of pass B's rows
+    int ea = fs.n1 == 8192 ? 32 : preferred_col_e(fs.n1, wa), eb = fourstep_row_e(rown);
+    int wb = fourstep_row_w(rown);
     if (const char *ev = getenv("GB300FFT_FS_EA"))
         if (col_variant(ilog2(fs.n1), atoi(ev), wa)) ea = atoi(ev);
-    if (const char *ev = getenv("GB300FFT_FS_EB"))
-        if (fourstep_row_variant(ilog2(fs.n2), atoi(ev), wb)) eb = atoi(ev);
-    if (const char *ev = getenv("GB300FFT_FS_WB"))
-        if (fourstep_row_variant(ilog2(fs.n2), eb, atoi(ev))) wb = atoi(ev);
+    if (fs.m == 1) {
+        if (const char *ev = getenv("GB300FFT_FS_EB"))
+            if (fourstep_row_variant(ilog2(fs.n2), atoi(ev), wb)) eb = atoi(ev);
+        if (const char *ev = getenv("GB300FFT_FS_WB"))
+            if (fourstep_row_variant(ilog2(fs.n2), eb, atoi(ev))) wb = atoi(ev);
+    }
     fs.a = col_variant(ilog2(fs.n1), ea, wa);
-    fs.b = fourstep_row_variant(ilog2(fs.n2), eb, wb);
+    fs.b = fourstep_row_variant(ilog2(rown), eb, wb);
     if (!fs.a || !fs.b || fs.a->w > fs.n2 || fs.b->w > fs.n1) return FFT_ERR_UNSUPPORTED;
     fs.tw_a = dev_alloc<float2>(p, fs.a->tw_size);
     fs.tw_b = dev_alloc<float2>(p, fs.b->tw_size);
@@ -335,7 +347,7 @@ int setup_fourstep(fft_plan_s *p, int n) {
     fs.work = dev_alloc<float2>(p, (size_t)n * p->batch);
     if (!fs.tw_a || !fs.tw_b || !fs.lohi || !fs.work) return FFT_ERR_ALLOC;
     if (build_twiddles(fs.tw_a, fs.n1, fs.a->e, 0) != cudaSuccess ||
-        build_twiddles(fs.tw_b, fs.n2, fs.b->e, 0) != cudaSuccess ||
+        build_twiddles(fs.tw_b, rown, fs.b->e, 0) != cudaSuccess ||
         build_roots_strided(fs.lohi, 8192, n, 1, 0) != cudaSuccess ||
         build_roots_strided(fs.lohi + 8192, n / 8192, n, 8192, 0) != cudaSuccess)
         return FFT_ERR_CUDA;
@@ -664,8 +676,10 @@ int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_
 
 // Large 1D transform: pass A (the plain column pass over the [n1][n2] view of
 // `in`, out of place into the workspace), pass B (twiddle on load, rows of the
-// workspace, stored transposed into `out`).  The inverse is the forward
-// transform stored at the reflected index (n - k) mod n.
+// workspace, stored transposed into `out`); with m > 1 (2^25, 2^26) an m-point
+// middle pass between them carries the twiddles and pass B's rows are n2 / m
+// long.  The inverse is the forward transform stored at the reflected index
+// (n - k) mod n.
 int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaStream_t s) {
     FourStepPlan &fs = p->fs;
     if (fs.map_base != src) {
@@ -678,8 +692,10 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
         cudaSuccess)
         return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, p->status, s) !=
-        cudaSuccess)
+    if (fs.m > 1 && launch_fs_mid(fs.work, fs.lohi, fs.n1, fs.m, fs.n2 / fs.m, p->batch, s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, p->status, s,
+                             fs.m) != cudaSuccess)
         return FFT_ERR_CUDA;
     if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
@@ -1143,14 +1159,16 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
         const gb300fft::FourStepPlan &fs = p->fs;
         char ra[96], rb[96];
         rad(fs.n1, fs.a->e, ra, sizeof ra);
-        rad(fs.n2, fs.b->e, rb, sizeof rb);
+        rad(fs.n2 / fs.m, fs.b->e, rb, sizeof rb);
         k = snprintf(tmp, sizeof tmp,
                      "{\"kind\": \"dense\", \"precision\": \"fp32\", \"fourstep\": {\"n\": %d, \"n1\": %d, "
-                     "\"n2\": %d}, \"rows\": {\"kernel\": \"k_rows_fourstep<%d,%d,%d>\", \"n\": %d, \"e\": %d, "
+                     "\"n2\": %d, \"m\": %d, \"mid\": \"%s\"}, \"rows\": {\"kernel\": "
+                     "\"k_rows_fourstep<%d,%d,%d>\", \"n\": %d, \"e\": %d, "
                      "\"w\": %d, \"radices\": %s, \"persistent\": 0}, \"cols\": {\"kernel\": "
                      "\"k_cols<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
                      "\"grid\": %d}, \"split\": 1}",
-                     fs.n, fs.n1, fs.n2, fs.n2, fs.b->e, fs.b->w, fs.n2, fs.b->e, fs.b->w, rb, fs.n1, fs.a->e, fs.a->w,
+                     fs.n, fs.n1, fs.n2, fs.m, fs.m == 4 ? "k_fs_mid<4>" : fs.m == 2 ? "k_fs_mid<2>" : "",
+                     fs.n2 / fs.m, fs.b->e, fs.b->w, fs.n2 / fs.m, fs.b->e, fs.b->w, rb, fs.n1, fs.a->e, fs.a->w,
                      fs.n1, fs.a->e, fs.a->w, ra, fs.grid_a);
     } else {
         const bool tc = p->prec == FFT_PREC_SPLIT_FP16_TC;

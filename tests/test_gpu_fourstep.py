@@ -102,15 +102,21 @@ def test_weighted_adjoint_unsupported(g):
         plan.backward_weighted(X, w, 2.0)
 
 
-@pytest.mark.parametrize("L,batch", [(24, 4), (26, 1)])
-def test_large_sampled_bins_parseval_roundtrip(g, L, batch):
+@pytest.mark.parametrize("L,batch,three", [(24, 4, "1"), (25, 2, "1"), (25, 2, "0"), (26, 1, "1"), (26, 1, "0")])
+def test_large_sampled_bins_parseval_roundtrip(g, monkeypatch, L, batch, three):
     """The bench's workloads: sampled bins of every transform against the
     oracle's per-bin definition; Parseval and inverse(forward(x)) = n x over
-    the whole output."""
+    the whole output.  2^25 and 2^26 run three passes (a middle pass of 2 or
+    4 points between 4096-point columns and rows) unless GB300FFT_FS_THREE=0
+    keeps the two-pass split."""
     n = 1 << L
     x = synth.uniform_complex((batch, n), seed=2506)
-    fwd = g.get_plan(n, 1, batch, False, "fp32", "cuda")
-    inv = g.get_plan(n, 1, batch, True, "fp32", "cuda")
+    monkeypatch.setenv("GB300FFT_FS_THREE", three)
+    fwd = g.Plan(n, 1, batch)
+    inv = g.Plan(n, 1, batch, inverse=True)
+    monkeypatch.delenv("GB300FFT_FS_THREE")
+    fsd = fwd.describe()["fourstep"]
+    assert fsd["m"] == (n >> 24 if L >= 25 and three == "1" else 1)
     d = torch.from_numpy(x).cuda()
     X = fwd.execute(d)
     back = inv.execute(X)
@@ -130,3 +136,27 @@ def test_large_sampled_bins_parseval_roundtrip(g, L, batch):
     assert np.all(np.abs(e_X - n * e_x) <= 2 * tol * n * e_x)
     rt = back.cpu().numpy()
     assert worst_rel_l2(rt, n * x.astype(np.complex128), n) <= 2 * tol
+    fwd.close()
+    inv.close()
+
+
+@pytest.mark.parametrize("L", [25, 26])
+def test_three_pass_matches_two_pass(g, monkeypatch, L):
+    """The three-pass and two-pass forms of the same transform share no pass
+    schedule (4096 x M x 4096 against 8192 x 4096 or 8192 x 8192): every
+    output agrees within twice the FP32 bound, both directions."""
+    n = 1 << L
+    x = torch.from_numpy(synth.uniform_complex((1, n), seed=77 + L)).cuda()
+    for inverse in (False, True):
+        three = g.Plan(n, 1, 1, inverse=inverse)
+        monkeypatch.setenv("GB300FFT_FS_THREE", "0")
+        two = g.Plan(n, 1, 1, inverse=inverse)
+        monkeypatch.delenv("GB300FFT_FS_THREE")
+        assert three.describe()["fourstep"]["m"] == n >> 24 and two.describe()["fourstep"]["m"] == 1
+        a = three.execute(x)
+        b = two.execute(x)
+        torch.cuda.synchronize()
+        err = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+        assert err <= 2 * tol_fp32(n), (L, inverse, err)
+        three.close()
+        two.close()
