@@ -74,7 +74,10 @@ enum {
  *              the [n1][n2] view, then the twiddle w_n^{i2*k1} applied as the
  *              rows are loaded and length-n2 FFTs along them, stored
  *              transposed -- two HBM passes through a plan-owned workspace
- *              of n*batch complex values.  Every other shape is planned axis
+ *              of n*batch complex values (2^25 and 2^26: three passes,
+ *              n = 4096*M*4096, with an M-point middle pass that applies the
+ *              twiddles, so no pass works on a length-8192 axis).  Every
+ *              other shape is planned axis
  *              by axis (the paper's uneven sizes, Sections 6 and 7):
  *              lengths 2^a 3^b 5^c 7^d up to 14336 by mixed-radix stages
  *              (radices 16, 8, 4, 2, 15, 9, 3, 5, 7) in one pass, longer such
