@@ -277,6 +277,16 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len);
  * `radices` (capacity 16) or a negative error. */
 int fft_debug_radices(int n, int axis, int *radices);
 
+/* The mixed-radix schedule of length n (2 <= n <= 2^24; Sections 6-7's
+ * uneven sizes): for n = 2^a 3^b 5^c 7^d <= 14336 the stage radices of the
+ * one-CTA kernel, first stage first, written to `radices` (capacity 16) and
+ * their count returned, *n1 = *n2 = 0; for longer such n, 0 returned and the
+ * four-step split n = n1 * n2 written (columns of length n1, then rows of
+ * length n2); FFT_ERR_INVALID_SIZE when n has a prime factor above 7 or is
+ * out of range, FFT_ERR_INVALID_ARG for NULL pointers.  Host only: no
+ * device call. */
+int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2);
+
 /* Library version string. */
 const char *fft_version(void);
 

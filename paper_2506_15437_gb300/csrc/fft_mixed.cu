@@ -472,11 +472,8 @@ bool mixed_factor(int n, MixedStages *st) {
         if (!push(16)) return false;
     for (int R : {8, 4, 2})
         if (rest % R == 0 && !push(R)) return false;
-    if (e5 >= 1 && e3 >= 1) {
+    for (; e5 >= 1 && e3 >= 1; --e5, --e3)
         if (!push(15)) return false;
-        --e5;
-        --e3;
-    }
     for (; e3 >= 2; e3 -= 2)
         if (!push(9)) return false;
     if (e3 == 1 && !push(3)) return false;

@@ -1215,6 +1215,19 @@ int fft_debug_radices(int n, int axis, int *radices) {
     return schedule_radices(n, e, radices);
 }
 
+int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2) {
+    if (!radices || !n1 || !n2) return FFT_ERR_INVALID_ARG;
+    *n1 = *n2 = 0;
+    if (n < 2 || n > (1 << 24)) return FFT_ERR_INVALID_SIZE;
+    gb300fft::MixedStages st;
+    if (n <= gb300fft::kMixedMaxN) {
+        if (!gb300fft::mixed_factor(n, &st)) return FFT_ERR_INVALID_SIZE;
+        for (int s = 0; s < st.S; ++s) radices[s] = st.radix[s];
+        return st.S;
+    }
+    return gb300fft::mixed_split(n, n1, n2) ? 0 : FFT_ERR_INVALID_SIZE;
+}
+
 int fft_debug_reorder_map(int n, int axis, void *map, void *stream) {
     if (!is_pow2(n) || n > 8192 || !map || (axis != 0 && axis != 1)) return FFT_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

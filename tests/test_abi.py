@@ -114,6 +114,50 @@ def test_stage_schedules(lib, axis):
     assert lib.fft_debug_radices(12, axis, buf) < 0
 
 
+def _smooth7(n):
+    for p in (2, 3, 5, 7):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def test_mixed_radix_schedules(lib):
+    """Host-side mixed-radix planning, without a GPU: every length up to
+    3000 and the longest one-CTA length factor into the compiled radices
+    (16s, then one of 8/4/2, then 15s/9s, single 3/5/7) whose product is n;
+    other lengths are refused."""
+    buf = (ctypes.c_int * 16)()
+    n1, n2 = ctypes.c_int(), ctypes.c_int()
+    for n in list(range(2, 3001)) + [14336, 14335, 12288, 10000]:
+        k = lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2))
+        if not _smooth7(n):
+            assert k == -1, n
+            continue
+        assert 1 <= k <= 16 and n1.value == 0 and n2.value == 0, n
+        rad = [buf[i] for i in range(k)]
+        assert int(np.prod(rad)) == n, (n, rad)
+        assert set(rad) <= {2, 3, 4, 5, 7, 8, 9, 15, 16}, (n, rad)
+        pow2 = [r for r in rad if r in (2, 4, 8, 16)]
+        assert pow2 == rad[:len(pow2)] and sum(r != 16 for r in pow2) <= 1, (n, rad)  # 16s, then one of 8/4/2
+        assert not (3 in rad and 5 in rad) and rad.count(3) <= 1, (n, rad)  # 3 x 5 -> 15, 3 x 3 -> 9
+
+
+def test_mixed_fourstep_splits(lib):
+    """Smooth lengths beyond one CTA: n = n1 n2, both mixed-radix lengths
+    (<= 14336), with n2 the divisor closest to sqrt(n) in log scale."""
+    buf = (ctypes.c_int * 16)()
+    n1, n2 = ctypes.c_int(), ctypes.c_int()
+    for n in [15360, 20000, 10 ** 6, 3 << 20, 6 ** 9, 5 ** 10, 7 ** 8, 14337 * 0 + 16384 * 3]:
+        assert lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2)) == 0, n
+        a, b = n1.value, n2.value
+        assert a * b == n and max(a, b) <= 14336 and _smooth7(a) and _smooth7(b), (n, a, b)
+        divs = [d for d in range(2, 14337) if n % d == 0 and n // d <= 14336]
+        best = min(divs, key=lambda d: abs(np.log(d) - 0.5 * np.log(n)))
+        assert abs(np.log(b) - 0.5 * np.log(n)) <= abs(np.log(best) - 0.5 * np.log(n)) + 1e-12, (n, b, best)
+    for n in (11 * 3000, 1 << 25, 0, 1):
+        assert lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2)) < 0, n
+
+
 def test_digit_reversal_helper_is_a_bijection_and_bit_reversal_for_radix2():
     for L in range(1, 12):
         n = 1 << L

@@ -174,7 +174,7 @@ def test_describe_and_unsupported(g):
 # the two-level 15 and 9, the single 3, 5, 7), prime powers, the longest
 # length, and short rows packed several to a CTA.
 MIXED_1D = [3, 5, 6, 7, 9, 10, 14, 15, 21, 24, 25, 35, 45, 49, 60, 96, 105, 120, 135, 210, 225, 343, 360, 405,
-            625, 1080, 1920, 2025, 2187, 3125, 6000, 7168, 10000, 12288, 14336]
+            625, 1080, 1125, 1920, 2025, 2187, 3125, 3375, 6000, 7168, 10000, 12288, 14336]
 
 
 @pytest.mark.parametrize("n", MIXED_1D)
