@@ -20,7 +20,8 @@ def g():
     return g
 
 
-@pytest.mark.parametrize("nx,ny,batch", [(8192, 8192, 1), (1024, 512, 3), (1 << 16, 1, 4), (1000, 300, 2)])
+@pytest.mark.parametrize("nx,ny,batch", [(8192, 8192, 1), (1024, 512, 3), (1 << 16, 1, 4), (1000, 300, 2),
+                                         (1 << 25, 1, 1), (10 ** 6, 1, 2)])
 def test_host_round_trip_matches_device_path(g, nx, ny, batch):
     plan = g.Plan(nx, ny, batch)
     xs = [synth.uniform_complex((batch, ny, nx), seed=40 + k) for k in range(4)]
