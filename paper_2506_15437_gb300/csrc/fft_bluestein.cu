@@ -19,6 +19,8 @@
 // A 2D transform whose sizes are not both powers of two runs axis by axis:
 // the x axis over all rows, a tiled transpose, the y axis over the rows of
 // the transposed array, and the transpose back.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(BluShape<N, E>::THREADS, BluShape<N, E>::MINB)
 
 namespace {
 BluVariant g_blu[kMaxLog2 + 1];
-bool g_blu_init = false;
+std::once_flag g_blu_once;  // registry filled once, safe across host threads
 
 template <int N>
 void reg_blu() {
@@ -195,20 +197,20 @@ void reg_blu() {
     v.smem = Sh::SMEM;
 }
 void init_blu() {
-    if (g_blu_init) return;
-    reg_blu<4>();
-    reg_blu<8>();
-    reg_blu<16>();
-    reg_blu<32>();
-    reg_blu<64>();
-    reg_blu<128>();
-    reg_blu<256>();
-    reg_blu<512>();
-    reg_blu<1024>();
-    reg_blu<2048>();
-    reg_blu<4096>();
-    reg_blu<8192>();
-    g_blu_init = true;
+    std::call_once(g_blu_once, [] {
+        reg_blu<4>();
+        reg_blu<8>();
+        reg_blu<16>();
+        reg_blu<32>();
+        reg_blu<64>();
+        reg_blu<128>();
+        reg_blu<256>();
+        reg_blu<512>();
+        reg_blu<1024>();
+        reg_blu<2048>();
+        reg_blu<4096>();
+        reg_blu<8192>();
+    });
 }
 
 int blocks_for(long long count) {

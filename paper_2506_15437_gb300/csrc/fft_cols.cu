@@ -11,6 +11,8 @@
 // prefetch issued one tile ahead) and its TMA load into shared memory starts
 // as soon as every thread has read its last-stage operands of tile k, so the
 // load overlaps the last butterflies and the stores of tile k.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -168,7 +170,7 @@ struct ColEntry {
 };
 constexpr int kWSlots = 4;  // W = 2, 4, 8, 16
 ColEntry g_cols[kMaxLog2 + 1][3][kWSlots];  // [log2n][E slot: default, 32, 64][W slot]
-bool g_cols_init = false;
+std::once_flag g_cols_once;  // registry filled once, safe across host threads
 
 int w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : -1; }
 
@@ -204,21 +206,21 @@ void reg_cols_n() {
 }
 
 void init_cols() {
-    if (g_cols_init) return;
-    reg_cols_n<2>();
-    reg_cols_n<4>();
-    reg_cols_n<8>();
-    reg_cols_n<16>();
-    reg_cols_n<32>();
-    reg_cols_n<64>();
-    reg_cols_n<128>();
-    reg_cols_n<256>();
-    reg_cols_n<512>();
-    reg_cols_n<1024>();
-    reg_cols_n<2048>();
-    reg_cols_n<4096>();
-    reg_cols_n<8192>();
-    g_cols_init = true;
+    std::call_once(g_cols_once, [] {
+        reg_cols_n<2>();
+        reg_cols_n<4>();
+        reg_cols_n<8>();
+        reg_cols_n<16>();
+        reg_cols_n<32>();
+        reg_cols_n<64>();
+        reg_cols_n<128>();
+        reg_cols_n<256>();
+        reg_cols_n<512>();
+        reg_cols_n<1024>();
+        reg_cols_n<2048>();
+        reg_cols_n<4096>();
+        reg_cols_n<8192>();
+    });
 }
 
 const ColEntry *col_entry(int log2n, int e, int w) {

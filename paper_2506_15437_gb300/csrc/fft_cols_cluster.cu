@@ -20,6 +20,8 @@
 // column pre-split): element i of block (slice b, kp) is row b*P*N + kp + P*i.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -135,7 +137,7 @@ struct ClusterEntry {
     int tw_size = 0;
 };
 ClusterEntry g_cl[3][2][2];  // [C slot: 2, 4][NQ slot: 1024, 2048][E slot: 16, 32]
-bool g_cl_init = false;
+std::once_flag g_cl_once;  // registry filled once, safe across host threads
 
 template <int NQ, int E, int C>
 void reg_cl() {
@@ -150,16 +152,16 @@ void reg_cl() {
     en.tw_size = Sched<NQ, E>::tw_size;
 }
 void init_cl() {
-    if (g_cl_init) return;
-    reg_cl<1024, 16, 2>();
-    reg_cl<1024, 32, 2>();
-    reg_cl<2048, 16, 2>();
-    reg_cl<2048, 32, 2>();
-    reg_cl<1024, 16, 4>();
-    reg_cl<1024, 32, 4>();
-    reg_cl<2048, 16, 4>();
-    reg_cl<2048, 32, 4>();
-    g_cl_init = true;
+    std::call_once(g_cl_once, [] {
+        reg_cl<1024, 16, 2>();
+        reg_cl<1024, 32, 2>();
+        reg_cl<2048, 16, 2>();
+        reg_cl<2048, 32, 2>();
+        reg_cl<1024, 16, 4>();
+        reg_cl<1024, 32, 4>();
+        reg_cl<2048, 16, 4>();
+        reg_cl<2048, 32, 4>();
+    });
 }
 const ClusterEntry *cl_entry(int n, int e, int C) {
     init_cl();

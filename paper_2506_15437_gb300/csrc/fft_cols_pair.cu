@@ -20,6 +20,8 @@
 // of block (slice b, kp) is row b*P*N + kp + P*i.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -101,7 +103,7 @@ struct PairEntry {
     int tw_size = 0;
 };
 PairEntry g_pair[kMaxLog2 + 1][2];  // [log2 N2][E slot: 16, 32]
-bool g_pair_init = false;
+std::once_flag g_pair_once;  // registry filled once, safe across host threads
 
 template <int N2, int E, int W>
 void reg_pair() {
@@ -115,14 +117,14 @@ void reg_pair() {
     en.tw_size = Sched<N2, E>::tw_size;
 }
 void init_pair() {
-    if (g_pair_init) return;
-    reg_pair<1024, 16, 8>();
-    reg_pair<1024, 32, 8>();
-    reg_pair<2048, 16, 4>();
-    reg_pair<2048, 32, 4>();
-    reg_pair<4096, 16, 2>();
-    reg_pair<4096, 32, 2>();
-    g_pair_init = true;
+    std::call_once(g_pair_once, [] {
+        reg_pair<1024, 16, 8>();
+        reg_pair<1024, 32, 8>();
+        reg_pair<2048, 16, 4>();
+        reg_pair<2048, 32, 4>();
+        reg_pair<4096, 16, 2>();
+        reg_pair<4096, 32, 2>();
+    });
 }
 const PairEntry *pair_entry(int n2, int e) {
     init_pair();

@@ -28,6 +28,8 @@
 // in place on the intermediate; or (planar) the row pass wrote each block as
 // a plane of its own in a workspace, read here through a P = 1 map, and the
 // output goes to the interleaved rows of the destination.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -193,23 +195,23 @@ struct StreamEntry {
     int g = 0, r0 = 0;
 };
 StreamEntry g_stream;
-bool g_stream_init = false;
+std::once_flag g_stream_once;  // registry filled once, safe across host threads
 
 void init_stream() {
-    if (g_stream_init) return;
-    constexpr int N = 4096, E = 64, W = 4, S = 5;  // 130 KiB exchange + 80 KiB ring
-    using Sh = StreamShape<N, E, W, S>;
-    g_stream.v.fn = (const void *)k_cols_stream<N, E, W, S>;
-    g_stream.v.n = N;
-    g_stream.v.e = E;
-    g_stream.v.w = W;
-    g_stream.v.threads = Sh::THREADS;
-    g_stream.v.smem = Sh::SMEM;
-    g_stream.v.box_rows = Sh::BOXR;
-    g_stream.v.tw_size = Sched<N, E>::tw_size;
-    g_stream.g = Sh::G;
-    g_stream.r0 = Sh::R0;
-    g_stream_init = true;
+    std::call_once(g_stream_once, [] {
+        constexpr int N = 4096, E = 64, W = 4, S = 5;  // 130 KiB exchange + 80 KiB ring
+        using Sh = StreamShape<N, E, W, S>;
+        g_stream.v.fn = (const void *)k_cols_stream<N, E, W, S>;
+        g_stream.v.n = N;
+        g_stream.v.e = E;
+        g_stream.v.w = W;
+        g_stream.v.threads = Sh::THREADS;
+        g_stream.v.smem = Sh::SMEM;
+        g_stream.v.box_rows = Sh::BOXR;
+        g_stream.v.tw_size = Sched<N, E>::tw_size;
+        g_stream.g = Sh::G;
+        g_stream.r0 = Sh::R0;
+    });
 }
 }  // namespace
 

@@ -36,6 +36,8 @@
 //   pass B   length-4096 row FFTs of row (k1, k2) without twiddle, stored at
 //            k1 + n1 k2 + n1 M k3, W = 4 rows of adjacent k1 per CTA.
 // 48 bytes per point instead of 32, every pass with 32-byte tiles.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(FsRowShape<N, E, W>::THREADS, FsRowShape<N, E,
 namespace {
 ColVariant g_fs_rows[kMaxLog2 + 1][3][4];  // [log2 n2][E slot: 16, 32, 64][W slot: 2, 4, 8, 16]
 const void *g_fs_mid_fn = nullptr;         // the three-pass form's last pass (4096, E = 64, W = 4)
-bool g_fs_rows_init = false;
+std::once_flag g_fs_rows_once;  // registry filled once, safe across host threads
 
 int e_slot(int e) { return e == 16 ? 0 : e == 32 ? 1 : e == 64 ? 2 : -1; }
 int w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : -1; }
@@ -198,18 +200,18 @@ void reg_fs_row_ws() {
     if constexpr (N <= 1024) reg_fs_row<N, 16, 16>();
 }
 void init_fs_rows() {
-    if (g_fs_rows_init) return;
-    reg_fs_row_ws<128>();
-    reg_fs_row_ws<256>();
-    reg_fs_row_ws<512>();
-    reg_fs_row_ws<1024>();
-    reg_fs_row_ws<2048>();
-    reg_fs_row<4096, 16, 4>();
-    reg_fs_row<4096, 64, 4>();
-    g_fs_mid_fn = (const void *)k_rows_fourstep<4096, 64, 4, true>;
-    reg_fs_row<8192, 16, 2>();
-    reg_fs_row<8192, 32, 2>();
-    g_fs_rows_init = true;
+    std::call_once(g_fs_rows_once, [] {
+        reg_fs_row_ws<128>();
+        reg_fs_row_ws<256>();
+        reg_fs_row_ws<512>();
+        reg_fs_row_ws<1024>();
+        reg_fs_row_ws<2048>();
+        reg_fs_row<4096, 16, 4>();
+        reg_fs_row<4096, 64, 4>();
+        g_fs_mid_fn = (const void *)k_rows_fourstep<4096, 64, 4, true>;
+        reg_fs_row<8192, 16, 2>();
+        reg_fs_row<8192, 32, 2>();
+    });
 }
 }  // namespace
 

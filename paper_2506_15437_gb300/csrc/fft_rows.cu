@@ -10,6 +10,8 @@
 // between butterfly steps never leave the SM.
 #include <cstdio>
 
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -216,7 +218,7 @@ struct RowEntry {
     int movemap_threads = 0;
 };
 RowEntry g_rows[kMaxLog2 + 1][3];  // [log2n][E slot: 8, 16, 32]
-bool g_rows_init = false;
+std::once_flag g_rows_once;  // registry filled once, safe across host threads
 
 int e_slot(int e) { return e == 8 ? 0 : e == 16 ? 1 : e == 32 ? 2 : -1; }
 
@@ -260,21 +262,21 @@ void reg_rows_n() {
 }
 
 void init_rows() {
-    if (g_rows_init) return;
-    reg_rows_n<2>();
-    reg_rows_n<4>();
-    reg_rows_n<8>();
-    reg_rows_n<16>();
-    reg_rows_n<32>();
-    reg_rows_n<64>();
-    reg_rows_n<128>();
-    reg_rows_n<256>();
-    reg_rows_n<512>();
-    reg_rows_n<1024>();
-    reg_rows_n<2048>();
-    reg_rows_n<4096>();
-    reg_rows_n<8192>();
-    g_rows_init = true;
+    std::call_once(g_rows_once, [] {
+        reg_rows_n<2>();
+        reg_rows_n<4>();
+        reg_rows_n<8>();
+        reg_rows_n<16>();
+        reg_rows_n<32>();
+        reg_rows_n<64>();
+        reg_rows_n<128>();
+        reg_rows_n<256>();
+        reg_rows_n<512>();
+        reg_rows_n<1024>();
+        reg_rows_n<2048>();
+        reg_rows_n<4096>();
+        reg_rows_n<8192>();
+    });
 }
 
 const RowEntry *row_entry(int log2n, int e) {

@@ -13,6 +13,8 @@
 // as every thread has read its last-stage operands.  The arithmetic (sum or
 // difference, then the twiddle, then the same engine) is the plain row
 // pass's, operation for operation.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -122,12 +124,14 @@ namespace {
 const void *g_land_fn = nullptr;
 size_t g_land_smem = 0;
 int g_land_threads = 0;
+std::once_flag g_land_once;
 void init_land() {
-    if (g_land_fn) return;
-    constexpr int N = 8192, E = 32;
-    g_land_fn = (const void *)k_rows_land<N, E>;
-    g_land_smem = LandShape<N, E>::SMEM;
-    g_land_threads = LandShape<N, E>::THREADS;
+    std::call_once(g_land_once, [] {
+        constexpr int N = 8192, E = 32;
+        g_land_fn = (const void *)k_rows_land<N, E>;
+        g_land_smem = LandShape<N, E>::SMEM;
+        g_land_threads = LandShape<N, E>::THREADS;
+    });
 }
 }  // namespace
 

@@ -14,6 +14,8 @@
 // P = 2: a unit is one row pair (q, q + ny/2) of the column pre-split (see
 // fft_rows.cu); both slots hold the pair, and the CTA produces both output
 // rows 2q (a + b) and 2q + 1 ((a - b) * w_ny^q) from one copy of the inputs.
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -175,7 +177,7 @@ struct RingEntry {
     size_t smem = 0;
 };
 RingEntry g_ring[kMaxLog2 + 1];
-bool g_ring_init = false;
+std::once_flag g_ring_once;  // registry filled once, safe across host threads
 
 template <int N>
 void reg_ring() {
@@ -191,12 +193,11 @@ void reg_ring() {
 }
 
 const RingEntry *ring_entry(int n) {
-    if (!g_ring_init) {
+    std::call_once(g_ring_once, [] {
         reg_ring<2048>();
         reg_ring<4096>();
         reg_ring<8192>();
-        g_ring_init = true;
-    }
+    });
     if (n < 2048 || n > 8192 || (n & (n - 1))) return nullptr;
     return &g_ring[ilog2(n)];
 }

@@ -24,6 +24,8 @@
 // fused reorders and the column pre-split are the same as on the FP32 path.
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "fft_common.cuh"
 #include "fft_internal.h"
 
@@ -596,7 +598,7 @@ struct TcColEntry {
 };
 TcRowEntry g_tc_rows[kMaxLog2 + 1];
 TcColEntry g_tc_cols[kMaxLog2 + 1][5];  // W slot: 2, 4, 8, 16, 32
-bool g_tc_init = false;
+std::once_flag g_tc_once;  // registry filled once, safe across host threads
 
 int tc_w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : w == 32 ? 4 : -1; }
 
@@ -639,28 +641,28 @@ void reg_tc_cols() {
     if constexpr (N * 32 <= 16384 && (N / 16) * 32 >= 32 && (N / 16) * 32 <= 1024) reg_tc_col<N, 32>();
 }
 void init_tc() {
-    if (g_tc_init) return;
-    reg_tc_row<16>();
-    reg_tc_row<32>();
-    reg_tc_row<64>();
-    reg_tc_row<128>();
-    reg_tc_row<256>();
-    reg_tc_row<512>();
-    reg_tc_row<1024>();
-    reg_tc_row<2048>();
-    reg_tc_row<4096>();
-    reg_tc_row<8192>();
-    reg_tc_cols<16>();
-    reg_tc_cols<32>();
-    reg_tc_cols<64>();
-    reg_tc_cols<128>();
-    reg_tc_cols<256>();
-    reg_tc_cols<512>();
-    reg_tc_cols<1024>();
-    reg_tc_cols<2048>();
-    reg_tc_cols<4096>();
-    reg_tc_cols<8192>();
-    g_tc_init = true;
+    std::call_once(g_tc_once, [] {
+        reg_tc_row<16>();
+        reg_tc_row<32>();
+        reg_tc_row<64>();
+        reg_tc_row<128>();
+        reg_tc_row<256>();
+        reg_tc_row<512>();
+        reg_tc_row<1024>();
+        reg_tc_row<2048>();
+        reg_tc_row<4096>();
+        reg_tc_row<8192>();
+        reg_tc_cols<16>();
+        reg_tc_cols<32>();
+        reg_tc_cols<64>();
+        reg_tc_cols<128>();
+        reg_tc_cols<256>();
+        reg_tc_cols<512>();
+        reg_tc_cols<1024>();
+        reg_tc_cols<2048>();
+        reg_tc_cols<4096>();
+        reg_tc_cols<8192>();
+    });
 }
 }  // namespace
 
