@@ -24,6 +24,9 @@
  * allocates all of it at creation; execute calls allocate nothing and do
  * not synchronise, so they are stream-ordered and may be captured in a CUDA
  * graph.  A plan must not be used on two streams at the same time.
+ * Different plans may be created, used and destroyed from several host
+ * threads at once (the library's kernel tables are filled once, under
+ * std::call_once).
  *
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream).
