@@ -290,6 +290,12 @@ int fft_debug_radices(int n, int axis, int *radices);
  * device call. */
 int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2);
 
+/* cos(2 pi m / r) and sin(2 pi m / r) as the float constants the composite
+ * mixed-radix DFTs use (evaluated at compile time from an integer quadrant
+ * split and Taylor series in double, rounded once): written to *c and *s.
+ * FFT_ERR_INVALID_ARG for NULL pointers or r < 1.  Host only. */
+int fft_debug_root(int m, int r, float *c, float *s);
+
 /* Library version string. */
 const char *fft_version(void);
 

@@ -588,3 +588,12 @@ cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *i
 }
 
 }  // namespace gb300fft
+
+// The float constants the composite-radix DFTs multiply by, as the
+// compiler evaluates them (host copy of the same constexpr functions).
+extern "C" int fft_debug_root(int m, int r, float *c, float *s) {
+    if (!c || !s || r < 1) return FFT_ERR_INVALID_ARG;
+    *c = (float)gb300fft::cos_2pi(m, r);
+    *s = (float)gb300fft::sin_2pi(m, r);
+    return FFT_OK;
+}

@@ -158,6 +158,34 @@ def test_mixed_fourstep_splits(lib):
         assert lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2)) < 0, n
 
 
+def test_compile_time_roots_are_correctly_rounded(lib):
+    """The constants of the composite-radix DFTs (cos and sin of 2 pi m / R
+    evaluated by the compiler): equal to the float nearest the exact value
+    for every R <= 128 and m < R, and exactly 0 or +-1 on the axes.  The
+    reference is mpmath-free: FP64 libm values, accepted only where the
+    float rounding is unambiguous (|x - float midpoint| well above 1e-15)."""
+    import math
+    c, s = ctypes.c_float(), ctypes.c_float()
+    checked = 0
+    for R in range(1, 129):
+        for m in range(R):
+            assert lib.fft_debug_root(m, R, ctypes.byref(c), ctypes.byref(s)) == 0
+            for got, want in ((c.value, math.cos(2 * math.pi * m / R)), (s.value, math.sin(2 * math.pi * m / R))):
+                if (4 * m) % R == 0:  # on an axis: exact
+                    want = float(round(want))
+                    assert got == want, (m, R, got, want)
+                    continue
+                f = float(np.float32(want))
+                # skip the rare values within 1e-15 of a rounding midpoint
+                nxt = float(np.nextafter(np.float32(f), np.float32(np.inf if want > f else -np.inf)))
+                if abs(abs(want - f) - abs(nxt - f) / 2) < 1e-15:
+                    continue
+                assert got == f, (m, R, got, f)
+                checked += 1
+    assert checked > 10000
+    assert lib.fft_debug_root(1, 0, ctypes.byref(c), ctypes.byref(s)) < 0
+
+
 def test_digit_reversal_helper_is_a_bijection_and_bit_reversal_for_radix2():
     for L in range(1, 12):
         n = 1 << L
