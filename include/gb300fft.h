@@ -290,6 +290,20 @@ int fft_debug_radices(int n, int axis, int *radices);
  * device call. */
 int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2);
 
+/*
+ * fft_debug_row_variant -- launch shape of the compiled row-pass kernel for
+ * length n (a power of two, 2..8192), e elements per thread and column
+ * pre-split `split` (1: none; 2: the row pass also applies the first radix-2
+ * step of the column transform, Section 5's column FFTs split as 2 x ny/2).
+ * Writes to the host array info[20]: threads per CTA, rows per CTA,
+ * shared-memory float2 elements per row, the stage count S, then the S stage
+ * radices (first stage first) and zeros.  FFT_ERR_UNSUPPORTED if that kernel
+ * is not compiled, FFT_ERR_INVALID_SIZE for a bad n, FFT_ERR_INVALID_ARG for
+ * a NULL info.  Host only: no device call (the tests model the kernel's
+ * index arithmetic on the CPU from these shapes).
+ */
+int fft_debug_row_variant(int n, int e, int split, int *info);
+
 /* cos(2 pi m / r) and sin(2 pi m / r) as the float constants the composite
  * mixed-radix DFTs use (evaluated at compile time from an integer quadrant
  * split and Taylor series in double, rounded once): written to *c and *s.

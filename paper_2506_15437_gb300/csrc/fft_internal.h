@@ -39,6 +39,9 @@ const RowVariant *row_variant(int log2n, int e);           // nullptr if not com
 const ColVariant *col_variant(int log2n, int e, int w);    // nullptr if not compiled
 int default_row_e(int n);
 bool row_split_available(int n, int e);  // a column pre-split (P = 2) row kernel exists
+// Launch shape of the compiled row kernel (n, e, split): threads per CTA,
+// rows per CTA and shared-memory float2 elements per row; false if none.
+bool row_variant_info(int n, int e, int split, int *threads, int *rows_per_cta, int *smem_elems);
 int default_col_e(int n);
 int preferred_col_e(int n, int w);
 int default_col_w(int n, int nx);

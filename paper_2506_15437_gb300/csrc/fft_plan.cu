@@ -1215,6 +1215,22 @@ int fft_debug_radices(int n, int axis, int *radices) {
     return schedule_radices(n, e, radices);
 }
 
+int fft_debug_row_variant(int n, int e, int split, int *info) {
+    if (!info) return FFT_ERR_INVALID_ARG;
+    if (!is_pow2(n) || n < 2 || n > 8192) return FFT_ERR_INVALID_SIZE;
+    int threads = 0, rows = 0, elems = 0;
+    if (!gb300fft::row_variant_info(n, e, split, &threads, &rows, &elems)) return FFT_ERR_UNSUPPORTED;
+    int rad[16];
+    const int S = schedule_radices(n, e > n ? n : e, rad);
+    if (S < 1) return FFT_ERR_UNSUPPORTED;
+    info[0] = threads;
+    info[1] = rows;
+    info[2] = elems;
+    info[3] = S;
+    for (int k = 0; k < 16; ++k) info[4 + k] = k < S ? rad[k] : 0;
+    return FFT_OK;
+}
+
 int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2) {
     if (!radices || !n1 || !n2) return FFT_ERR_INVALID_ARG;
     *n1 = *n2 = 0;
