@@ -201,10 +201,13 @@ int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *strea
 /*
  * fft_execute_ragged_noalloc -- the ragged transform of fft_execute_ragged
  * (same persistent kernel, same packing: instance i starts at the sum of the
- * earlier nx*ny) for callers that cannot allocate device memory, e.g. code
- * running while a CUDA graph is being captured, or a process whose device
- * memory belongs to a pool or framework allocator it must not go around.  The
- * paper has no counterpart; it is an addition of this library.
+ * earlier nx*ny) for callers that cannot allocate device memory: a process
+ * whose device memory belongs to a pool or framework allocator that it must
+ * not go around (a cudaMalloc there would be memory the pool does not know
+ * of), or a runtime that forbids device allocation once it has started (all
+ * memory is reserved at start-up so that a long-running service cannot fail
+ * later for lack of it).  The paper has no counterpart; it is an addition of
+ * this library.
  *   count    1..1024 instances; nx[i], ny[i] powers of two in 32..1024 (host
  *            arrays, read during the call); at most 65536 work items (one item
  *            is 8192 elements of one pass; a 512 x 512 instance takes 64).
@@ -216,8 +219,10 @@ int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *strea
  * It allocates nothing.  Its scratch is one fixed array of about 1.1 MiB
  * inside the library, present on every GPU that loads the library until the
  * process exits.  The first call on each device looks up that array's address
- * and fills its twiddle tables (a short synchronising set-up with the device
- * current), so make it before any stream capture.  Every call reuses the same
+ * and fills its twiddle tables (a short set-up, with the device current, that
+ * synchronises `stream`), so that first call should come before any stream
+ * capture.  Each call copies its small work list (about 16 bytes per work
+ * item) from host memory into the array.  Every call reuses the same
  * array and it keeps the previous call's contents; the call clears what must
  * start at zero.  Calls that overlap on the GPU (different streams, or
  * concurrent host threads) race on the array: serialise them.

@@ -634,10 +634,11 @@ namespace gb300fft {
 // ---------------------------------------------------------------------------
 // Ragged execution without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, processes whose device memory is owned by a pool or a
-// framework allocator they must not bypass, and runtimes that forbid device
-// allocation after start-up.  fft_execute_ragged_noalloc serves them: it runs
+// Some callers cannot call cudaMalloc: processes whose device memory is
+// owned by a pool or a framework allocator they must not bypass, and
+// runtimes that forbid device allocation after start-up (everything is
+// reserved up front so a long-running service cannot run out later).
+// fft_execute_ragged_noalloc serves them: it runs
 // the same persistent kernel as fft_execute_ragged, but its scratch (work
 // queue, instance table, offsets, completion counters and twiddle tables)
 // lives in the fixed array below instead of a plan.  The array is part of the

@@ -1,7 +1,10 @@
 """fft_execute_ragged_noalloc: the ragged transform for callers that cannot
-allocate device memory (graph capture in progress, memory owned by a pool or
-framework allocator).  Its scratch is a fixed array inside the library; this
-file checks it, through the C ABI, against the plan-based fft_execute_ragged.
+allocate device memory (a process whose device memory belongs to a pool or
+framework allocator it must not go around, or a runtime that forbids device
+allocation after start-up).  Its scratch is a fixed array inside the
+library.  These tests call it through the C ABI and compare it with the
+plan-based fft_execute_ragged (same kernel, plan-owned scratch) and with the
+FP64 oracle, instance by instance.
 
 Collected last (file name), so a run that stops at the first failure has
 already run every other test; it also passes alone in a fresh process.
@@ -11,8 +14,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from tests.helpers import rel_l2, tol_fp32
+from tests.helpers import ORACLE_THREADS, rel_l2, tol_fp32
 
 torch = pytest.importorskip("torch")
 
@@ -27,19 +31,35 @@ def lib():
     return _native.load()
 
 
-def noalloc(lib, nx, ny, x, inverse=False, status=None):
+def noalloc(lib, nx, ny, x, inverse=False, status=None, out=None):
     n = len(nx)
     ax = (ctypes.c_int * n)(*[int(v) for v in nx])
     ay = (ctypes.c_int * n)(*[int(v) for v in ny])
-    out = torch.empty_like(x)
+    if out is None:
+        out = torch.empty_like(x)
     rc = lib.fft_execute_ragged_noalloc(n, ax, ay, 1 if inverse else -1, x.data_ptr(), out.data_ptr(),
                                         status.data_ptr() if status is not None else None,
                                         torch.cuda.current_stream().cuda_stream)
     return rc, out
 
 
+def check_instances(got, ref, nx, ny, offs):
+    for i in range(len(nx)):
+        n = int(nx[i] * ny[i])
+        assert rel_l2(got[offs[i]:offs[i] + n], ref[offs[i]:offs[i] + n]) <= tol_fp32(n), i
+
+
+def oracle_packed(packed, nx, ny, offs, inverse):
+    ref = np.empty(packed.shape, np.complex128)
+    for i in range(len(nx)):
+        a, n = offs[i], int(nx[i] * ny[i])
+        ref[a:a + n] = oracle.fft2d(packed[a:a + n].reshape(int(ny[i]), int(nx[i])),
+                                    dir=1 if inverse else -1, threads=ORACLE_THREADS).ravel()
+    return ref
+
+
 @pytest.mark.gpu
-def test_noalloc_matches_plan_on_two_calls_in_a_row(lib):
+def test_noalloc_matches_plan_and_oracle_on_two_calls_in_a_row(lib):
     import paper_2506_15437_gb300 as g
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     # two different batches back to back: the second call must not see the
@@ -49,14 +69,46 @@ def test_noalloc_matches_plan_on_two_calls_in_a_row(lib):
         x = torch.from_numpy(packed).cuda()
         rc, got = noalloc(lib, nx, ny, x, inverse=inverse, status=status)
         assert rc == 0
-        ref = g.RaggedPlan(nx, ny, inverse=inverse).execute(x)
+        plan = g.RaggedPlan(nx, ny, inverse=inverse)
+        ref = plan.execute(x)
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         got = got.cpu().numpy()
-        ref = ref.cpu().numpy()
-        for i in range(count):
-            n = int(nx[i] * ny[i])
-            assert rel_l2(got[offs[i]:offs[i] + n], ref[offs[i]:offs[i] + n]) <= tol_fp32(n), i
+        check_instances(got, ref.cpu().numpy(), nx, ny, offs)
+        check_instances(got, oracle_packed(packed, nx, ny, offs, inverse), nx, ny, offs)
+        plan.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_in_place(lib):
+    """in == out: the same kernel reads each instance's pass input before any
+    pass of that instance writes over it."""
+    import paper_2506_15437_gb300 as g
+    nx, ny, offs, packed = synth.ragged_batch(64, seed=33)
+    x = torch.from_numpy(packed).cuda()
+    plan = g.RaggedPlan(nx, ny)
+    ref = plan.execute(x).cpu().numpy()
+    d = x.clone()
+    rc, out = noalloc(lib, nx, ny, d, out=d)
+    assert rc == 0 and out.data_ptr() == d.data_ptr()
+    torch.cuda.synchronize()
+    check_instances(d.cpu().numpy(), ref, nx, ny, offs)
+    check_instances(d.cpu().numpy(), oracle_packed(packed, nx, ny, offs, False), nx, ny, offs)
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_leaves_a_set_status_word_alone(lib):
+    """The kernel only ever records a failure into a status word that still
+    reads 0; a word the caller already set keeps its value."""
+    nx, ny, offs, packed = synth.ragged_batch(16, seed=34)
+    x = torch.from_numpy(packed).cuda()
+    status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    rc, got = noalloc(lib, nx, ny, x, status=status)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 7
+    check_instances(got.cpu().numpy(), oracle_packed(packed, nx, ny, offs, False), nx, ny, offs)
 
 
 @pytest.mark.gpu
