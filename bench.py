@@ -421,11 +421,12 @@ def diff_form(torch, g, steps, dev):
     plan = g.get_plan(n, n, b, False, "fp32", dev)
     X = torch.empty_like(x)
     G = torch.empty_like(x)
+    upstream = torch.ones(1, dtype=torch.float32, device=dev)  # dOut/dL, read on the device
 
     def step():
         plan.execute(x, out=X)
         plan.weighted_power(X, w)
-        plan.backward_weighted(X, w, 2.0, out=G)
+        plan.backward_weighted_dev(X, w, upstream, 2.0, out=G)
 
     ms = time_fn(torch, step, max(10, steps // 4))
     fl = 2 * flops_2d(n, n, b)
@@ -458,13 +459,28 @@ def ragged_form(torch, g, steps, dev):
     x = torch.from_numpy(packed).to(dev)
     y = torch.empty_like(x)
     fl = sum(flops_2d(int(a), int(b)) for a, b in zip(nx, ny))
+    byts = ragged_algorithmic_bytes(nx, ny)
     ms_graph = time_fn(torch, lambda: plan.execute(x, out=y), max(10, steps // 4))
     ms_loop = time_fn(torch, lambda: plan.execute_loop(x, out=y), max(5, steps // 10))
     plan.close()
+    peak, peak_kind, _ = read_peaks()
+    gbs = byts / ms_graph / 1e6
     return {"ragged_512": {"ms_graph": ms_graph, "ms_loop": ms_loop, "GFLOP/s": fl / ms_graph / 1e6,
                            "GFLOP/s_loop": fl / ms_loop / 1e6, "speedup_vs_loop": ms_loop / ms_graph,
-                           "points": int(packed.size),
-                           "HBM_GB/s_algorithmic_2pass": 32.0 * packed.size / ms_graph / 1e6}}
+                           "points": int(packed.size), "algorithmic_bytes": byts,
+                           "HBM_GB/s_algorithmic": gbs, "frac_of_peak": gbs / peak,
+                           "peak": f"{peak:.1f} GB/s ({peak_kind})"}}
+
+
+def ragged_algorithmic_bytes(nx, ny, fused_max=8192):
+    """One read and one write of complex64 per point per HBM pass: instances
+    of at most `fused_max` points run rows and columns in one CTA (one pass,
+    16 B per point), larger ones two passes (32 B per point)."""
+    total = 0
+    for a, b in zip(nx, ny):
+        n = int(a) * int(b)
+        total += (16 if n <= fused_max else 32) * n
+    return float(total)
 
 
 def profile_form(torch, name, steps, warmup, dev):
@@ -484,7 +500,9 @@ def profile_form(torch, name, steps, warmup, dev):
         w = torch.from_numpy(synth.mask((b, n, n), seed=SEED + 1)).to(dev)
         plan = g.Plan(n, n, b)
         X = torch.empty_like(x)
-        run = lambda: (plan.execute(x, out=X), plan.backward_weighted(X, w, 2.0))  # noqa: E731
+        upstream = torch.ones(1, dtype=torch.float32, device=dev)
+        run = lambda: (plan.execute(x, out=X), plan.weighted_power(X, w),  # noqa: E731
+                       plan.backward_weighted_dev(X, w, upstream, 2.0))
     elif name == "mixed_3000":
         # 8192 signals of 3000 = 2^3 3 5^3 points (mixed radix, 196 MB each way)
         x = torch.from_numpy(synth.uniform_complex((8192, 3000), seed=SEED)).to(dev)

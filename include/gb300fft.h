@@ -155,6 +155,20 @@ int fft_backward_weighted(fft_plan_t p, const void *X, const void *w, float scal
                           void *grad_in, void *stream);
 
 /*
+ * fft_backward_weighted_dev -- fft_backward_weighted with the scale read on
+ * the device: grad_in = F^H (scale * scale_dev[0] * w (.) X).  scale_dev is a
+ * device pointer to one float32 (4-byte aligned), read by the adjoint's first
+ * pass when it runs, so a scale produced by earlier work on `stream` (an
+ * autograd output gradient, for instance) never has to be copied to the host.
+ * For L = sum w*|F x|^2 with upstream gradient g = dOut/dL, passing X = F x,
+ * scale = 2 and scale_dev = &g gives dOut/dx.  Same sizes, aliasing rules and
+ * FFT_ERR_UNSUPPORTED cases as fft_backward_weighted; FFT_ERR_INVALID_ARG for
+ * a NULL or misaligned scale_dev.
+ */
+int fft_backward_weighted_dev(fft_plan_t p, const void *X, const void *w, const void *scale_dev,
+                              float scale, void *grad_in, void *stream);
+
+/*
  * fft_weighted_power -- partial sums of L = sum w*|X|^2 over X, w of the
  * plan's full size: writes `nparts` float32 partial sums to the device array
  * `partials` (the caller adds them, preferably in double).  nparts is

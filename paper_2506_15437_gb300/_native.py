@@ -35,6 +35,7 @@ SIGNATURES = [
     ("fft_execute_host", _I, [_P, _P, _P, _P]),
     ("fft_backward", _I, [_P, _P, _P, _P]),
     ("fft_backward_weighted", _I, [_P, _P, _P, _F, _P, _P]),
+    ("fft_backward_weighted_dev", _I, [_P, _P, _P, _P, _F, _P, _P]),
     ("fft_weighted_power", _I, [_P, _P, _P, _P, _P]),
     ("fft_weighted_power_parts", _I, [_P]),
     ("fft_plan_destroy", _I, [_P]),

@@ -56,17 +56,19 @@ cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s);
 // Row pass over `nrows` rows of length v.n.  split = P in {1, 2}: with P = 2
 // the rows form [.][ny][n] slices and the pass also applies the column
 // pre-split (2-point DFT across rows y and y + ny/2, twiddle twp[q*kp]).
+// A weighted pass multiplies each input by wscale * weight[i], and by
+// *wscale_dev too when that device pointer is not null.
 cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw,
                         const float2 *twp, long long nrows, int ny, int split, int conj_in,
-                        int conj_out, const float *weight, float wscale, int grid, int pf_dist,
-                        int perm_t, int perm_g, int planar, cudaStream_t s);
+                        int conj_out, const float *weight, float wscale, const float *wscale_dev, int grid,
+                        int pf_dist, int perm_t, int perm_g, int planar, cudaStream_t s);
 int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, int split, bool persistent);
 // Long-row pass with a TMA landing ring (fft_rows_ring.cu), n in 2048..8192.
 bool ring_rows_available(int n);
 int ring_rows_grid(int n, long long nrows, int split, int num_sms, bool weighted);
 cudaError_t launch_rows_ring(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
-                             float wscale, int *status, int grid, cudaStream_t s);
+                             float wscale, const float *wscale_dev, int *status, int grid, cudaStream_t s);
 // Split-FP16 tensor-core variants (fft_tc.cu), E = 16.
 cudaError_t build_w16_table(void *t, cudaStream_t s);
 bool tc_rows_available(int n);
@@ -359,7 +361,7 @@ namespace gb300fft {
 // out = DFT_sign(in) of a dense plan (optionally weighted by wscale * w on
 // load); returns an FFT_* code.  Defined in fft_plan.cu.
 int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
-              cudaStream_t s);
+              cudaStream_t s, const float *wscale_dev = nullptr);
 // Frees a plan and everything it owns.
 void free_plan(fft_plan_s *p);
 }  // namespace gb300fft

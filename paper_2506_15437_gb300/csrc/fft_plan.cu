@@ -703,7 +703,7 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
 
 // out = DFT_{sign}(in) (optionally weighted by scale*w on load) for a dense plan.
 int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
-              cudaStream_t s) {
+              cudaStream_t s, const float *wscale_dev) {
     const bool inv = sign > 0;
     const float2 *src = static_cast<const float2 *>(in);
     float2 *dst = static_cast<float2 *>(out);
@@ -766,9 +766,10 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                                 stream ? cp.perm_t : 0, stream ? cp.perm_g : 0, planar ? 1 : 0, p->status,
                                 p->num_sms, s)
         : p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
-                                   (inv && !two_pass) ? 1 : 0, weight, wscale, p->status, grid, s)
+                                   (inv && !two_pass) ? 1 : 0, weight, wscale, wscale_dev, p->status, grid, s)
                 : launch_rows(*p->rows.row, src, row_dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
-                              (inv && !two_pass) ? 1 : 0, weight, wscale, grid, p->row_pf, stream ? cp.perm_t : 0,
+                              (inv && !two_pass) ? 1 : 0, weight, wscale, wscale_dev, grid, p->row_pf,
+                              stream ? cp.perm_t : 0,
                               stream ? cp.perm_g : 0, planar ? 1 : 0, s);
     if (er != cudaSuccess) return FFT_ERR_CUDA;
     if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
@@ -980,6 +981,16 @@ int fft_backward_weighted(fft_plan_t p, const void *X, const void *w, float scal
     p->last_use_host = false;
     return run_dense(p, X, grad_in, -p->dir, static_cast<const float *>(w), scale,
                      static_cast<cudaStream_t>(stream));
+}
+
+int fft_backward_weighted_dev(fft_plan_t p, const void *X, const void *w, const void *scale_dev, float scale,
+                              void *grad_in, void *stream) {
+    if (!p || p->kind != 0 || !w || !aligned16(w) || !scale_dev ||
+        (reinterpret_cast<uintptr_t>(scale_dev) & 3))
+        return FFT_ERR_INVALID_ARG;
+    p->last_use_host = false;
+    return run_dense(p, X, grad_in, -p->dir, static_cast<const float *>(w), scale,
+                     static_cast<cudaStream_t>(stream), static_cast<const float *>(scale_dev));
 }
 
 int fft_weighted_power_parts(fft_plan_t p) { return p ? p->wp_parts : FFT_ERR_INVALID_ARG; }

@@ -52,7 +52,8 @@ template <int N, int E, bool WEIGHTED, int P>
 __global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
     k_rows(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
            const float2 *__restrict__ twp, long long nrows, int ny, int conj_in, int conj_out,
-           const float *__restrict__ weight, float wscale, int pf_dist, int perm_t, int perm_g, int planar) {
+           const float *__restrict__ weight, float wscale, const float *__restrict__ wscale_dev, int pf_dist,
+           int perm_t, int perm_g, int planar) {
     using Sh = RowShape<N, E>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
@@ -66,6 +67,9 @@ __global__ void __launch_bounds__(RowShape<N, E>::THREADS, RowShape<N, E>::MINB)
     const int Q = ny / P;
     float2 *sm = smem + g * Eng::SMEM_ELEMS;
     const long long step = (long long)gridDim.x * ROWS;
+    if constexpr (WEIGHTED) {
+        if (wscale_dev) wscale *= __ldg(wscale_dev);  // a scale that lives on the device (no host read)
+    }
 
     // first input row of output row r, for input part p (P == 1: r itself)
     auto in_row = [&](long long r, int p) -> long long {
@@ -343,7 +347,8 @@ int row_grid(const RowVariant &v, long long nrows, int num_sms, bool weighted, i
 
 cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                         long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
-                        float wscale, int grid, int pf_dist, int perm_t, int perm_g, int planar, cudaStream_t s) {
+                        float wscale, const float *wscale_dev, int grid, int pf_dist, int perm_t, int perm_g,
+                        int planar, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
     if (split != 1 && split != 2) return cudaErrorInvalidValue;
     const void *fn = row_fn(v, weight != nullptr, split);
@@ -358,7 +363,7 @@ cudaError_t launch_rows(const RowVariant &v, const float2 *in, float2 *out, cons
         return cudaErrorInvalidValue;
     void *args[] = {(void *)&in,      (void *)&out,     (void *)&tw,       (void *)&twp,    (void *)&nrows,
                     (void *)&ny,      (void *)&conj_in, (void *)&conj_out, (void *)&weight, (void *)&wscale,
-                    (void *)&pf_dist, (void *)&perm_t,  (void *)&perm_g,   (void *)&planar};
+                    (void *)&wscale_dev, (void *)&pf_dist, (void *)&perm_t, (void *)&perm_g, (void *)&planar};
     return cudaLaunchKernel(fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 

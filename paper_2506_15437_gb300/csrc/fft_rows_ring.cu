@@ -38,7 +38,7 @@ template <int N, int E, int P, bool WEIGHTED>
 __global__ void __launch_bounds__(RingShape<N, E>::THREADS, RingShape<N, E>::MINB)
     k_rows_ring(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
                 const float2 *__restrict__ twp, long long nrows, int ny, int conj_in, int conj_out,
-                const float *__restrict__ weight, float wscale, int *status) {
+                const float *__restrict__ weight, float wscale, const float *__restrict__ wscale_dev, int *status) {
     using Sh = RingShape<N, E>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::THREADS;
@@ -50,6 +50,9 @@ __global__ void __launch_bounds__(RingShape<N, E>::THREADS, RingShape<N, E>::MIN
     __shared__ int s_ok;
 
     const int tt = threadIdx.x;
+    if constexpr (WEIGHTED) {
+        if (wscale_dev) wscale *= __ldg(wscale_dev);  // a scale that lives on the device (no host read)
+    }
     const float si = conj_in ? -1.f : 1.f;
     const float so = conj_out ? -1.f : 1.f;
     const int Q = ny / P;
@@ -222,7 +225,7 @@ int ring_rows_grid(int n, long long nrows, int split, int num_sms, bool weighted
 
 cudaError_t launch_rows_ring(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              long long nrows, int ny, int split, int conj_in, int conj_out, const float *weight,
-                             float wscale, int *status, int grid, cudaStream_t s) {
+                             float wscale, const float *wscale_dev, int *status, int grid, cudaStream_t s) {
     const RingEntry *en = ring_entry(n);
     if (!en || (split != 1 && split != 2) || grid < 1) return cudaErrorInvalidValue;
     if (nrows <= 0) return cudaSuccess;
@@ -231,7 +234,7 @@ cudaError_t launch_rows_ring(int n, const float2 *in, float2 *out, const float2 
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&in,       (void *)&out,    (void *)&tw,     (void *)&twp,
                     (void *)&nrows,    (void *)&ny,     (void *)&conj_in, (void *)&conj_out,
-                    (void *)&weight,   (void *)&wscale, (void *)&status};
+                    (void *)&weight,   (void *)&wscale, (void *)&wscale_dev, (void *)&status};
     return cudaLaunchKernel(fn, dim3(grid), dim3(en->threads), args, en->smem, s);
 }
 

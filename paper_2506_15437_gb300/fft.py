@@ -105,6 +105,21 @@ class Plan:
                 "fft_backward_weighted")
         return out
 
+    def backward_weighted_dev(self, X: torch.Tensor, w: torch.Tensor, scale_dev: torch.Tensor,
+                              scale: float = 1.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """F^H (scale * scale_dev * w (.) X) with scale_dev a one-element
+        float32 CUDA tensor read on the device (no host synchronisation)."""
+        out = self._io(X, out)
+        _check_tensor(w, torch.float32, "w")
+        _check_tensor(scale_dev, torch.float32, "scale_dev")
+        if w.numel() != self.numel or scale_dev.numel() != 1:
+            raise ValueError("w must have the plan's size and scale_dev one element")
+        N.check(self._lib.fft_backward_weighted_dev(self._p, X.data_ptr(), w.data_ptr(), scale_dev.data_ptr(),
+                                                    ctypes.c_float(scale), out.data_ptr(),
+                                                    _stream_handle(X.device)),
+                "fft_backward_weighted_dev")
+        return out
+
     def weighted_power(self, X: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
         """sum w*|X|^2 as a float64 0-d tensor (partials reduced by torch)."""
         _check_tensor(X, torch.complex64, "X")
@@ -235,8 +250,10 @@ class WeightedPowerLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gL):
         X, w = ctx.saved_tensors
-        scale = 2.0 * float(gL)
-        return ctx.plan.backward_weighted(X, w, scale), None, None
+        # the upstream gradient stays on the device: the adjoint's first pass
+        # reads it, so backward issues no host synchronisation
+        g = gL.detach().to(device=X.device, dtype=torch.float32).reshape(1).contiguous()
+        return ctx.plan.backward_weighted_dev(X, w, g, 2.0), None, None
 
 
 def weighted_power_loss(x: torch.Tensor, w: torch.Tensor, precision: str = "fp32") -> torch.Tensor:

@@ -85,10 +85,9 @@ def tol_bluestein_axis(n: int) -> float:
 
 
 def tol_mixed_axis(n: int) -> float:
-    """Mixed radix: the power-of-two bound per radix-2-equivalent level
-    (2e-7 * log2 n) plus one level for each odd-radix stage, whose DFT folds
-    the legs into sums and differences before its multiply-adds."""
-    return 2e-7 * (math.log2(n) + odd_factors(n))
+    """Mixed radix (one pass or the four-step form): the plain path's bound
+    2e-7 * log2 n, with log2 n the radix-2-equivalent depth of the length."""
+    return 2e-7 * math.log2(n)
 
 
 def mixed_fourstep_eligible(n: int) -> bool:
@@ -101,16 +100,13 @@ def mixed_fourstep_eligible(n: int) -> bool:
 def tol_any_axis(n: int, mixed: bool = True) -> float:
     """FP32 bound for one axis of any length: a power of two is the plain
     path (2e-7 * log2 n); a 7-smooth length up to MIXED_MAX_N the mixed-radix
-    kernel, a longer one its four-step form (two more levels: the inter-pass
-    twiddle is the product of two rounded table entries), unless `mixed` is
-    False (the plan was made with it switched off); any other length
-    Bluestein."""
+    kernel and a longer one its four-step form, both held to the same
+    2e-7 * log2 n, unless `mixed` is False (the plan was made with it switched
+    off); any other length Bluestein."""
     if n & (n - 1) == 0:
         return 2e-7 * max(1.0, math.log2(n))
-    if mixed and mixed_eligible(n):
+    if mixed and (mixed_eligible(n) or mixed_fourstep_eligible(n)):
         return tol_mixed_axis(n)
-    if mixed and mixed_fourstep_eligible(n):
-        return tol_mixed_axis(n) + 2 * 2e-7
     return tol_bluestein_axis(n)
 
 

@@ -71,27 +71,17 @@ def test_config2_square_full(g, n, inverse):
 
 
 @pytest.mark.parametrize("inverse", [False, True])
-def test_config2_8192_sampled(g, inverse):
-    """8192^2 in the bench's launch configuration: sampled output rows and
-    columns against the oracle's one-row / one-column evaluation, plus
-    Parseval over the whole transform."""
+def test_config2_8192_full(g, inverse):
+    """8192^2 in the bench's launch configuration (landed-pair rows with the
+    column pre-split, streaming planar columns): every output element
+    against the oracle's full transform of the same input."""
     n = 8192
     x = synth.normal_complex((n, n), seed=2506)
     got = run_plan(g, x, inverse)
-    d = 1 if inverse else -1
-    rng = np.random.default_rng(7)
-    ky = np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 4)])
-    kx = np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 4)])
-    rows = oracle.fft2d_rows(x, ky, dir=d, threads=ORACLE_THREADS)
-    cols = oracle.fft2d_cols(x, kx, dir=d, threads=ORACLE_THREADS)
-    tol = tol_fp32(n * n)
-    for t, k in enumerate(ky):
-        assert rel_l2(got[k], rows[t]) <= tol, ("row", k)
-    for t, k in enumerate(kx):
-        assert rel_l2(got[:, k], cols[t]) <= tol, ("col", k)
-    e_in = np.sum(np.abs(x.astype(np.complex128)) ** 2)
-    e_out = np.sum(np.abs(got.astype(np.complex128)) ** 2)
-    assert abs(e_out / (n * n * e_in) - 1.0) < 1e-5
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    err = rel_l2(got, ref)
+    print(f"8192^2 inverse={inverse}: whole-output rel L2 {err:.3e} (bound {tol_fp32(n * n):.2e})")
+    assert err <= tol_fp32(n * n)
 
 
 @pytest.mark.parametrize("ny,nx", [(8192, 2), (2, 8192), (8192, 16), (16, 8192), (4096, 64),
@@ -108,13 +98,14 @@ def test_batched_2d(g):
 
 
 def test_batch_of_1d_signals_4096(g):
-    """nx=4096, ny=1, batch 16384 (the 1D batch workload), sampled signals."""
+    """nx=4096, ny=1, batch 16384 (the 1D batch workload): every signal."""
     x, _ = synth.exp_mix_1d(16384, 4096, seed=2506)
     plan = g.get_plan(4096, 1, 16384, False, "fp32", "cuda")
     out = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
-    idx = np.array([0, 1, 777, 8191, 16383])
-    ref = oracle.fft1d_batch(x[idx], threads=ORACLE_THREADS)
-    assert worst_rel_l2(out[idx], ref, 4096) <= tol_fp32(4096)
+    ref = oracle.fft1d_batch(x, threads=ORACLE_THREADS)
+    err = worst_rel_l2(out, ref, 4096)
+    print(f"1D 4096 x 16384: worst per-signal rel L2 {err:.3e}")
+    assert err <= tol_fp32(4096)
 
 
 def test_exponential_spikes_2048(g):
