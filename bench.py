@@ -503,6 +503,24 @@ def profile_form(torch, name, steps, warmup, dev):
         upstream = torch.ones(1, dtype=torch.float32, device=dev)
         run = lambda: (plan.execute(x, out=X), plan.weighted_power(X, w),  # noqa: E731
                        plan.backward_weighted_dev(X, w, upstream, 2.0))
+    elif name == "fp32_8192":
+        # the headline transform alone (row pass, column pass)
+        x = torch.from_numpy(synth.normal_complex((8192, 8192), seed=SEED)).to(dev)
+        plan = g.Plan(8192, 8192, 1)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
+    elif name == "bluestein_4095":
+        # 8192 signals of 4095 = 3^2 5 7 13 points: fused Bluestein over M = 8192
+        x = torch.from_numpy(synth.uniform_complex((8192, 4095), seed=SEED)).to(dev)
+        plan = g.Plan(4095, 1, 8192)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
+    elif name == "transpose_2d":
+        # 4096 x 4093 (4093 prime): the y axis runs between two tiled transposes
+        x = torch.from_numpy(synth.uniform_complex((4093, 4096), seed=SEED)).to(dev)
+        plan = g.Plan(4096, 4093, 1)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     elif name == "mixed_3000":
         # 8192 signals of 3000 = 2^3 3 5^3 points (mixed radix, 196 MB each way)
         x = torch.from_numpy(synth.uniform_complex((8192, 3000), seed=SEED)).to(dev)
@@ -542,8 +560,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
-                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "ragged", "diff", "fourstep_2p24",
-                             "fourstep_2p26", "mixed_3000"],
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff",
+                             "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

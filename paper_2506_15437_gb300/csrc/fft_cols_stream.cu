@@ -35,7 +35,7 @@
 
 namespace gb300fft {
 
-template <int N, int E, int W, int S>
+template <int N, int E, int W, int S, bool TS>
 struct StreamShape {
     using Eng = Engine<N, E, W, PadShift<E>::value>;
     static constexpr int T = N / E;   // stage-0 butterflies per column
@@ -52,18 +52,27 @@ struct StreamShape {
     // pad(w * SEG_ELEMS); a warp without a ring slot lands its segment there
     static constexpr int xch_seg(int w) { return Eng::pad(w * SEG_ELEMS); }
     static constexpr size_t RING_OFF = ((size_t)Eng::SMEM_ELEMS * sizeof(float2) + 127) / 128 * 128;
-    static constexpr size_t BAR_OFF = RING_OFF + (size_t)S * SEG_BYTES;
+    // TS: outputs leave through TMA stores.  Stage-1 output k of thread
+    // (tt, c) is output row tt + T*k; a warp's G butterflies are G adjacent
+    // rows tt, so KB consecutive k form a box of KB x G rows x W columns,
+    // staged per warp in two alternating chunks.
+    static constexpr int KB = 8;
+    static constexpr int CHUNK_ELEMS = KB * G * W;
+    static constexpr size_t STG_OFF = RING_OFF + (size_t)S * SEG_BYTES;
+    static constexpr size_t STG_BYTES = TS ? (size_t)WARPS * 2 * CHUNK_ELEMS * sizeof(float2) : 0;
+    static constexpr size_t BAR_OFF = STG_OFF + STG_BYTES;
     static constexpr size_t SMEM = BAR_OFF + 8 * WARPS + 16;
+    static_assert(E % KB == 0 && (CHUNK_ELEMS * sizeof(float2)) % 128 == 0, "store chunks");
     static_assert(WARPS * G == T, "one warp per G butterflies");
     static_assert(S >= 1 && S <= WARPS, "ring slots");
     static_assert(Eng::pad((WARPS - 1) * SEG_ELEMS) + SEG_ELEMS <= Eng::SMEM_ELEMS, "landing span");
 };
 
-template <int N, int E, int W, int S>
-__global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
-    k_cols_stream(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw, int nx,
-                  int batch, int P, int conj_out, int *status, int planar) {
-    using Sh = StreamShape<N, E, W, S>;
+template <int N, int E, int W, int S, bool TS>
+__global__ void __launch_bounds__(StreamShape<N, E, W, S, TS>::THREADS, 1)
+    k_cols_stream(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap omap, float2 *out,
+                  const float2 *__restrict__ tw, int nx, int batch, int P, int conj_out, int *status, int planar) {
+    using Sh = StreamShape<N, E, W, S, TS>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
     constexpr int R0 = Sh::R0;
@@ -72,6 +81,7 @@ __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
     extern __shared__ __align__(128) unsigned char raw[];
     float2 *xch = reinterpret_cast<float2 *>(raw);
     float2 *ring = reinterpret_cast<float2 *>(raw + Sh::RING_OFF);
+    float2 *stg = reinterpret_cast<float2 *>(raw + Sh::STG_OFF);  // TS: [warp][2][CHUNK_ELEMS]
     uint64_t *full = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);  // one per warp
     __shared__ int s_fail;
     __shared__ int s_armed[WARPS];
@@ -107,7 +117,6 @@ __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
             tma_load_3d(dst + k * Sh::BOXR * W, &map, x, kp, z0 + k * Sh::BOXR, full + w);
         s_armed[w] += 1;
     };
-
     if (t == 0) {
         s_fail = 0;
         for (int w = 0; w < WARPS; ++w) {
@@ -170,14 +179,43 @@ __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
         const long long blk = id / groups_x;  // b*P + kp
         const long long b = blk / P;
         const int kp = (int)(blk - b * P);
-        float2 *dst = out + (b * N * P + kp) * (long long)nx + (long long)(id % groups_x) * W + c;
-        const long long rstride = (long long)P * nx;
+        if constexpr (TS) {
+            // output box (x, kp, rows tt of this warp, k-blocks) of the map
+            // {floats of a row, kp, ky mod T, slice*E + ky / T}
+            float2 *wst = stg + (size_t)warp * 2 * Sh::CHUNK_ELEMS;
+            const int xo = (int)(id % groups_x) * 2 * W;
+            const int kb0 = (int)b * E;
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            float2 x = v[k];
-            x.y *= so;
-            dst[(long long)(tt + k * (N / E)) * rstride] = x;
+            for (int rr = 0; rr < E / Sh::KB; ++rr) {
+                float2 *cb = wst + (rr & 1) * Sh::CHUNK_ELEMS;
+                if (lane == 0) bulk_wait_read_1();  // the chunk's store of two rounds ago has read it
+                __syncwarp();
+#pragma unroll
+                for (int kk = 0; kk < Sh::KB; ++kk) {
+                    float2 x = v[rr * Sh::KB + kk];
+                    x.y *= so;
+                    cb[(kk * G + ttl) * W + c] = x;
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_4d(&omap, cb, xo, kp, warp * G, kb0 + rr * Sh::KB);
+                    bulk_commit();
+                }
+            }
+        } else {
+            float2 *dst = out + (b * N * P + kp) * (long long)nx + (long long)(id % groups_x) * W + c;
+            const long long rstride = (long long)P * nx;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                float2 x = v[k];
+                x.y *= so;
+                dst[(long long)(tt + k * (N / E)) * rstride] = x;
+            }
         }
+    }
+    if constexpr (TS) {
+        if (lane == 0) bulk_wait_all();  // this warp's stores are complete before the CTA leaves
     }
     if (s_fail && t == 0) {
         record_status(status, kStatusTimeout);
@@ -192,43 +230,72 @@ __global__ void __launch_bounds__(StreamShape<N, E, W, S>::THREADS, 1)
 namespace {
 struct StreamEntry {
     ColVariant v;
-    int g = 0, r0 = 0;
+    int g = 0, r0 = 0, t = 0, kb = 0;
 };
-StreamEntry g_stream;
+StreamEntry g_stream[2];  // [TMA stores]
 std::once_flag g_stream_once;  // registry filled once, safe across host threads
+
+template <int N, int E, int W, int S, bool TS>
+void reg_stream(StreamEntry &en) {
+    using Sh = StreamShape<N, E, W, S, TS>;
+    en.v.fn = (const void *)k_cols_stream<N, E, W, S, TS>;
+    en.v.n = N;
+    en.v.e = E;
+    en.v.w = W;
+    en.v.threads = Sh::THREADS;
+    en.v.smem = Sh::SMEM;
+    en.v.box_rows = Sh::BOXR;
+    en.v.tw_size = Sched<N, E>::tw_size;
+    en.g = Sh::G;
+    en.r0 = Sh::R0;
+    en.t = Sh::T;
+    en.kb = Sh::KB;
+}
 
 void init_stream() {
     std::call_once(g_stream_once, [] {
-        constexpr int N = 4096, E = 64, W = 4, S = 5;  // 130 KiB exchange + 80 KiB ring
-        using Sh = StreamShape<N, E, W, S>;
-        g_stream.v.fn = (const void *)k_cols_stream<N, E, W, S>;
-        g_stream.v.n = N;
-        g_stream.v.e = E;
-        g_stream.v.w = W;
-        g_stream.v.threads = Sh::THREADS;
-        g_stream.v.smem = Sh::SMEM;
-        g_stream.v.box_rows = Sh::BOXR;
-        g_stream.v.tw_size = Sched<N, E>::tw_size;
-        g_stream.g = Sh::G;
-        g_stream.r0 = Sh::R0;
+        // 130 KiB exchange + 80 KiB ring; with TMA stores 130 KiB + 64 KiB
+        // ring + 32 KiB store staging
+        reg_stream<4096, 64, 4, 5, false>(g_stream[0]);
+        reg_stream<4096, 64, 4, 4, true>(g_stream[1]);
     });
 }
 }  // namespace
 
-const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g) {
+const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g, int tstore) {
     init_stream();
-    if (n != g_stream.v.n || nx < g_stream.v.w) return nullptr;
-    if (perm_t) *perm_t = n / g_stream.r0;
-    if (perm_g) *perm_g = g_stream.g;
-    return &g_stream.v;
+    const StreamEntry &en = g_stream[tstore ? 1 : 0];
+    if (n != en.v.n || nx < en.v.w) return nullptr;
+    if (perm_t) *perm_t = n / en.r0;
+    if (perm_g) *perm_g = en.g;
+    return &en.v;
 }
 
-cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw, int nx,
-                               int batch, int split, int conj_out, int *status, int grid, int planar, cudaStream_t s) {
+bool stream_tstore(const ColVariant &v) {
+    init_stream();
+    return v.fn == g_stream[1].v.fn;
+}
+
+int encode_stream_store_map(CUtensorMap *map, const ColVariant &v, const void *base, int nx, long long rows,
+                            int split) {
+    init_stream();
+    const StreamEntry &en = g_stream[1];
+    if (v.fn != en.v.fn) return -1;
+    const int T = en.t;  // output row ky = tt + T*k
+    if (split < 1 || rows % ((long long)split * T) != 0) return -1;
+    return encode_map4(map, base, nx, rows, split, T, en.v.w, en.g, en.kb);
+}
+
+cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, const CUtensorMap *omap, float2 *out,
+                               const float2 *tw, int nx, int batch, int split, int conj_out, int *status, int grid,
+                               int planar, cudaStream_t s) {
+    const bool ts = stream_tstore(v);
+    if (ts && !omap) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     if (e != cudaSuccess) return e;
     CUtensorMap m = map;
-    void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&nx,     (void *)&batch,
+    CUtensorMap om = ts ? *omap : map;  // unused by the plain-store kernel
+    void *args[] = {(void *)&m,     (void *)&om,    (void *)&out,      (void *)&tw,     (void *)&nx, (void *)&batch,
                     (void *)&split, (void *)&conj_out, (void *)&status, (void *)&planar};
     return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, v.smem, s);
 }

@@ -128,16 +128,22 @@ cudaError_t build_roots_strided(float2 *t, int count, long long n, long long str
 // per pair q, both output rows kp = 0, 1, stored like launch_rows stores them.
 bool land_rows_available(int n, int e);
 cudaError_t launch_rows_land(const float2 *in, float2 *out, const float2 *tw, const float2 *twp, int ny, int batch,
-                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms,
+                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms, int pf,
                              cudaStream_t s);
 
 // Streaming column pass (fft_cols_stream.cu) over a row-permuted
 // intermediate: the variant for column length n and row length nx, or
 // nullptr; *perm_t / *perm_g receive the row permutation launch_rows must
 // apply (perm_t = stage-0 butterflies T, perm_g = butterflies per warp G).
-const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g);
-cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw, int nx,
-                               int batch, int split, int conj_out, int *status, int grid, int planar, cudaStream_t s);
+// tstore: the variant whose outputs leave through TMA stores (4D map from
+// encode_stream_store_map); else plain global stores.
+const ColVariant *stream_col_variant(int n, int nx, int *perm_t, int *perm_g, int tstore = 1);
+bool stream_tstore(const ColVariant &v);
+int encode_stream_store_map(CUtensorMap *map, const ColVariant &v, const void *base, int nx, long long rows,
+                            int split);
+cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, const CUtensorMap *omap, float2 *out,
+                               const float2 *tw, int nx, int batch, int split, int conj_out, int *status, int grid,
+                               int planar, cudaStream_t s);
 
 // Reorder-map debug launchers: write map[i] = output position of input i.
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s);
@@ -151,6 +157,11 @@ void set_last_error(int code);
 // 2w floats x 1 x box_rows.
 int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, int split, int w,
                    int box_rows);
+// 4D tensor map over the same buffer seen as (float within row, kp < split,
+// r mod t, r / t) with row = kp + split * r; boxes of 2w floats x 1 x
+// box_rows x box_k.
+int encode_map4(CUtensorMap *map, const void *base, int nx, long long rows, int split, int t, int w, int box_rows,
+                int box_k);
 
 // Tunable schedule of a dense plan (every field has a default).
 enum { kColTile = 0, kColPair = 1, kColCluster = 2 };
@@ -166,8 +177,10 @@ struct Schedule {
     int col_c = 2;         // cluster size of the DSMEM column kernel
     int col_pf = 0;        // TMA column pass: L2 prefetch distance (tiles)
     int col_stream = 1;    // out-of-place calls: streaming column pass over row-permuted rows, where compiled
+    int col_tstore = 1;    // streaming column pass through TMA stores: 1 unsplit blocks, 2 always, 0 never
     int planar = 1;        // pre-split plans with the streaming pass: blocks as planes of a workspace
     int row_land = 1;      // pre-split 8192-point rows: one CTA per landed pair of input rows
+    int land_pf = 1;       // landed-pair rows: L2 prefetch distance in pairs
 };
 
 // One axis of a dense plan: a row-pass length (contiguous) or a column-pass
@@ -191,6 +204,9 @@ struct AxisPlan {
     // column pass: cached tensor map of the last output pointer
     CUtensorMap map;
     const void *map_base = nullptr;
+    // streaming column pass with TMA stores: cached output map
+    CUtensorMap omap;
+    const void *omap_base = nullptr;
 };
 
 

@@ -92,6 +92,8 @@ void apply_env_overrides(Schedule *sc) {
     geti("GB300FFT_COL_W", &sc->col_w);
     geti("GB300FFT_COL_PF", &sc->col_pf);
     geti("GB300FFT_COL_STREAM", &sc->col_stream);
+    geti("GB300FFT_COL_TSTORE", &sc->col_tstore);
+    geti("GB300FFT_LAND_PF", &sc->land_pf);
     geti("GB300FFT_PLANAR", &sc->planar);
     geti("GB300FFT_ROW_LAND", &sc->row_land);
     if (const char *ev = getenv("GB300FFT_COL_CLUSTER")) {
@@ -155,6 +157,7 @@ bool tune_cache_lookup(int nx, int ny, int batch, int prec, Schedule *sc) {
         sc->col_w = json_int(l, "col_w", sc->col_w);
         sc->col_c = json_int(l, "col_c", sc->col_c);
         sc->col_stream = json_int(l, "col_stream", sc->col_stream);
+        sc->col_tstore = json_int(l, "col_tstore", sc->col_tstore);
         sc->planar = json_int(l, "planar", sc->planar);
         sc->row_land = json_int(l, "row_land", sc->row_land);
         found = true;  // the last matching line wins
@@ -176,10 +179,11 @@ void tune_cache_store(int nx, int ny, int batch, int prec, const Schedule &sc, f
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"row_e\": %d, \"row_persist\": %d, \"row_pf\": %d, \"split\": %d, "
-            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"planar\": %d, "
+            "\"col_kind\": %d, \"col_e\": %d, \"col_w\": %d, \"col_c\": %d, \"col_stream\": %d, \"col_tstore\": %d, "
+            "\"planar\": %d, "
             "\"row_land\": %d, \"ms\": %.5f}\n",
             tune_key(nx, ny, batch, prec).c_str(), sc.row_e, sc.row_persist, sc.row_pf, sc.split, sc.col_kind,
-            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, sc.planar, sc.row_land, ms);
+            sc.col_e, sc.col_w, sc.col_c, sc.col_stream, sc.col_tstore, sc.planar, sc.row_land, ms);
     fclose(f);
 }
 
@@ -275,7 +279,7 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
     if (grid < 1) grid = 1;
     ax.grid = (int)grid;
     int pt = 0, pg = 0;
-    const ColVariant *sv = sc.col_stream ? stream_col_variant(n, nx, &pt, &pg) : nullptr;
+    const ColVariant *sv = sc.col_stream ? stream_col_variant(n, nx, &pt, &pg, sc.col_tstore) : nullptr;
     if (sv && sv->w == ax.col->w && sv->box_rows == ax.col->box_rows) {
         ax.stream = sv;
         ax.perm_t = pt;
@@ -399,7 +403,11 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         const int split =
             (sc.split == 2 && ny >= 4 && p->rows.row && row_split_available(p->rows.n, p->rows.row->e)) ? 2 : 1;
         if (rc == FFT_OK && split > 1) {
-            rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split, sc);
+            // TMA stores for the pre-split blocks only when asked for (2):
+            // their output rows lie P apart and plain stores measured faster
+            Schedule ss = sc;
+            if (ss.col_tstore == 1) ss.col_tstore = 0;
+            rc = setup_col_axis(p, p->cols_split, ny / split, nx, (long long)nx * batch * split, ss);
             if (rc == FFT_OK) {
                 p->twp = dev_alloc<float2>(p, ny);
                 if (!p->twp) rc = FFT_ERR_ALLOC;
@@ -764,7 +772,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     const cudaError_t er =
         land ? launch_rows_land(src, row_dst, p->rows.tw, p->twp, p->ny, p->batch, inv ? 1 : 0,
                                 stream ? cp.perm_t : 0, stream ? cp.perm_g : 0, planar ? 1 : 0, p->status,
-                                p->num_sms, s)
+                                p->num_sms, p->sched.land_pf, s)
         : p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
                                    (inv && !two_pass) ? 1 : 0, weight, wscale, wscale_dev, p->status, grid, s)
                 : launch_rows(*p->rows.row, src, row_dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
@@ -797,13 +805,19 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
+    if (stream && stream_tstore(*cp.stream) && cp.omap_base != out) {
+        if (encode_stream_store_map(&cp.omap, *cp.stream, out, p->nx, (long long)p->ny * p->batch, P) != 0)
+            return FFT_ERR_CUDA;
+        cp.omap_base = out;
+    }
     if (!planar && cp.map_base != out) {
         if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.col->w, cp.col->box_rows) != 0)
             return FFT_ERR_CUDA;
         cp.map_base = out;
     }
     const cudaError_t ec =
-        stream ? launch_cols_stream(*cp.stream, planar ? p->planar_map : cp.map, dst, cp.stream_tw, p->nx, p->batch, P,
+        stream ? launch_cols_stream(*cp.stream, planar ? p->planar_map : cp.map, &cp.omap, dst, cp.stream_tw, p->nx,
+                                    p->batch, P,
                                     inv ? 1 : 0, p->status, cp.stream_grid, planar ? 1 : 0, s)
                : launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid,
                              p->col_pf, s);
@@ -824,6 +838,23 @@ int encode_col_map(CUtensorMap *map, const void *base, int nx, long long rows, i
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+int encode_map4(CUtensorMap *map, const void *base, int nx, long long rows, int split, int t, int w, int box_rows,
+                int box_k) {
+    EncodeTiledFn enc = get_encode_fn();
+    if (!enc || split < 1 || t < 1 || rows % ((long long)split * t)) return -1;
+    // (float within a row, kp, r mod t, r / t): row = kp + split * r
+    const cuuint64_t rs = (cuuint64_t)nx * sizeof(float2);
+    cuuint64_t dims[4] = {(cuuint64_t)2 * nx, (cuuint64_t)split, (cuuint64_t)t,
+                          (cuuint64_t)(rows / ((long long)split * t))};
+    cuuint64_t strides[3] = {rs, rs * split, rs * split * t};
+    cuuint32_t box[4] = {(cuuint32_t)(2 * w), 1, (cuuint32_t)box_rows, (cuuint32_t)box_k};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }
@@ -1078,6 +1109,9 @@ int fft_plan_autotune(fft_plan_t p, void *stream) {
                     Schedule d = c;
                     d.col_stream = 0;
                     cands.push_back(d);
+                    Schedule t = c;
+                    t.col_tstore = 0;
+                    cands.push_back(t);
                     if (split == 2) {
                         Schedule e = c;
                         e.planar = 0;
@@ -1202,7 +1236,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "{\"kind\": \"dense\", \"precision\": \"%s\", \"rows\": {\"kernel\": \"%s<%d,%d,split%d>\", "
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
-                     "\"grid\": %d}, \"split\": %d}",
+                     "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d}",
                      tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
                      !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
@@ -1210,7 +1244,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
                      cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
                      cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0, r2,
-                     cp.grid, p->split);
+                     cp.grid, p->split, (!tc && cp.stream && !p->ring && stream_tstore(*cp.stream)) ? 1 : 0);
     }
     if (len > 0) {
         const int c = k < len - 1 ? k : len - 1;

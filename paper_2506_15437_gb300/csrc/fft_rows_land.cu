@@ -36,7 +36,7 @@ template <int N, int E>
 __global__ void __launch_bounds__(LandShape<N, E>::THREADS, 1)
     k_rows_land(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
                 const float2 *__restrict__ twp, int ny, long long npairs, int conj_in, int perm_t, int perm_g,
-                int planar, int *status) {
+                int planar, int *status, int pf) {
     using Sh = LandShape<N, E>;
     using Eng = typename Sh::Eng;
     constexpr int T = Sh::T;
@@ -65,10 +65,23 @@ __global__ void __launch_bounds__(LandShape<N, E>::THREADS, 1)
         fence_proxy_async_smem();
     }
     __syncthreads();
+    // L2 bulk prefetch of pair `pid`'s two input rows (thread 0)
+    auto prefetch = [&](long long pid) {
+        const long long b = pid / Q;
+        const int q = (int)(pid - b * Q);
+        bulk_prefetch_l2(in + (b * ny + q) * (long long)N, N * sizeof(float2));
+        bulk_prefetch_l2(in + (b * ny + q + Q) * (long long)N, N * sizeof(float2));
+    };
     long long id = blockIdx.x;
     uint32_t phase = 0;
-    if (t == 0 && id < npairs) issue(id);
+    if (t == 0 && id < npairs) {
+        issue(id);
+        for (int d = 1; d < pf; ++d)
+            if (id + (long long)d * gridDim.x < npairs) prefetch(id + (long long)d * gridDim.x);
+    }
     for (; id < npairs; id += gridDim.x) {
+        // the pair pf steps ahead starts moving into L2 while this one computes
+        if (t == 0 && pf > 0 && id + (long long)pf * gridDim.x < npairs) prefetch(id + (long long)pf * gridDim.x);
         if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
         __syncthreads();
         if (!s_ok) {
@@ -138,7 +151,7 @@ void init_land() {
 bool land_rows_available(int n, int e) { return n == 8192 && e == 32; }
 
 cudaError_t launch_rows_land(const float2 *in, float2 *out, const float2 *tw, const float2 *twp, int ny, int batch,
-                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms,
+                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms, int pf,
                              cudaStream_t s) {
     init_land();
     if (ny < 2 || ny % 2) return cudaErrorInvalidValue;
@@ -151,7 +164,8 @@ cudaError_t launch_rows_land(const float2 *in, float2 *out, const float2 *tw, co
     long long grid = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
     if (grid > npairs) grid = npairs;
     void *args[] = {(void *)&in,     (void *)&out,    (void *)&tw,     (void *)&twp,   (void *)&ny,    (void *)&npairs,
-                    (void *)&conj_in, (void *)&perm_t, (void *)&perm_g, (void *)&planar, (void *)&status};
+                    (void *)&conj_in, (void *)&perm_t, (void *)&perm_g, (void *)&planar, (void *)&status,
+                    (void *)&pf};
     return cudaLaunchKernel(g_land_fn, dim3((unsigned)grid), dim3(g_land_threads), args, g_land_smem, s);
 }
 
