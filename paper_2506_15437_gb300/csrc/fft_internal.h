@@ -83,6 +83,20 @@ cudaError_t launch_rows_tc(int n, int tcg, const float2 *in, float2 *out, const 
 cudaError_t launch_cols_tc(int n, int w, int tcg, const CUtensorMap &map, float2 *out, const float2 *tw,
                            const void *w16, int nx, int batch, int split, int conj_out, int *status, int grid,
                            cudaStream_t s);
+// Split-FP16 tensor-core variants with radix-32 tcgen05 stages (fft_tc32.cu):
+// rows and columns of 1024..8192 points; the plan owns the FP64-built B table.
+cudaError_t build_w32_table(void *t, cudaStream_t s);
+constexpr size_t kW32TableBytes = 2 * 64 * 64 * 2;
+bool tc32_rows_available(int n);
+int tc32_col_width(int n, int nx);
+int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
+cudaError_t launch_rows_tc32(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                             const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
+                             int *status, cudaStream_t s);
+cudaError_t launch_cols_tc32(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32,
+                             int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+// Entries of the stage twiddle table of the (n, e) schedule (build_twiddles).
+int twiddle_table_size(int n, int e);
 // Column pass by 2-CTA clusters (fft_cols_pair.cu): block length n = 2 * N2.
 int pair_cols_width(int n, int e, int nx);
 int pair_cols_tw_size(int n, int e);
@@ -193,6 +207,7 @@ struct AxisPlan {
     int grid = 0;  // column pass: persistent grid size
     int tc_w = 0;  // tensor-core column pass: tile width
     int tcg = 0;   // tensor-core column pass: 1 tcgen05 butterflies, 0 mma.sync
+    int tc32 = 0;  // tensor-core pass with radix-32 tcgen05 stages (rows: the plan's rows axis)
     int pair_e = 0;  // >0: column pass by 2-CTA clusters with this E (length n/2 sub-FFTs)
     int cl_c = 0, cl_e = 0;  // >0: column pass by cl_c-CTA DSMEM clusters with E = cl_e
     float2 *roots = nullptr;  // pair column pass: exp(-2*pi*i*k/n), k < n
@@ -366,6 +381,8 @@ struct fft_plan_s {
     int col_pf = 0;        // column pass: L2 prefetch distance in tiles (0: measured best)
     int *status = nullptr;  // device status word
     void *w16 = nullptr;    // split-FP16 plans: hi/lo W16 table (FP64-built)
+    void *w32 = nullptr;    // split-FP16 plans with radix-32 stages: hi/lo B table (FP64-built)
+    int tc_radix = 32;      // split-FP16 plans: largest tensor-core radix allowed (32, or 16)
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events

@@ -194,6 +194,11 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n, const Schedule &sc) {
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (!tc_rows_available(n)) return FFT_ERR_UNSUPPORTED;
         e = 16;
+        // radix-32 tensor-core stages (tcgen05 only) where compiled
+        if (p->tcg && p->tc_radix >= 32 && p->w32 && tc32_rows_available(n)) {
+            e = 32;
+            ax.tc32 = 1;
+        }
     } else if (sc.row_e > 0 && row_variant(ilog2(n), sc.row_e)) {
         e = sc.row_e;
     }
@@ -217,6 +222,23 @@ int setup_row_axis(fft_plan_s *p, AxisPlan &ax, int n, const Schedule &sc) {
 
 int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_per_w, const Schedule &sc) {
     ax.n = n;
+    if (p->prec == FFT_PREC_SPLIT_FP16_TC && p->tcg && p->tc_radix >= 32 && p->w32 && tc32_col_width(n, nx) > 0) {
+        // radix-32 tcgen05 column pass: E = 32 twiddles, tiles of tc_w columns
+        ax.tc32 = 1;
+        ax.tcg = 1;
+        ax.tc_w = tc32_col_width(n, nx);
+        ax.col = col_variant(ilog2(n), 16 > n ? n : 16, 2);  // keeps ax.col non-null (the pass exists)
+        if (!ax.col) return FFT_ERR_UNSUPPORTED;
+        const int sz = twiddle_table_size(n, 32);
+        if (sz < 0) return FFT_ERR_UNSUPPORTED;
+        if (sz > 0) {
+            ax.tw = dev_alloc<float2>(p, sz);
+            if (!ax.tw) return FFT_ERR_ALLOC;
+            if (build_twiddles(ax.tw, n, 32, 0) != cudaSuccess) return FFT_ERR_CUDA;
+        }
+        ax.grid = tc32_cols_grid(n, ax.tc_w, tiles_per_w / ax.tc_w, p->num_sms);
+        return ax.grid > 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
+    }
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         ax.tc_w = tc_col_width(n, nx);
         if (ax.tc_w == 0) return FFT_ERR_UNSUPPORTED;
@@ -383,9 +405,15 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
     if (rc == FFT_OK && precision == FFT_PREC_SPLIT_FP16_TC) {
         if (const char *ev = getenv("GB300FFT_TC_MMA")) p->tcg = strcmp(ev, "sync") != 0;
         if (p->tcg && !tcg_available(nx > 1 ? nx : ny, 1, 0)) p->tcg = 0;
+        if (const char *ev = getenv("GB300FFT_TC_RADIX")) p->tc_radix = atoi(ev) >= 32 ? 32 : 16;
         p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
         if (!p->w16) rc = FFT_ERR_ALLOC;
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+        if (rc == FFT_OK && p->tcg && p->tc_radix >= 32) {
+            p->w32 = dev_alloc<unsigned char>(p, kW32TableBytes);
+            if (!p->w32) rc = FFT_ERR_ALLOC;
+            else if (build_w32_table(p->w32, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+        }
     }
     if (rc != FFT_OK) {
     } else if ((nx == 1 || ny == 1) && (nx > 8192 || ny > 8192)) {
@@ -400,8 +428,17 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         // Column pre-split: a length-8192 column needs a 128 KiB tile (one CTA
         // per SM); splitting it as 2 x 4096 halves the tile.  Only row
         // schedules compiled with the pre-split take it.
-        const int split =
+        int split =
             (sc.split == 2 && ny >= 4 && p->rows.row && row_split_available(p->rows.n, p->rows.row->e)) ? 2 : 1;
+        if (precision == FFT_PREC_SPLIT_FP16_TC && p->rows.tc32) {
+            // radix-32 tensor-core rows: pre-split when ny = 8192 (as on the
+            // FP32 path); GB300FFT_TC_SPLIT = 1 or 2 overrides
+            split = ny >= 8192 ? 2 : 1;
+            if (const char *ev = getenv("GB300FFT_TC_SPLIT")) {
+                const int v = atoi(ev);
+                if ((v == 1 || v == 2) && ny % v == 0 && ny / v >= 16) split = v;
+            }
+        }
         if (rc == FFT_OK && split > 1) {
             // TMA stores for the pre-split blocks only when asked for (2):
             // their output rows lie P apart and plain stores measured faster
@@ -737,9 +774,12 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (weight) return FFT_ERR_UNSUPPORTED;
         if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
-        if (launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P, inv ? 1 : 0,
-                           (inv && !two_pass) ? 1 : 0, p->status, s) != cudaSuccess)
-            return FFT_ERR_CUDA;
+        const cudaError_t er =
+            p->rows.tc32 ? launch_rows_tc32(p->rows.n, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
+                                            inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s)
+                         : launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P,
+                                          inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s);
+        if (er != cudaSuccess) return FFT_ERR_CUDA;
         if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
         if (two_pass) {
             if (cp.map_base != out) {
@@ -748,9 +788,12 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                     return FFT_ERR_CUDA;
                 cp.map_base = out;
             }
-            if (launch_cols_tc(cp.n, cp.tc_w, cp.tcg, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P, inv ? 1 : 0,
-                               p->status, cp.grid, s) != cudaSuccess)
-                return FFT_ERR_CUDA;
+            const cudaError_t ec =
+                cp.tc32 ? launch_cols_tc32(cp.n, cp.tc_w, cp.map, dst, cp.tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
+                                           p->status, cp.grid, s)
+                        : launch_cols_tc(cp.n, cp.tc_w, cp.tcg, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P,
+                                         inv ? 1 : 0, p->status, cp.grid, s);
+            if (ec != cudaSuccess) return FFT_ERR_CUDA;
         }
         if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
@@ -1218,7 +1261,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
     } else {
         const bool tc = p->prec == FFT_PREC_SPLIT_FP16_TC;
         char r1[96] = "[]", r2[96] = "[]";
-        const int re = p->rows.row ? (tc ? 16 : p->rows.row->e) : 1;
+        const int re = p->rows.row ? (tc ? (p->rows.tc32 ? 32 : 16) : p->rows.row->e) : 1;
         if (p->rows.row) rad(p->rows.n, re, r1, sizeof r1);
         const gb300fft::AxisPlan &cp = p->split > 1 ? p->cols_split : p->cols;
         if (cp.cl_c > 0) {
@@ -1230,19 +1273,19 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
             rad(cp.n / 2, cp.pair_e, r3, sizeof r3);
             snprintf(r2, sizeof r2, "[2,%s", r3 + 1);
         } else if (cp.col) {
-            rad(cp.n, tc ? 16 : cp.col->e, r2, sizeof r2);
+            rad(cp.n, tc ? (cp.tc32 ? 32 : 16) : cp.col->e, r2, sizeof r2);
         }
         k = snprintf(tmp, sizeof tmp,
                      "{\"kind\": \"dense\", \"precision\": \"%s\", \"rows\": {\"kernel\": \"%s<%d,%d,split%d>\", "
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
                      "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d}",
-                     tc ? "split_fp16_tc" : "fp32", tc ? (p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
+                     tc ? "split_fp16_tc" : "fp32", tc ? (p->rows.tc32 ? "k_rows_tc32" : p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
-                     !cp.col ? "none" : tc ? (cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
-                     cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
+                     !cp.col ? "none" : tc ? (cp.tc32 ? "k_cols_tc32" : cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
+                     cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (cp.tc32 ? 32 : 16) : cp.col->e) : 0,
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
-                     cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? 16 : cp.col->e) : 0,
+                     cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (cp.tc32 ? 32 : 16) : cp.col->e) : 0,
                      cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0, r2,
                      cp.grid, p->split, (!tc && cp.stream && !p->ring && stream_tstore(*cp.stream)) ? 1 : 0);
     }

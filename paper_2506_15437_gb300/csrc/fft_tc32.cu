@@ -1,0 +1,667 @@
+// Split-FP16 tensor-core form with radix-32 stages on tcgen05.
+//
+// Every radix-32 butterfly of the Stockham engine (Section 2.2's butterflies,
+// 32 points at a time) is the product y = W32 x with W32[k][r] =
+// exp(-2*pi*i*k*r/32).  In real arithmetic, x = (xr, xi) stacked as a
+// 64-vector, y = B x with the 64 x 64 matrix B = [[Wr, -Wi], [Wi, Wr]].  B is
+// split once, in FP64, as B = B_hi + B_lo (both float16; B_lo holds the
+// rounding error of B_hi unscaled).  Each butterfly is scaled by 2048 / s, s
+// the power of two just above its largest |component|, so every scaled value
+// has |xs| < 2048, and split as xs = hi + lo: hi keeps the top 11 significant
+// bits of xs (mask of the float32 mantissa, exact in float16), lo = xs - hi
+// (exact in float32, rounded once to float16).  Three products are kept,
+//     D1 = B_hi hi,   D2 = B_hi lo + B_lo hi,   y = (D1 + D2) * s / 2048,
+// accumulated in float32 in two TMEM accumulators (after Ootomo & Yokota's
+// error-corrected tensor-core GEMM; B_lo lo is below 2^-21 relative).
+//
+// One 128-thread group holds 128 butterflies, one per thread and one per row
+// of A: the M = 128 x N = 64 x K = 64 product is 4 K-steps x 3 products =
+// 12 tcgen05.mma (kind::f16, f32 accumulate) issued by one thread and
+// committed to the group's mbarrier.  The A operand is staged in the same
+// shared memory the stage's exchange uses (its reads are complete by then),
+// so a row CTA needs only its exchange, the 16 KiB B and no extra staging.
+// A 8192-point transform is then radix 8 (float32) + two radix-32 tensor-core
+// stages; 4096 is 4 + 32 + 32, 2048 is 2 + 32 + 32, 1024 is 32 + 32.
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "fft_common.cuh"
+#include "fft_internal.h"
+
+namespace gb300fft {
+
+constexpr int kT32E = 32;                 // elements per thread = the tensor-core radix
+constexpr int kT32Group = 128;            // threads (butterflies) per MMA group
+constexpr int kT32ABytes = 128 * 64 * 2;  // one float16 A operand of a group: 128 rows x 64 halves (16 KiB)
+constexpr int kT32GroupStage = 2 * kT32ABytes;  // A_hi + A_lo of a group: 32 KiB
+constexpr int kT32BBytes = 64 * 64 * 2;   // one float16 B operand (8 KiB)
+static_assert(kT32GroupStage == 32768, "A_hi + A_lo of a group");
+
+// B_hi then B_lo (64 x 64 float16 each) in the canonical K-major layout of the
+// tensor-core descriptors: element (n, k) at byte (n/8)*1024 + (k/8)*128 +
+// (n%8)*16 + (k%8)*2.  Built in FP64 once per plan.
+__global__ void k_w32_table(__half *t) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // 4096 entries
+    if (idx >= 64 * 64) return;
+    const int n = idx >> 6, k = idx & 63;
+    const int kr = k & 31, nr = n & 31;
+    double sv, cv;
+    sincospi(2.0 * (double)((nr * kr) & 31) / 32.0, &sv, &cv);
+    const double wr = cv, wi = -sv;
+    // [[Wr, -Wi], [Wi, Wr]]: rows 0-31 the real outputs, 32-63 the imaginary
+    const double b = (n < 32) ? (k < 32 ? wr : -wi) : (k < 32 ? wi : wr);
+    const __half hi = __double2half(b);
+    const __half lo = __double2half(b - (double)__half2float(hi));
+    const int off = ((n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2;
+    t[off] = hi;
+    t[kT32BBytes / 2 + off] = lo;
+}
+
+cudaError_t build_w32_table(void *t, cudaStream_t s) {
+    k_w32_table<<<16, 256, 0, s>>>(static_cast<__half *>(t));
+    return cudaGetLastError();
+}
+
+// Shared-memory descriptor of a K-major operand without swizzle: core
+// matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes apart, 8-row
+// groups 1024 bytes apart (K = 64 halves).
+__device__ __forceinline__ uint64_t t32_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+// kind::f16: D = F32 (bit 4), A = B = F16, both K-major, N = 64, M = 128
+constexpr uint32_t kT32Idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void t32_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kT32Idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void t32_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// try_wait that may suspend the thread up to `ns` nanoseconds in hardware
+// instead of returning at once, so waiting threads do not spin.
+__device__ __forceinline__ bool t32_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (~limit_ns of global time, at most 2^20 suspended polls).
+__device__ __forceinline__ bool t32_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        if (t32_try_wait_sleep(bar, parity, 20000)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t f2h2_bits(float lo_elem, float hi_elem) {
+    const __half2 h = __floats2half2_rn(lo_elem, hi_elem);  // .x (low half) = lo_elem
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// Per-CTA tensor-core state of the radix-32 butterflies.
+struct Tc32 {
+    unsigned char *bsm;    // B_hi, B_lo (16 KiB) in shared memory
+    unsigned char *stage;  // this group's A_hi (16 KiB) then A_lo (16 KiB)
+    uint64_t *bar;         // this group's mbarrier
+    uint32_t tmem;         // this group's D1 column (D2 = +64), lane field 0
+    int *status;
+    uint32_t phase;
+    int group, row;        // group index, row of A (thread within the group)
+
+    // Every thread of the CTA calls init (it synchronises).  `bsrc` is the
+    // global B table, `bsm_p` 16 KiB of shared memory, `bars` one mbarrier
+    // per group, `slot` a shared word for the TMEM base, `stage_base` the
+    // (exchange) memory the groups stage A in, 32 KiB per group.
+    __device__ void init(const __half *__restrict__ bsrc, unsigned char *bsm_p, uint64_t *bars, uint32_t *slot,
+                         unsigned char *stage_base, int *status_word) {
+        const int t = threadIdx.x;
+        const int ngroups = blockDim.x / kT32Group;
+        status = status_word;
+        bsm = bsm_p;
+        group = t / kT32Group;
+        row = t % kT32Group;
+        bar = bars + group;
+        stage = stage_base + (size_t)group * kT32GroupStage;
+        phase = 0;
+        const uint4 *src = reinterpret_cast<const uint4 *>(bsrc);
+        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
+        for (int i = t; i < 2 * kT32BBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+        const uint32_t cols = (uint32_t)ngroups * 128;  // 128, 256 or 512: powers of two
+        if (t < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                         "r"(cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        if (t == 0) {
+            for (int g = 0; g < ngroups; ++g) mbar_init(bars + g, 1);
+            fence_mbar_init();
+        }
+        fence_proxy_async_smem();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = *slot + (uint32_t)(group * 128);
+    }
+
+    // Every thread calls finish once all its tensor-core work is done.
+    __device__ void finish() {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x < 32) {
+            const uint32_t base_col = tmem - (uint32_t)(group * 128);
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base_col),
+                         "r"((uint32_t)(blockDim.x / kT32Group) * 128)
+                         : "memory");
+        }
+    }
+
+    // The calling thread's length-32 DFT (forward sign) of v, in place.
+    // Every thread of the CTA must call it: it starts with a CTA barrier
+    // (the staging area is the exchange the stage has just read).  If `hook`
+    // is true, `after_mma()` runs once every group's products are complete
+    // (all threads, after a CTA barrier): the staging memory is free again.
+    template <class AfterMma>
+    __device__ __forceinline__ void dft32(float2 (&v)[kT32E], bool hook, AfterMma after_mma) {
+        // scale: s = 2^(eb - 126) > max |component|; xs = x * 2048 / s
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < kT32E; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].x), fabsf(v[k].y)));
+        int eb = (__float_as_int(m) >> 23) & 0xff;
+        eb = eb < 11 ? 11 : eb;  // keeps both scale factors normal (tiny or zero rows)
+        const float up = __int_as_float((264 - eb) << 23);  // 2^(137 - eb) = 2048 / s
+        const float down = __int_as_float((eb - 10) << 23);  // 2^(eb - 137) = s / 2048
+        __syncthreads();  // every thread has read the exchange: it becomes the staging area
+        // row `row` of A_hi / A_lo: 8 chunks of 8 halves (re 0-31, then im 0-31)
+        unsigned char *row_hi = stage + (row >> 3) * 1024 + (row & 7) * 16;
+        unsigned char *row_lo = row_hi + kT32ABytes;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k0 = (c & 3) * 8 + 2 * q;
+                const float x0 = ((c & 4) ? v[k0].y : v[k0].x) * up;
+                const float x1 = ((c & 4) ? v[k0 + 1].y : v[k0 + 1].x) * up;
+                const float h0 = __int_as_float(__float_as_int(x0) & 0xFFFFE000);
+                const float h1 = __int_as_float(__float_as_int(x1) & 0xFFFFE000);
+                wh[q] = f2h2_bits(h0, h1);
+                wl[q] = f2h2_bits(x0 - h0, x1 - h1);
+            }
+            *reinterpret_cast<uint4 *>(row_hi + c * 128) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4 *>(row_lo + c * 128) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        named_sync(1 + group, kT32Group);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (row == 0) {
+            const uint32_t a_hi = smem_u32(stage), a_lo = a_hi + kT32ABytes;
+            const uint32_t b_hi = smem_u32(bsm), b_lo = b_hi + kT32BBytes;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {  // K = 64 as four K = 16 steps (two core chunks each)
+                t32_mma(tmem, t32_desc(a_hi + ks * 256), t32_desc(b_hi + ks * 256), ks);
+                t32_mma(tmem + 64, t32_desc(a_lo + ks * 256), t32_desc(b_hi + ks * 256), ks);
+                t32_mma(tmem + 64, t32_desc(a_hi + ks * 256), t32_desc(b_lo + ks * 256), 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        if (!t32_wait(bar, phase)) record_status(status, kStatusTimeout);
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (hook) {
+            __syncthreads();
+            after_mma();
+        }
+        // this warp's 32 TMEM lanes; columns 0-31 real outputs, 32-63 imaginary
+        const uint32_t lane = (uint32_t)(threadIdx.x & 96) << 16;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t d1[16], d2[16];
+            t32_ld16(tmem + lane + h * 16, d1);
+            t32_ld16(tmem + 64 + lane + h * 16, d2);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float y = (__int_as_float(d1[k]) + __int_as_float(d2[k])) * down;
+                if (h < 2)
+                    v[(h & 1) * 16 + k].x = y;
+                else
+                    v[(h & 1) * 16 + k].y = y;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Row pass: T = N/32 threads per row, 256 threads per CTA (two groups), two
+// CTAs per SM (128 registers, 86 KiB of shared memory, 256 TMEM columns
+// each), one CTA per row group.  Optional column pre-split P = 2 as in the
+// FP32 row pass (the 2-point DFT across rows q and q + ny/2 and the twiddle
+// w_ny^q), so the column pass runs on blocks of ny/2 rows.
+// ---------------------------------------------------------------------------
+template <int N>
+struct T32RowShape {
+    static constexpr int E = kT32E;
+    static constexpr int T = N / E;
+    static constexpr int ROWS = 256 / T;
+    static constexpr int THREADS = 256;
+    using Eng = Engine<N, E, 1, PadShift<E>::value, RowPadShift1<E>::value>;
+    static constexpr int R0 = Eng::R0;
+    static constexpr int S = Eng::S;
+    static constexpr size_t EX_BYTES = sizeof(float2) * (size_t)ROWS * Eng::SMEM_ELEMS;
+    static constexpr size_t B_OFF = (EX_BYTES + 1023) / 1024 * 1024;
+    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;
+    static constexpr size_t SMEM = BAR_OFF + 64;
+    static_assert(T >= 32 && 256 % T == 0, "rows of 1024..8192 points");
+    static_assert(EX_BYTES >= 2 * (size_t)kT32GroupStage, "the exchange holds both groups' A staging");
+    static_assert(S >= 2 && (R0 == E || R0 < E), "stage 0 radix");
+};
+
+template <int N, int P>
+__global__ void __launch_bounds__(256, 2)
+    k_rows_tc32(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
+                const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nrows, int ny, int conj_in,
+                int conj_out, int *status) {
+    using Sh = T32RowShape<N>;
+    using Eng = typename Sh::Eng;
+    using Sc = Sched<N, kT32E>;
+    constexpr int E = kT32E;
+    constexpr int T = Sh::T;
+    constexpr int R0 = Sh::R0;
+    constexpr int S = Sh::S;
+    static_assert(P == 1 || P == 2, "pre-split of 1 or 2");
+    extern __shared__ __align__(1024) unsigned char raw[];
+    float2 *ex = reinterpret_cast<float2 *>(raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::BAR_OFF + 32);
+    Tc32 tc;
+    tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
+    const int g = threadIdx.x / T;
+    const int tt = threadIdx.x - g * T;
+    const long long row = (long long)blockIdx.x * Sh::ROWS + g;
+    const bool active = row < nrows;
+    const float si = conj_in ? -1.f : 1.f;
+    const float so = conj_out ? -1.f : 1.f;
+    const int Q = ny / P;
+    int kp = 0, q = 0;
+    long long in0 = row;
+    if constexpr (P > 1) {
+        const long long b = active ? row / ny : 0;
+        const int y = active ? (int)(row - b * ny) : 0;
+        kp = y % P;
+        q = y / P;
+        in0 = b * ny + q;
+    }
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < E / R0; ++b) {
+        const int j = tt + b * T;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+            const int i = j + r * (N / R0);
+            float2 x = active ? __ldg(in + in0 * N + i) : make_float2(0.f, 0.f);
+            x.y *= si;
+            if constexpr (P == 2) {
+                float2 y = active ? __ldg(in + (in0 + Q) * N + i) : make_float2(0.f, 0.f);
+                y.y *= si;
+                x = kp ? csub(x, y) : cadd(x, y);
+            }
+            v[b * R0 + r] = x;
+        }
+    }
+    if constexpr (P == 2) {
+        if (kp) {
+            const float2 w = __ldg(twp + q);
+#pragma unroll
+            for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
+        }
+    }
+    auto none = [] {};
+    float2 *sm = ex + g * Eng::SMEM_ELEMS;
+    // stage 0
+    if constexpr (R0 == E) {
+        tc.dft32(v, false, none);
+    } else {
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) dft<R0>(&v[b * R0]);
+    }
+    // stages 1 .. S-1: exchange, twiddles, tensor-core radix-32
+#pragma unroll
+    for (int s = 1; s < S; ++s) {
+        const int Rp = (s == 1) ? R0 : E;
+        const int Nsp = Sc::ns(s - 1);
+        if (s > 1 || R0 == E) __syncthreads();  // the previous stage's staging / exchange reads are done
+#pragma unroll
+        for (int b = 0; b < E / Rp; ++b) {
+            const int j = tt + b * T;
+            const int m = j & (Nsp - 1);
+#pragma unroll
+            for (int k = 0; k < Rp; ++k) sm[Eng::pad_s((j - m) * Rp + m + k * Nsp, s)] = v[b * Rp + k];
+        }
+        __syncthreads();
+        const int Ns = Sc::ns(s);
+        const int m = tt & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = sm[Eng::pad_s(tt + r * T, s)];
+        const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) {
+            const float4 w2 = __ldg(tws + k * Ns);
+            v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w2.x, w2.y));
+            if (2 * k + 2 < E) v[2 * k + 2] = cmul(v[2 * k + 2], make_float2(w2.z, w2.w));
+        }
+        tc.dft32(v, false, none);
+    }
+    if (active) {
+        float2 *dst = out + row * N;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            float2 x = v[k];
+            x.y *= so;
+            dst[tt + k * T] = x;
+        }
+    }
+    tc.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: tiles of W adjacent columns x N rows staged by TMA (3D map,
+// rows P apart), T*W threads = 128, 256 or 512 (one to four groups), one CTA
+// per SM, persistent.  The tile buffer is also the exchange and the A staging;
+// the next tile's copy starts once the last stage's products are complete.
+// ---------------------------------------------------------------------------
+template <int N, int W>
+struct T32ColShape {
+    static constexpr int E = kT32E;
+    static constexpr int T = N / E;
+    static constexpr int THREADS = T * W;
+    static constexpr int GROUPS = THREADS / kT32Group;
+    using Sc = Sched<N, E>;
+    static constexpr int R0 = Sc::R0;
+    static constexpr int S = Sc::S;
+    // exchange index swizzle: element i of the [N][W] tile lives at
+    // i ^ (((i >> 4) & (16/W - 1)) * W), a permutation within each 16-element
+    // group that puts the 16 lanes of every half-warp access on distinct
+    // bank pairs for all stage writes and reads (half-warp bank model), so
+    // the exchange needs no padding
+    static_assert(W >= 2 && W <= 16, "tile widths 2..16");
+    __host__ __device__ static constexpr int sw(int i) { return i ^ (((i >> 4) & (16 / W - 1)) * W); }
+    static constexpr int ELEMS = N * W;
+    static constexpr int BOXR = N < 256 ? N : 256;
+    static constexpr uint32_t TILE_BYTES = (uint32_t)N * W * sizeof(float2);
+    static constexpr size_t B_OFF = ((size_t)ELEMS * sizeof(float2) + 1023) / 1024 * 1024;
+    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;
+    static constexpr size_t SMEM = BAR_OFF + 64;
+    static_assert(THREADS % kT32Group == 0 && THREADS <= 512, "one to four MMA groups");
+    static_assert((size_t)ELEMS * sizeof(float2) >= (size_t)GROUPS * kT32GroupStage, "tile holds the staging");
+    static_assert(S >= 2, "at least one exchange");
+    static_assert(2 * W * sizeof(float) >= 16, "TMA rows of at least 16 bytes");
+};
+
+template <int N, int W>
+__global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
+    k_cols_tc32(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw,
+                const __half *__restrict__ w32, int nx, int batch, int P, int conj_out, int *status) {
+    using Sh = T32ColShape<N, W>;
+    using Sc = Sched<N, kT32E>;
+    constexpr int E = kT32E;
+    constexpr int T = Sh::T;
+    constexpr int R0 = Sh::R0;
+    constexpr int S = Sh::S;
+    extern __shared__ __align__(1024) unsigned char raw[];
+    float2 *tile = reinterpret_cast<float2 *>(raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);  // [0, 4): groups, [4]: tile
+    uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::BAR_OFF + 48);
+    uint64_t *tbar = bars + 4;
+    __shared__ int s_ok;
+    Tc32 tc;
+    tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
+
+    const int t = threadIdx.x;
+    const int c = t % W;
+    const int tt = t / W;
+    const int groups_x = nx / W;
+    const long long ntiles = (long long)groups_x * P * batch;
+    const float so = conj_out ? -1.f : 1.f;
+    auto issue = [&](long long id) {  // thread 0: TMA loads of tile `id`
+        const int x = (int)(id % groups_x) * 2 * W;
+        const int kp = (int)((id / groups_x) % P);
+        const int z0 = (int)((id / groups_x) / P) * N;
+        mbar_expect_tx(tbar, Sh::TILE_BYTES);
+#pragma unroll 1
+        for (int k = 0; k < N / Sh::BOXR; ++k) tma_load_3d(tile + k * Sh::BOXR * W, &map, x, kp, z0 + k * Sh::BOXR, tbar);
+    };
+    if (t == 0) {
+        mbar_init(tbar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long id = blockIdx.x;
+    uint32_t tphase = 0;
+    if (t == 0 && id < ntiles) issue(id);
+    for (; id < ntiles; id += gridDim.x) {
+        if (t == 0) s_ok = mbar_wait_bounded(tbar, tphase) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (t == 0) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(tbar, tphase);  // give the copy in flight a last chance to land
+            }
+            break;  // leave through finish(): the TMEM columns must be freed
+        }
+        tphase ^= 1;
+        const long long next = id + gridDim.x;
+        const long long blk = id / groups_x;
+        const long long b = blk / P;
+        const int kp = (int)(blk - b * P);
+        float2 v[E];
+#pragma unroll
+        for (int bb = 0; bb < E / R0; ++bb) {
+            const int j = tt + bb * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) v[bb * R0 + r] = tile[(j + r * (N / R0)) * W + c];
+        }
+        auto next_copy = [&] {  // every group's products are complete: the tile is free
+            if (t == 0 && next < ntiles) {
+                fence_proxy_async_smem();
+                issue(next);
+            }
+        };
+        if constexpr (R0 == E) {
+            tc.dft32(v, false, next_copy);
+        } else {
+#pragma unroll
+            for (int bb = 0; bb < E / R0; ++bb) dft<R0>(&v[bb * R0]);
+        }
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+            const int Rp = (s == 1) ? R0 : E;
+            const int Nsp = Sc::ns(s - 1);
+            __syncthreads();  // tile reads (s = 1) or the previous staging are done
+#pragma unroll
+            for (int bb = 0; bb < E / Rp; ++bb) {
+                const int j = tt + bb * T;
+                const int m = j & (Nsp - 1);
+#pragma unroll
+                for (int k = 0; k < Rp; ++k) tile[Sh::sw(((j - m) * Rp + m + k * Nsp) * W + c)] = v[bb * Rp + k];
+            }
+            __syncthreads();
+            const int Ns = Sc::ns(s);
+            const int m = tt & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = tile[Sh::sw((tt + r * T) * W + c)];
+            const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
+#pragma unroll
+            for (int k = 0; k < E / 2; ++k) {
+                const float4 w2 = __ldg(tws + k * Ns);
+                v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w2.x, w2.y));
+                if (2 * k + 2 < E) v[2 * k + 2] = cmul(v[2 * k + 2], make_float2(w2.z, w2.w));
+            }
+            tc.dft32(v, s == S - 1, next_copy);
+        }
+        float2 *dst = out + (b * N * P + kp) * (long long)nx + (long long)(id % groups_x) * W + c;
+        const long long rstride = (long long)P * nx;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            float2 x = v[k];
+            x.y *= so;
+            dst[(long long)(tt + k * T) * rstride] = x;
+        }
+    }
+    tc.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Variant tables and launchers.
+// ---------------------------------------------------------------------------
+namespace {
+struct T32RowEntry {
+    const void *fn[2] = {nullptr, nullptr};  // [P = 1, 2]
+    int rows_per_cta = 0;
+    size_t smem = 0;
+};
+struct T32ColEntry {
+    const void *fn = nullptr;
+    int threads = 0, w = 0;
+    size_t smem = 0;
+};
+T32RowEntry g_t32_rows[kMaxLog2 + 1];
+T32ColEntry g_t32_cols[kMaxLog2 + 1][4];  // W slot: 2, 4, 8, 16
+std::once_flag g_t32_once;
+
+int t32_w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : -1; }
+
+template <int N>
+void reg_t32_row() {
+    using Sh = T32RowShape<N>;
+    T32RowEntry &en = g_t32_rows[ilog2(N)];
+    en.fn[0] = (const void *)k_rows_tc32<N, 1>;
+    en.fn[1] = (const void *)k_rows_tc32<N, 2>;
+    en.rows_per_cta = Sh::ROWS;
+    en.smem = Sh::SMEM;
+}
+template <int N, int W>
+void reg_t32_col() {
+    using Sh = T32ColShape<N, W>;
+    T32ColEntry &en = g_t32_cols[ilog2(N)][t32_w_slot(W)];
+    en.fn = (const void *)k_cols_tc32<N, W>;
+    en.threads = Sh::THREADS;
+    en.w = W;
+    en.smem = Sh::SMEM;
+}
+void init_t32() {
+    std::call_once(g_t32_once, [] {
+        reg_t32_row<1024>();
+        reg_t32_row<2048>();
+        reg_t32_row<4096>();
+        reg_t32_row<8192>();
+        // 512-thread tiles (the split form's rows are at least 16 long, so
+        // every 2D shape has nx >= 16 columns to fill them)
+        // 512-thread tiles (the split form's rows are at least 16 long, so
+        // every 2D shape has nx >= 16 columns to fill them)
+        reg_t32_col<1024, 16>();
+        reg_t32_col<2048, 8>();
+        reg_t32_col<4096, 4>();
+        reg_t32_col<8192, 2>();
+    });
+}
+}  // namespace
+
+bool tc32_rows_available(int n) {
+    init_t32();
+    return n >= 1024 && n <= 8192 && (n & (n - 1)) == 0 && g_t32_rows[ilog2(n)].fn[0] != nullptr;
+}
+
+// Widest compiled tile (at most 512 threads) that fits nx columns; 0 if none.
+int tc32_col_width(int n, int nx) {
+    init_t32();
+    if (n < 1024 || n > 8192 || (n & (n - 1))) return 0;
+    int best = 0;
+    for (int w = 2; w <= 16 && w <= nx; w <<= 1)
+        if (g_t32_cols[ilog2(n)][t32_w_slot(w)].fn) best = w;
+    return best;
+}
+
+int tc32_cols_grid(int n, int w, long long ntiles, int num_sms) {
+    init_t32();
+    const int slot = t32_w_slot(w);
+    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn) return 0;
+    const T32ColEntry &en = g_t32_cols[ilog2(n)][slot];
+    cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, en.fn, en.threads, en.smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    // TMEM: 128 columns per group, 512 per SM
+    const int tmem_per_sm = 512 / ((en.threads / kT32Group) * 128);
+    if (per_sm > tmem_per_sm) per_sm = tmem_per_sm;
+    long long grid = (long long)num_sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    return grid < 1 ? 1 : (int)grid;
+}
+
+cudaError_t launch_rows_tc32(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                             const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
+                             int *status, cudaStream_t s) {
+    init_t32();
+    if (!tc32_rows_available(n) || (split != 1 && split != 2) || ny % split) return cudaErrorInvalidValue;
+    if (nrows <= 0) return cudaSuccess;
+    const T32RowEntry &en = g_t32_rows[ilog2(n)];
+    const void *fn = en.fn[split == 2 ? 1 : 0];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = (nrows + en.rows_per_cta - 1) / en.rows_per_cta;  // one CTA per row group
+    const __half *w = static_cast<const __half *>(w32);
+    void *args[] = {(void *)&in,    (void *)&out, (void *)&tw,      (void *)&twp,      (void *)&w,
+                    (void *)&nrows, (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&status};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(256), args, en.smem, s);
+}
+
+cudaError_t launch_cols_tc32(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32,
+                             int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s) {
+    init_t32();
+    const int slot = t32_w_slot(w);
+    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn || grid < 1) return cudaErrorInvalidValue;
+    const T32ColEntry &en = g_t32_cols[ilog2(n)][slot];
+    cudaError_t e = cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    if (e != cudaSuccess) return e;
+    CUtensorMap m = map;
+    const __half *wt = static_cast<const __half *>(w32);
+    void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&wt,     (void *)&nx,
+                    (void *)&batch, (void *)&split, (void *)&conj_out, (void *)&status};
+    return cudaLaunchKernel(en.fn, dim3(grid), dim3(en.threads), args, en.smem, s);
+}
+
+}  // namespace gb300fft

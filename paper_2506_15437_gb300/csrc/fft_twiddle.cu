@@ -38,6 +38,18 @@ __global__ void k_twiddles(float2 *tw, int r0, int e, int stages, int total) {
     }
 }
 
+int twiddle_table_size(int n, int e) {
+    int rad[16];
+    const int S = schedule_radices(n, e, rad);
+    if (S < 0) return -1;
+    long long total = 0, ns = rad[0];
+    for (int k = 1; k < S; ++k) {
+        total += (long long)rad[k] * ns;
+        ns *= rad[k];
+    }
+    return (int)total;
+}
+
 cudaError_t build_twiddles(float2 *tw, int n, int e, cudaStream_t s) {
     int rad[16];
     const int S = schedule_radices(n, e, rad);

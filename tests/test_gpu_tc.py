@@ -23,11 +23,13 @@ def g():
     return g
 
 
-@pytest.fixture(params=["tcgen05", "sync"])
+@pytest.fixture(params=["tcgen05", "tcgen05_r16", "sync"])
 def mma(request, monkeypatch):
     """Which tensor-core butterfly the split plans use: tcgen05 (TMEM
-    accumulators, the default) or mma.sync."""
-    monkeypatch.setenv("GB300FFT_TC_MMA", request.param)
+    accumulators; radix-32 stages for lengths 1024..8192, the default),
+    tcgen05 held to radix-16 stages, or mma.sync (radix 16)."""
+    monkeypatch.setenv("GB300FFT_TC_MMA", "sync" if request.param == "sync" else "tcgen05")
+    monkeypatch.setenv("GB300FFT_TC_RADIX", "16" if request.param != "tcgen05" else "32")
     return request.param
 
 
@@ -130,3 +132,65 @@ def test_split_tc_default_is_tcgen05(g):
     d = plan.describe()
     assert d["rows"]["kernel"].startswith("k_rows_tcgen05")
     assert d["cols"]["kernel"].startswith("k_cols_tcgen05")
+    # lengths 1024..8192: radix-32 tensor-core stages
+    plan = g.Plan(8192, 8192, 1, precision="split_tc")
+    d = plan.describe()
+    assert d["rows"]["kernel"].startswith("k_rows_tc32") and d["rows"]["radices"] == [8, 32, 32]
+    # the rows pre-split the columns by 2: 4096-point column blocks
+    assert d["split"] == 2
+    assert d["cols"]["kernel"].startswith("k_cols_tc32") and d["cols"]["radices"] == [4, 32, 32]
+    plan.close()
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(1024, 1024, 1), (2048, 2048, 1), (4096, 4096, 1), (1024, 16, 3),
+                                         (2048, 16, 2), (4096, 16, 2), (8192, 16, 1), (32, 8192, 2),
+                                         (8192, 64, 1), (16, 1024, 5), (8192, 1024, 1), (4096, 2048, 2)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse):
+    """Radix-32 tcgen05 stages on every compiled row length and column tile
+    (rows of 1024..8192 points; columns of 1024, 2048, 4096, 8192 points in
+    16-, 8-, 4- and 2-column tiles; the column pre-split at ny = 8192), both
+    directions, against the oracle."""
+    monkeypatch.setenv("GB300FFT_TC_MMA", "tcgen05")
+    monkeypatch.setenv("GB300FFT_TC_RADIX", "32")
+    plan = g.Plan(nx, ny, batch, inverse=inverse, precision="split_tc")
+    d = plan.describe()
+    x = synth.uniform_complex((batch, ny, nx), seed=7 * ny + nx + batch)
+    got = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.status() == 0
+    plan.close()
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    N = nx * ny
+    err = worst_rel_l2(got, ref, N)
+    print(f"tc32 {ny}x{nx}x{batch} inv={inverse} rows={d['rows']['kernel']} cols={d['cols']['kernel']}: {err:.3e}")
+    assert err <= tol_split_tc(N)
+    if nx >= 1024:
+        assert d["rows"]["kernel"].startswith("k_rows_tc32")
+    if ny >= 1024 and nx > 1:
+        assert d["cols"]["kernel"].startswith("k_cols_tc32")
+
+
+@pytest.mark.parametrize("ny,nx,split", [(8192, 1024, "2"), (8192, 1024, "1"), (4096, 4096, "2"), (4096, 1024, "1")])
+def test_radix32_column_presplit_choices(g, monkeypatch, ny, nx, split):
+    """The radix-32 row pass pre-splits the columns by 1 or 2 (the 2-point
+    DFT across rows q and q + ny/2 and the twiddle w_ny^q); every choice gives
+    the transform within the bound, out of place and in place (in place runs
+    unsplit)."""
+    monkeypatch.setenv("GB300FFT_TC_MMA", "tcgen05")
+    monkeypatch.setenv("GB300FFT_TC_RADIX", "32")
+    monkeypatch.setenv("GB300FFT_TC_SPLIT", split)
+    plan = g.Plan(nx, ny, 1, precision="split_tc")
+    monkeypatch.delenv("GB300FFT_TC_SPLIT")
+    d = plan.describe()
+    assert d["split"] == int(split)
+    assert d["cols"]["n"] == ny // int(split)
+    x = synth.uniform_complex((ny, nx), seed=ny + nx + int(split))
+    ref = oracle.fft2d(x, threads=ORACLE_THREADS)
+    xd = torch.from_numpy(x).cuda()
+    got = plan.execute(xd).cpu().numpy()
+    assert plan.status() == 0
+    assert rel_l2(got, ref) <= tol_split_tc(nx * ny)
+    plan.execute(xd, out=xd)
+    assert plan.status() == 0
+    assert rel_l2(xd.cpu().numpy(), ref) <= tol_split_tc(nx * ny)
+    plan.close()
