@@ -90,11 +90,13 @@ constexpr size_t kW32TableBytes = 2 * 64 * 64 * 2;
 bool tc32_rows_available(int n);
 int tc32_col_width(int n, int nx);
 int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
-cudaError_t launch_rows_tc32(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+// tmem_a: the A operand in tensor memory (else staged in shared memory)
+cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
                              int *status, cudaStream_t s);
-cudaError_t launch_cols_tc32(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32,
-                             int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s);
+cudaError_t launch_cols_tc32(int n, int w, int tmem_a, const CUtensorMap &map, float2 *out, const float2 *tw,
+                             const void *w32, int nx, int batch, int split, int conj_out, int *status, int grid,
+                             cudaStream_t s);
 // Entries of the stage twiddle table of the (n, e) schedule (build_twiddles).
 int twiddle_table_size(int n, int e);
 // Column pass by 2-CTA clusters (fft_cols_pair.cu): block length n = 2 * N2.
@@ -383,6 +385,7 @@ struct fft_plan_s {
     void *w16 = nullptr;    // split-FP16 plans: hi/lo W16 table (FP64-built)
     void *w32 = nullptr;    // split-FP16 plans with radix-32 stages: hi/lo B table (FP64-built)
     int tc_radix = 32;      // split-FP16 plans: largest tensor-core radix allowed (32, or 16)
+    int tc_tmem_a = 1;      // radix-32 tensor-core stages: A operand in tensor memory (0: shared memory)
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events

@@ -406,6 +406,7 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         if (const char *ev = getenv("GB300FFT_TC_MMA")) p->tcg = strcmp(ev, "sync") != 0;
         if (p->tcg && !tcg_available(nx > 1 ? nx : ny, 1, 0)) p->tcg = 0;
         if (const char *ev = getenv("GB300FFT_TC_RADIX")) p->tc_radix = atoi(ev) >= 32 ? 32 : 16;
+        if (const char *ev = getenv("GB300FFT_TC_TMEM_A")) p->tc_tmem_a = atoi(ev) != 0;
         p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
         if (!p->w16) rc = FFT_ERR_ALLOC;
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
@@ -775,7 +776,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (weight) return FFT_ERR_UNSUPPORTED;
         if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
         const cudaError_t er =
-            p->rows.tc32 ? launch_rows_tc32(p->rows.n, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
+            p->rows.tc32 ? launch_rows_tc32(p->rows.n, p->tc_tmem_a, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
                                             inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s)
                          : launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P,
                                           inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s);
@@ -789,7 +790,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                 cp.map_base = out;
             }
             const cudaError_t ec =
-                cp.tc32 ? launch_cols_tc32(cp.n, cp.tc_w, cp.map, dst, cp.tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
+                cp.tc32 ? launch_cols_tc32(cp.n, cp.tc_w, p->tc_tmem_a, cp.map, dst, cp.tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
                                            p->status, cp.grid, s)
                         : launch_cols_tc(cp.n, cp.tc_w, cp.tcg, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P,
                                          inv ? 1 : 0, p->status, cp.grid, s);

@@ -90,6 +90,21 @@ __device__ __forceinline__ void t32_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
+__device__ __forceinline__ void t32_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// MMA with A read from tensor memory (rows = lanes, two float16 per column).
+__device__ __forceinline__ void t32_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(kT32Idesc), "r"(accumulate)
+        : "memory");
+}
+
 // try_wait that may suspend the thread up to `ns` nanoseconds in hardware
 // instead of returning at once, so waiting threads do not spin.
 __device__ __forceinline__ bool t32_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
@@ -124,7 +139,13 @@ __device__ __forceinline__ uint32_t f2h2_bits(float lo_elem, float hi_elem) {
     return u;
 }
 
-// Per-CTA tensor-core state of the radix-32 butterflies.
+// Per-CTA tensor-core state of the radix-32 butterflies.  TA: the A operand
+// lives in tensor memory (each thread writes its own row with tcgen05.st;
+// one accumulator D = B_hi hi + B_hi lo + B_lo hi), so the stage needs no
+// shared-memory staging at all; otherwise A is staged in shared memory (the
+// caller's exchange) and the two products accumulate separately.
+// TMEM columns of a group: [0, 64) D (D1), [64, 96) A_hi or D2, [96, 128) A_lo.
+template <bool TA>
 struct Tc32 {
     unsigned char *bsm;    // B_hi, B_lo (16 KiB) in shared memory
     unsigned char *stage;  // this group's A_hi (16 KiB) then A_lo (16 KiB)
@@ -183,6 +204,75 @@ struct Tc32 {
         }
     }
 
+    // TA form of dft32: split into TMEM, 12 MMAs into one accumulator.  Every
+    // thread of the group calls it; no CTA barrier, no shared memory.
+    __device__ __forceinline__ void dft32_ta(float2 (&v)[kT32E]) {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < kT32E; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].x), fabsf(v[k].y)));
+        int eb = (__float_as_int(m) >> 23) & 0xff;
+        eb = eb < 11 ? 11 : eb;
+        const float up = __int_as_float((264 - eb) << 23);   // 2048 / s
+        const float down = __int_as_float((eb - 10) << 23);  // s / 2048
+        const uint32_t lane = (uint32_t)(threadIdx.x & 96) << 16;
+        // halves [16q, 16q + 16) of the row: q = 0, 1 real parts, q = 2, 3 imaginary
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t wh[8], wl[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const int k0 = (q & 1) * 16 + 2 * p;
+                const float x0 = ((q & 2) ? v[k0].y : v[k0].x) * up;
+                const float x1 = ((q & 2) ? v[k0 + 1].y : v[k0 + 1].x) * up;
+                const float h0 = __int_as_float(__float_as_int(x0) & 0xFFFFE000);
+                const float h1 = __int_as_float(__float_as_int(x1) & 0xFFFFE000);
+                wh[p] = f2h2_bits(h0, h1);
+                wl[p] = f2h2_bits(x0 - h0, x1 - h1);
+            }
+            t32_st8(tmem + lane + 64 + 8 * q, wh);
+            t32_st8(tmem + lane + 96 + 8 * q, wl);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        named_sync(1 + group, kT32Group);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (row == 0) {
+            const uint32_t b_hi = smem_u32(bsm), b_lo = b_hi + kT32BBytes;
+            // K = 64 as four K = 16 steps (8 TMEM columns of A each).  The
+            // small correction products accumulate first, at their own scale;
+            // the large B_hi hi terms come last, so only those four additions
+            // round at the scale of the result (as a separate accumulator and
+            // a final float32 add would)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 96 + 8 * ks, t32_desc(b_hi + ks * 256), ks);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 64 + 8 * ks, t32_desc(b_lo + ks * 256), 1);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 64 + 8 * ks, t32_desc(b_hi + ks * 256), 1);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        if (!t32_wait(bar, phase)) record_status(status, kStatusTimeout);
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t d[16];
+            t32_ld16(tmem + lane + h * 16, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float y = __int_as_float(d[k]) * down;
+                if (h < 2)
+                    v[(h & 1) * 16 + k].x = y;
+                else
+                    v[(h & 1) * 16 + k].y = y;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+
     // The calling thread's length-32 DFT (forward sign) of v, in place.
     // Every thread of the CTA must call it: it starts with a CTA barrier
     // (the staging area is the exchange the stage has just read).  If `hook`
@@ -190,6 +280,10 @@ struct Tc32 {
     // (all threads, after a CTA barrier): the staging memory is free again.
     template <class AfterMma>
     __device__ __forceinline__ void dft32(float2 (&v)[kT32E], bool hook, AfterMma after_mma) {
+        if constexpr (TA) {
+            dft32_ta(v);
+            return;
+        }
         // scale: s = 2^(eb - 126) > max |component|; xs = x * 2048 / s
         float m = 0.f;
 #pragma unroll
@@ -288,7 +382,7 @@ struct T32RowShape {
     static_assert(S >= 2 && (R0 == E || R0 < E), "stage 0 radix");
 };
 
-template <int N, int P>
+template <int N, int P, bool TA>
 __global__ void __launch_bounds__(256, 2)
     k_rows_tc32(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
                 const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nrows, int ny, int conj_in,
@@ -305,7 +399,7 @@ __global__ void __launch_bounds__(256, 2)
     float2 *ex = reinterpret_cast<float2 *>(raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
     uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::BAR_OFF + 32);
-    Tc32 tc;
+    Tc32<TA> tc;
     tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
     const int g = threadIdx.x / T;
     const int tt = threadIdx.x - g * T;
@@ -429,7 +523,7 @@ struct T32ColShape {
     static_assert(2 * W * sizeof(float) >= 16, "TMA rows of at least 16 bytes");
 };
 
-template <int N, int W>
+template <int N, int W, bool TA>
 __global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
     k_cols_tc32(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw,
                 const __half *__restrict__ w32, int nx, int batch, int P, int conj_out, int *status) {
@@ -445,7 +539,7 @@ __global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
     uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::BAR_OFF + 48);
     uint64_t *tbar = bars + 4;
     __shared__ int s_ok;
-    Tc32 tc;
+    Tc32<TA> tc;
     tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
 
     const int t = threadIdx.x;
@@ -522,6 +616,12 @@ __global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
             const int m = tt & (Ns - 1);
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = tile[Sh::sw((tt + r * T) * W + c)];
+            if constexpr (TA) {
+                if (s == S - 1) {  // A goes to tensor memory: the tile is free once every thread has read it
+                    __syncthreads();
+                    next_copy();
+                }
+            }
             const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
 #pragma unroll
             for (int k = 0; k < E / 2; ++k) {
@@ -529,7 +629,7 @@ __global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
                 v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w2.x, w2.y));
                 if (2 * k + 2 < E) v[2 * k + 2] = cmul(v[2 * k + 2], make_float2(w2.z, w2.w));
             }
-            tc.dft32(v, s == S - 1, next_copy);
+            tc.dft32(v, !TA && s == S - 1, next_copy);
         }
         float2 *dst = out + (b * N * P + kp) * (long long)nx + (long long)(id % groups_x) * W + c;
         const long long rstride = (long long)P * nx;
@@ -548,12 +648,12 @@ __global__ void __launch_bounds__(T32ColShape<N, W>::THREADS, 1)
 // ---------------------------------------------------------------------------
 namespace {
 struct T32RowEntry {
-    const void *fn[2] = {nullptr, nullptr};  // [P = 1, 2]
+    const void *fn[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [A in TMEM][P = 1, 2]
     int rows_per_cta = 0;
     size_t smem = 0;
 };
 struct T32ColEntry {
-    const void *fn = nullptr;
+    const void *fn[2] = {nullptr, nullptr};  // [A in TMEM]
     int threads = 0, w = 0;
     size_t smem = 0;
 };
@@ -567,8 +667,10 @@ template <int N>
 void reg_t32_row() {
     using Sh = T32RowShape<N>;
     T32RowEntry &en = g_t32_rows[ilog2(N)];
-    en.fn[0] = (const void *)k_rows_tc32<N, 1>;
-    en.fn[1] = (const void *)k_rows_tc32<N, 2>;
+    en.fn[0][0] = (const void *)k_rows_tc32<N, 1, false>;
+    en.fn[0][1] = (const void *)k_rows_tc32<N, 2, false>;
+    en.fn[1][0] = (const void *)k_rows_tc32<N, 1, true>;
+    en.fn[1][1] = (const void *)k_rows_tc32<N, 2, true>;
     en.rows_per_cta = Sh::ROWS;
     en.smem = Sh::SMEM;
 }
@@ -576,7 +678,8 @@ template <int N, int W>
 void reg_t32_col() {
     using Sh = T32ColShape<N, W>;
     T32ColEntry &en = g_t32_cols[ilog2(N)][t32_w_slot(W)];
-    en.fn = (const void *)k_cols_tc32<N, W>;
+    en.fn[0] = (const void *)k_cols_tc32<N, W, false>;
+    en.fn[1] = (const void *)k_cols_tc32<N, W, true>;
     en.threads = Sh::THREADS;
     en.w = W;
     en.smem = Sh::SMEM;
@@ -601,7 +704,7 @@ void init_t32() {
 
 bool tc32_rows_available(int n) {
     init_t32();
-    return n >= 1024 && n <= 8192 && (n & (n - 1)) == 0 && g_t32_rows[ilog2(n)].fn[0] != nullptr;
+    return n >= 1024 && n <= 8192 && (n & (n - 1)) == 0 && g_t32_rows[ilog2(n)].fn[0][0] != nullptr;
 }
 
 // Widest compiled tile (at most 512 threads) that fits nx columns; 0 if none.
@@ -610,18 +713,18 @@ int tc32_col_width(int n, int nx) {
     if (n < 1024 || n > 8192 || (n & (n - 1))) return 0;
     int best = 0;
     for (int w = 2; w <= 16 && w <= nx; w <<= 1)
-        if (g_t32_cols[ilog2(n)][t32_w_slot(w)].fn) best = w;
+        if (g_t32_cols[ilog2(n)][t32_w_slot(w)].fn[0]) best = w;
     return best;
 }
 
 int tc32_cols_grid(int n, int w, long long ntiles, int num_sms) {
     init_t32();
     const int slot = t32_w_slot(w);
-    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn) return 0;
+    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn[0]) return 0;
     const T32ColEntry &en = g_t32_cols[ilog2(n)][slot];
-    cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    cudaFuncSetAttribute(en.fn[0], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, en.fn, en.threads, en.smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, en.fn[0], en.threads, en.smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     // TMEM: 128 columns per group, 512 per SM
@@ -632,14 +735,14 @@ int tc32_cols_grid(int n, int w, long long ntiles, int num_sms) {
     return grid < 1 ? 1 : (int)grid;
 }
 
-cudaError_t launch_rows_tc32(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
                              int *status, cudaStream_t s) {
     init_t32();
     if (!tc32_rows_available(n) || (split != 1 && split != 2) || ny % split) return cudaErrorInvalidValue;
     if (nrows <= 0) return cudaSuccess;
     const T32RowEntry &en = g_t32_rows[ilog2(n)];
-    const void *fn = en.fn[split == 2 ? 1 : 0];
+    const void *fn = en.fn[tmem_a ? 1 : 0][split == 2 ? 1 : 0];
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
     if (e != cudaSuccess) return e;
     const long long grid = (nrows + en.rows_per_cta - 1) / en.rows_per_cta;  // one CTA per row group
@@ -649,19 +752,21 @@ cudaError_t launch_rows_tc32(int n, const float2 *in, float2 *out, const float2 
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(256), args, en.smem, s);
 }
 
-cudaError_t launch_cols_tc32(int n, int w, const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32,
-                             int nx, int batch, int split, int conj_out, int *status, int grid, cudaStream_t s) {
+cudaError_t launch_cols_tc32(int n, int w, int tmem_a, const CUtensorMap &map, float2 *out, const float2 *tw,
+                             const void *w32, int nx, int batch, int split, int conj_out, int *status, int grid,
+                             cudaStream_t s) {
     init_t32();
     const int slot = t32_w_slot(w);
-    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn || grid < 1) return cudaErrorInvalidValue;
+    if (slot < 0 || !g_t32_cols[ilog2(n)][slot].fn[0] || grid < 1) return cudaErrorInvalidValue;
     const T32ColEntry &en = g_t32_cols[ilog2(n)][slot];
-    cudaError_t e = cudaFuncSetAttribute(en.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    const void *fn = en.fn[tmem_a ? 1 : 0];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
     if (e != cudaSuccess) return e;
     CUtensorMap m = map;
     const __half *wt = static_cast<const __half *>(w32);
     void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&wt,     (void *)&nx,
                     (void *)&batch, (void *)&split, (void *)&conj_out, (void *)&status};
-    return cudaLaunchKernel(en.fn, dim3(grid), dim3(en.threads), args, en.smem, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(en.threads), args, en.smem, s);
 }
 
 }  // namespace gb300fft

@@ -146,13 +146,15 @@ def test_split_tc_default_is_tcgen05(g):
                                          (2048, 16, 2), (4096, 16, 2), (8192, 16, 1), (32, 8192, 2),
                                          (8192, 64, 1), (16, 1024, 5), (8192, 1024, 1), (4096, 2048, 2)])
 @pytest.mark.parametrize("inverse", [False, True])
-def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse):
+@pytest.mark.parametrize("tmem_a", ["1", "0"])
+def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, tmem_a):
     """Radix-32 tcgen05 stages on every compiled row length and column tile
     (rows of 1024..8192 points; columns of 1024, 2048, 4096, 8192 points in
     16-, 8-, 4- and 2-column tiles; the column pre-split at ny = 8192), both
     directions, against the oracle."""
     monkeypatch.setenv("GB300FFT_TC_MMA", "tcgen05")
     monkeypatch.setenv("GB300FFT_TC_RADIX", "32")
+    monkeypatch.setenv("GB300FFT_TC_TMEM_A", tmem_a)  # A operand in tensor memory or in shared memory
     plan = g.Plan(nx, ny, batch, inverse=inverse, precision="split_tc")
     d = plan.describe()
     x = synth.uniform_complex((batch, ny, nx), seed=7 * ny + nx + batch)
@@ -162,7 +164,8 @@ def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse):
     ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
     N = nx * ny
     err = worst_rel_l2(got, ref, N)
-    print(f"tc32 {ny}x{nx}x{batch} inv={inverse} rows={d['rows']['kernel']} cols={d['cols']['kernel']}: {err:.3e}")
+    print(f"tc32 A@{'tmem' if tmem_a == '1' else 'smem'} {ny}x{nx}x{batch} inv={inverse} rows={d['rows']['kernel']} "
+          f"cols={d['cols']['kernel']}: {err:.3e}")
     assert err <= tol_split_tc(N)
     if nx >= 1024:
         assert d["rows"]["kernel"].startswith("k_rows_tc32")
