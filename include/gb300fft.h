@@ -104,6 +104,38 @@ enum {
 fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision);
 
 /*
+ * fft_plan_create_columns -- plan only the column half of Section 5's
+ * decomposition: the length-ny transforms down every column of `batch`
+ * [ny][nx] slices (no row FFTs).  This is the local step a rank runs after
+ * the exchange of a slab-decomposed 2D transform (see fft_slab_pack).
+ *   nx  power of two, 2..65536 (columns per slice); ny power of two, 2..8192.
+ *   FFT_PREC_FP32 only (FFT_ERR_UNSUPPORTED otherwise).
+ * fft_execute / fft_backward then take in and out of batch*ny*nx complex64
+ * each; in == out is allowed (each column tile is read whole before it is
+ * written).  Returns NULL on failure (reason in fft_last_error()).
+ */
+fft_plan_t fft_plan_create_columns(int nx, int ny, int batch, int dir, int precision);
+
+/*
+ * fft_slab_pack / fft_slab_unpack -- the data layout of the exchange step of
+ * a slab-decomposed 2D transform over `parts` ranks (the multi-card form of
+ * Section 5's global transpose, which the paper's Section 6 leaves as future
+ * work).  Each rank holds `rows` = ny/parts consecutive rows of every slice.
+ *   pack:   out[s][b][y][x'] = in[b][y][s*w + x'],  w = nx/parts: the block of
+ *           rank s (its w columns of this rank's rows) made contiguous, so one
+ *           all-to-all chunk goes to each rank.  in: batch*rows*nx elements,
+ *           out: the same count; nx a multiple of parts.
+ *   unpack: out[b][r*rows + y][x'] = in[r][b][y][x']: the chunks received from
+ *           ranks r = 0..parts-1 assembled into this rank's column slab
+ *           [batch][parts*rows][w].
+ * Device pointers, complex64, 16-byte aligned, in != out; plain copies on
+ * `stream`.  FFT_ERR_INVALID_SIZE for inconsistent sizes (or more than 2^31
+ * elements), FFT_ERR_INVALID_ARG for NULL / misaligned / aliased pointers.
+ */
+int fft_slab_pack(const void *in, void *out, int parts, int batch, int rows, int nx, void *stream);
+int fft_slab_unpack(const void *in, void *out, int parts, int batch, int rows, int w, void *stream);
+
+/*
  * fft_execute -- out = DFT_dir(in) for the plan's batch (Section 5: row
  * FFTs, then column FFTs, natural-order output).  `in` and `out` are device
  * pointers to batch*ny*nx complex64 each, 16-byte aligned; in == out is

@@ -31,6 +31,9 @@ _F = ctypes.c_float
 _LL = ctypes.c_longlong
 SIGNATURES = [
     ("fft_plan_create", _P, [_I, _I, _I, _I, _I]),
+    ("fft_plan_create_columns", _P, [_I, _I, _I, _I, _I]),
+    ("fft_slab_pack", _I, [_P, _P, _I, _I, _I, _I, _P]),
+    ("fft_slab_unpack", _I, [_P, _P, _I, _I, _I, _I, _P]),
     ("fft_execute", _I, [_P, _P, _P, _P]),
     ("fft_execute_host", _I, [_P, _P, _P, _P]),
     ("fft_backward", _I, [_P, _P, _P, _P]),

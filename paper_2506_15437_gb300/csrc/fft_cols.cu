@@ -55,7 +55,10 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>:
     const int tt = t / W;
     const int groups_x = nx / W;
     const long long ntiles = (long long)groups_x * P * batch;
-    const float so = conj_out ? -1.f : 1.f;
+    // conj_out bit 0: conjugate the outputs; bit 1: conjugate the inputs (a
+    // column-only inverse, conj(F(conj x)), has no row pass to do it)
+    const float so = (conj_out & 1) ? -1.f : 1.f;
+    const bool conj_in = (conj_out & 2) != 0;
     // tile id -> (column group, kp, first row coordinate of its block)
     auto tile_x = [&](long long id) { return (int)(id % groups_x) * 2 * W; };
     auto tile_kp = [&](long long id) { return (int)((id / groups_x) % P); };
@@ -111,6 +114,10 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>:
             const int j = tt + bb * T;
 #pragma unroll
             for (int r = 0; r < R0; ++r) v[bb * R0 + r] = tile[(j + r * (N / R0)) * W + c];
+        }
+        if (conj_in) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) v[k].y = -v[k].y;
         }
         auto after_reads = [&] {
             __syncthreads();

@@ -358,6 +358,7 @@ void ragged_destroy(RaggedState *r);
 // A plan (opaque to the C ABI): dense or ragged.
 struct fft_plan_s {
     int kind = 0;  // 0 dense, 1 ragged
+    int axes = 3;  // dense plans: transformed axes, bit 0 x (rows), bit 1 y (columns)
     gb300fft::RaggedState *ragged = nullptr;
     int nx = 1, ny = 1, batch = 1, dir = FFT_FORWARD, prec = FFT_PREC_FP32;
     int device = 0;

@@ -747,6 +747,26 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
     return FFT_OK;
 }
 
+// Column-only plan: the column FFTs of each [ny][nx] slice, read through a
+// tensor map over `in` (so in and out may differ or coincide: every tile is
+// read whole before its columns are written).  The inverse conjugates on load
+// and on store.
+int run_columns(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaStream_t s) {
+    AxisPlan &cp = p->cols;
+    if (cp.map_base != src) {
+        if (encode_col_map(&cp.map, src, p->nx, (long long)p->ny * p->batch, 1, cp.col->w, cp.col->box_rows) != 0)
+            return FFT_ERR_CUDA;
+        cp.map_base = src;
+    }
+    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, 1, inv ? 3 : 0, p->status, cp.grid, p->col_pf, s) !=
+        cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
 // out = DFT_{sign}(in) (optionally weighted by scale*w on load) for a dense plan.
 int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *weight, float wscale,
               cudaStream_t s, const float *wscale_dev) {
@@ -755,6 +775,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     float2 *dst = static_cast<float2 *>(out);
     if (!src || !dst || !aligned16(src) || !aligned16(dst)) return FFT_ERR_INVALID_ARG;
     cudaSetDevice(p->device);
+    if (p->axes == 2) return weight ? FFT_ERR_UNSUPPORTED : run_columns(p, src, dst, inv, s);
     if (p->any) return weight ? FFT_ERR_UNSUPPORTED : run_any(p, src, dst, sign, s);
     if (p->fs.n1 > 0) return weight ? FFT_ERR_UNSUPPORTED : run_fourstep(p, src, dst, inv, s);
     const long long total = (long long)p->nx * p->ny * p->batch;
@@ -921,6 +942,58 @@ const char *fft_error_string(int code) {
         case FFT_ERR_TIMEOUT: return "device-side bounded wait timed out";
         default: return "unknown error code";
     }
+}
+
+fft_plan_t fft_plan_create_columns(int nx, int ny, int batch, int dir, int precision) {
+    t_last_error = FFT_OK;
+    if (nx < 2 || ny < 2 || batch < 1 || !is_pow2(nx) || !is_pow2(ny) || ny > 8192 || nx > 65536 ||
+        (long long)nx * ny * batch > (1LL << 31)) {
+        fail(FFT_ERR_INVALID_SIZE);
+        return nullptr;
+    }
+    if (dir != FFT_FORWARD && dir != FFT_INVERSE) {
+        fail(FFT_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    if (precision != FFT_PREC_FP32) {
+        fail(precision == FFT_PREC_SPLIT_FP16_TC ? FFT_ERR_UNSUPPORTED : FFT_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    fft_plan_s *p = new (std::nothrow) fft_plan_s();
+    if (!p) {
+        fail(FFT_ERR_ALLOC);
+        return nullptr;
+    }
+    p->nx = nx;
+    p->ny = ny;
+    p->batch = batch;
+    p->dir = dir;
+    p->prec = precision;
+    p->axes = 2;
+    Schedule sc = default_schedule(nx, ny);
+    apply_env_overrides(&sc);
+    sc.col_stream = 0;  // the streaming pass needs rows stored in its own order
+    sc.col_kind = kColTile;
+    p->sched = sc;
+    p->col_pf = sc.col_pf;
+    int rc = FFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        rc = FFT_ERR_CUDA;
+    if (rc == FFT_OK) rc = setup_col_axis(p, p->cols, ny, nx, (long long)nx * batch, sc);
+    if (rc == FFT_OK) {
+        p->status = dev_alloc<int>(p, 1);
+        if (!p->status) rc = FFT_ERR_ALLOC;
+        else if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = FFT_ERR_CUDA;
+    }
+    p->rows.n = 1;
+    if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
+    if (rc != FFT_OK) {
+        free_plan(p);
+        fail(rc);
+        return nullptr;
+    }
+    return p;
 }
 
 fft_plan_t fft_plan_create(int nx, int ny, int batch, int dir, int precision) {
@@ -1259,6 +1332,15 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      fs.n, fs.n1, fs.n2, fs.m, fs.m == 4 ? "k_fs_mid<4>" : fs.m == 2 ? "k_fs_mid<2>" : "",
                      fs.n2 / fs.m, fs.b->e, fs.b->w, fs.n2 / fs.m, fs.b->e, fs.b->w, rb, fs.n1, fs.a->e, fs.a->w,
                      fs.n1, fs.a->e, fs.a->w, ra, fs.grid_a);
+    } else if (p->axes == 2) {
+        char r2[96] = "[]";
+        rad(p->cols.n, p->cols.col->e, r2, sizeof r2);
+        k = snprintf(tmp, sizeof tmp,
+                     "{\"kind\": \"dense\", \"precision\": \"fp32\", \"axes\": \"y\", \"rows\": {\"kernel\": "
+                     "\"none\", \"n\": 1}, \"cols\": {\"kernel\": \"k_cols<%d,%d,%d>\", \"n\": %d, \"e\": %d, "
+                     "\"w\": %d, \"radices\": %s, \"grid\": %d}, \"split\": 1}",
+                     p->cols.n, p->cols.col->e, p->cols.col->w, p->cols.n, p->cols.col->e, p->cols.col->w, r2,
+                     p->cols.grid);
     } else {
         const bool tc = p->prec == FFT_PREC_SPLIT_FP16_TC;
         char r1[96] = "[]", r2[96] = "[]";

@@ -163,6 +163,48 @@ class Plan:
             pass
 
 
+class ColumnPlan(Plan):
+    """Only the column FFTs (length ny, down each column) of ``batch``
+    [ny][nx] slices: the local step of a slab-decomposed 2D transform after
+    its exchange (fft_plan_create_columns)."""
+
+    def __init__(self, nx: int, ny: int, batch: int = 1, inverse: bool = False):
+        lib = N.load()
+        self.nx, self.ny, self.batch = int(nx), int(ny), int(batch)
+        self.dir = N.FFT_INVERSE if inverse else N.FFT_FORWARD
+        self.precision = "fp32"
+        self._lib = lib
+        self._p = lib.fft_plan_create_columns(self.nx, self.ny, self.batch, self.dir, N.FFT_PREC_FP32)
+        if not self._p:
+            raise N.FFTError(lib.fft_last_error(), f"fft_plan_create_columns({nx}, {ny}, {batch})")
+
+
+def slab_pack(x: torch.Tensor, parts: int, batch: int, rows: int, nx: int, out: torch.Tensor | None = None):
+    """out[s][b][y][x'] = x[b][y][s*w + x'] (w = nx/parts): the all-to-all
+    chunk for each rank s, contiguous (fft_slab_pack)."""
+    _check_tensor(x, torch.complex64, "x")
+    if x.numel() != batch * rows * nx:
+        raise ValueError("x must hold batch*rows*nx elements")
+    out = torch.empty(parts, batch, rows, nx // parts, dtype=x.dtype, device=x.device) if out is None else out
+    _check_tensor(out, torch.complex64, "out")
+    N.check(N.load().fft_slab_pack(x.data_ptr(), out.data_ptr(), parts, batch, rows, nx, _stream_handle(x.device)),
+            "fft_slab_pack")
+    return out
+
+
+def slab_unpack(x: torch.Tensor, parts: int, batch: int, rows: int, w: int, out: torch.Tensor | None = None):
+    """out[b][r*rows + y][x'] = x[r][b][y][x']: the chunks received from every
+    rank assembled into this rank's column slab (fft_slab_unpack)."""
+    _check_tensor(x, torch.complex64, "x")
+    if x.numel() != parts * batch * rows * w:
+        raise ValueError("x must hold parts*batch*rows*w elements")
+    out = torch.empty(batch, parts * rows, w, dtype=x.dtype, device=x.device) if out is None else out
+    _check_tensor(out, torch.complex64, "out")
+    N.check(N.load().fft_slab_unpack(x.data_ptr(), out.data_ptr(), parts, batch, rows, w, _stream_handle(x.device)),
+            "fft_slab_unpack")
+    return out
+
+
 _cache: dict = {}
 _cache_lock = threading.Lock()
 
