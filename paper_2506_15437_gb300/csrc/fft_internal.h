@@ -86,7 +86,7 @@ cudaError_t launch_cols_tc(int n, int w, int tcg, const CUtensorMap &map, float2
 // Split-FP16 tensor-core variants with radix-32 tcgen05 stages (fft_tc32.cu):
 // rows and columns of 1024..8192 points; the plan owns the FP64-built B table.
 cudaError_t build_w32_table(void *t, cudaStream_t s);
-constexpr size_t kW32TableBytes = 2 * 64 * 64 * 2;
+constexpr size_t kW32TableBytes = 4 * 64 * 64 * 2;  // two tables of B_hi, B_lo
 bool tc32_rows_available(int n);
 int tc32_col_width(int n, int nx);
 int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
@@ -94,6 +94,13 @@ int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
 cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
                              int *status, cudaStream_t s);
+// Landed-row form (persistent, 512 threads, all TMEM columns of the SM):
+// rows per unit (0: not compiled), and whether a call is covered.
+int tc32_land_rows(int n);
+bool tc32_land_available(int n, long long nrows, int ny, int split);
+cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                                  const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
+                                  int *status, int num_sms, cudaStream_t s);
 cudaError_t launch_cols_tc32(int n, int w, int tmem_a, const CUtensorMap &map, float2 *out, const float2 *tw,
                              const void *w32, int nx, int batch, int split, int conj_out, int *status, int grid,
                              cudaStream_t s);
@@ -387,6 +394,7 @@ struct fft_plan_s {
     void *w32 = nullptr;    // split-FP16 plans with radix-32 stages: hi/lo B table (FP64-built)
     int tc_radix = 32;      // split-FP16 plans: largest tensor-core radix allowed (32, or 16)
     int tc_tmem_a = 1;      // radix-32 tensor-core stages: A operand in tensor memory (0: shared memory)
+    int tc_land = 1;        // radix-32 tensor-core rows from landed rows where the shape allows (A in TMEM)
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events

@@ -62,6 +62,23 @@ __host__ __device__ constexpr double sin_2pi(int m, int R) {
     return k == 0 ? taylor_sin(phi) : k == 1 ? taylor_cos(phi) : k == 2 ? -taylor_sin(phi) : -taylor_cos(phi);
 }
 
+// cos and sin of 2 pi j / R for j = 1 .. (R-1)/2, rounded to float.  Built
+// only in constant initialisers (a constexpr variable), so the double-precision
+// series never reach device code.
+template <int R>
+struct OddRoots {
+    float c[(R - 1) / 2], s[(R - 1) / 2];
+};
+template <int R>
+__host__ __device__ constexpr OddRoots<R> odd_roots() {
+    OddRoots<R> w{};
+    for (int j = 1; j <= (R - 1) / 2; ++j) {
+        w.c[j - 1] = (float)cos_2pi(j, R);
+        w.s[j - 1] = (float)sin_2pi(j, R);
+    }
+    return w;
+}
+
 // Forward R-point DFT for odd prime R, legs paired as (k, R - k):
 //   y_m     = a_0 + sum_k t_k cos(2 pi k m / R) - i sum_k d_k sin(2 pi k m / R)
 //   y_{R-m} = a_0 + sum_k t_k cos(2 pi k m / R) + i sum_k d_k sin(2 pi k m / R)
@@ -69,6 +86,7 @@ __host__ __device__ constexpr double sin_2pi(int m, int R) {
 template <int R>
 __device__ __forceinline__ void dft_odd(float2 *a) {
     constexpr int H = (R - 1) / 2;
+    constexpr OddRoots<R> W = odd_roots<R>();
     float2 t[H], d[H];
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
@@ -87,8 +105,8 @@ __device__ __forceinline__ void dft_odd(float2 *a) {
         for (int k = 1; k <= H; ++k) {
             const int q = (k * m) % R;  // angle index, folded into 1 .. H
             const int j = q <= H ? q : R - q;
-            const float c = (float)cos_2pi(j, R);
-            const float sn = q <= H ? (float)sin_2pi(j, R) : -(float)sin_2pi(j, R);
+            const float c = W.c[j - 1];
+            const float sn = q <= H ? W.s[j - 1] : -W.s[j - 1];
             A = make_float2(fmaf(c, t[k - 1].x, A.x), fmaf(c, t[k - 1].y, A.y));
             B = make_float2(fmaf(sn, d[k - 1].x, B.x), fmaf(sn, d[k - 1].y, B.y));
         }

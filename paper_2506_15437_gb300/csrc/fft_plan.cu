@@ -407,6 +407,7 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         if (p->tcg && !tcg_available(nx > 1 ? nx : ny, 1, 0)) p->tcg = 0;
         if (const char *ev = getenv("GB300FFT_TC_RADIX")) p->tc_radix = atoi(ev) >= 32 ? 32 : 16;
         if (const char *ev = getenv("GB300FFT_TC_TMEM_A")) p->tc_tmem_a = atoi(ev) != 0;
+        if (const char *ev = getenv("GB300FFT_TC_LAND")) p->tc_land = atoi(ev) != 0;
         p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
         if (!p->w16) rc = FFT_ERR_ALLOC;
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
@@ -751,6 +752,12 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
 // tensor map over `in` (so in and out may differ or coincide: every tile is
 // read whole before its columns are written).  The inverse conjugates on load
 // and on store.
+// The tensor-core row pass runs from landed rows when the plan allows it and
+// the rows divide into whole units (A in TMEM only).
+static bool tc32_land_used(const fft_plan_s *p, long long nrows, int P) {
+    return p->tc_land && p->tc_tmem_a && tc32_land_available(p->rows.n, nrows, p->ny, P);
+}
+
 int run_columns(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaStream_t s) {
     AxisPlan &cp = p->cols;
     if (cp.map_base != src) {
@@ -796,8 +803,11 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (weight) return FFT_ERR_UNSUPPORTED;
         if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+        const bool land = p->rows.tc32 && tc32_land_used(p, nrows, P);
         const cudaError_t er =
-            p->rows.tc32 ? launch_rows_tc32(p->rows.n, p->tc_tmem_a, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
+            land ? launch_rows_tc32_land(p->rows.n, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P, inv ? 1 : 0,
+                                         (inv && !two_pass) ? 1 : 0, p->status, p->num_sms, s)
+            : p->rows.tc32 ? launch_rows_tc32(p->rows.n, p->tc_tmem_a, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
                                             inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s)
                          : launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P,
                                           inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s);
@@ -1363,7 +1373,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
                      "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d}",
-                     tc ? "split_fp16_tc" : "fp32", tc ? (p->rows.tc32 ? "k_rows_tc32" : p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
+                     tc ? "split_fp16_tc" : "fp32", tc ? (p->rows.tc32 ? (tc32_land_used(p, (long long)p->nx * p->ny * p->batch / p->rows.n, p->split) ? "k_rows_tc32_land" : "k_rows_tc32") : p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
                      !cp.col ? "none" : tc ? (cp.tc32 ? "k_cols_tc32" : cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
                      cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (cp.tc32 ? 32 : 16) : cp.col->e) : 0,

@@ -38,28 +38,47 @@ constexpr int kT32GroupStage = 2 * kT32ABytes;  // A_hi + A_lo of a group: 32 Ki
 constexpr int kT32BBytes = 64 * 64 * 2;   // one float16 B operand (8 KiB)
 static_assert(kT32GroupStage == 32768, "A_hi + A_lo of a group");
 
-// B_hi then B_lo (64 x 64 float16 each) in the canonical K-major layout of the
-// tensor-core descriptors: element (n, k) at byte (n/8)*1024 + (k/8)*128 +
-// (n%8)*16 + (k%8)*2.  Built in FP64 once per plan.
+// Two B tables, each B_hi then B_lo (64 x 64 float16) in the canonical
+// K-major layout of the tensor-core descriptors: element (n, k) at byte
+// (n/8)*1024 + (k/8)*128 + (n%8)*16 + (k%8)*2.  Built in FP64 once per plan.
+//   Table 0, the full real form of W32: [[Wr, -Wi], [Wi, Wr]], rows 0-31 the
+//   real outputs, 32-63 the imaginary; columns 0-31 Re x, 32-63 Im x.
+//   Table 1, the even/odd form: y_k = E_k + O_k, y_{k+16} = E_k - O_k (k < 16)
+//   with E_k = sum_m W16^(k m) x_{2m} and O_k = sum_m W32^(k (2m+1)) x_{2m+1}:
+//   block-diagonal, rows 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O;
+//   columns 0-15 Re x_even, 16-31 Im x_even, 32-47 Re x_odd, 48-63 Im x_odd.
 __global__ void k_w32_table(__half *t) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // 4096 entries
-    if (idx >= 64 * 64) return;
+    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;  // 2 x 4096 entries
+    if (gidx >= 2 * 64 * 64) return;
+    const int table = gidx >> 12, idx = gidx & 4095;
     const int n = idx >> 6, k = idx & 63;
-    const int kr = k & 31, nr = n & 31;
-    double sv, cv;
-    sincospi(2.0 * (double)((nr * kr) & 31) / 32.0, &sv, &cv);
-    const double wr = cv, wi = -sv;
-    // [[Wr, -Wi], [Wi, Wr]]: rows 0-31 the real outputs, 32-63 the imaginary
-    const double b = (n < 32) ? (k < 32 ? wr : -wi) : (k < 32 ? wi : wr);
+    double b = 0.0;
+    if (table == 0) {
+        const int kr = k & 31, nr = n & 31;
+        double sv, cv;
+        sincospi(2.0 * (double)((nr * kr) & 31) / 32.0, &sv, &cv);
+        const double wr = cv, wi = -sv;
+        b = (n < 32) ? (k < 32 ? wr : -wi) : (k < 32 ? wi : wr);
+    } else if ((n < 32) == (k < 32)) {  // the two diagonal blocks
+        const int odd = n >= 32;
+        const int nq = n & 15, mq = k & 15;           // output k', input m
+        const int nim = (n >> 4) & 1, kim = (k >> 4) & 1;  // imaginary row / column
+        const int a = odd ? (nq * (2 * mq + 1)) & 31 : (2 * nq * mq) & 31;  // angle in units of 2 pi / 32
+        double sv, cv;
+        sincospi(2.0 * (double)a / 32.0, &sv, &cv);
+        const double wr = cv, wi = -sv;
+        b = nim == 0 ? (kim == 0 ? wr : -wi) : (kim == 0 ? wi : wr);
+    }
     const __half hi = __double2half(b);
     const __half lo = __double2half(b - (double)__half2float(hi));
     const int off = ((n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2;
-    t[off] = hi;
-    t[kT32BBytes / 2 + off] = lo;
+    __half *tb = t + table * kT32BBytes;  // kT32BBytes halves = two 8 KiB operands
+    tb[off] = hi;
+    tb[kT32BBytes / 2 + off] = lo;
 }
 
 cudaError_t build_w32_table(void *t, cudaStream_t s) {
-    k_w32_table<<<16, 256, 0, s>>>(static_cast<__half *>(t));
+    k_w32_table<<<32, 256, 0, s>>>(static_cast<__half *>(t));
     return cudaGetLastError();
 }
 
@@ -72,6 +91,8 @@ __device__ __forceinline__ uint64_t t32_desc(uint32_t saddr) {
 }
 // kind::f16: D = F32 (bit 4), A = B = F16, both K-major, N = 64, M = 128
 constexpr uint32_t kT32Idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// the same with N = 32 (one diagonal block of the even/odd table)
+constexpr uint32_t kT32IdescN32 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void t32_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -97,11 +118,12 @@ __device__ __forceinline__ void t32_st8(uint32_t taddr, const uint32_t (&r)[8]) 
 }
 
 // MMA with A read from tensor memory (rows = lanes, two float16 per column).
-__device__ __forceinline__ void t32_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void t32_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate,
+                                           uint32_t idesc = kT32Idesc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(kT32Idesc), "r"(accumulate)
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -170,7 +192,8 @@ struct Tc32 {
         bar = bars + group;
         stage = stage_base + (size_t)group * kT32GroupStage;
         phase = 0;
-        const uint4 *src = reinterpret_cast<const uint4 *>(bsrc);
+        // the A-in-TMEM form multiplies by the even/odd table (the second one)
+        const uint4 *src = reinterpret_cast<const uint4 *>(bsrc + (TA ? kT32BBytes : 0));
         uint4 *dst = reinterpret_cast<uint4 *>(bsm);
         for (int i = t; i < 2 * kT32BBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
         const uint32_t cols = (uint32_t)ngroups * 128;  // 128, 256 or 512: powers of two
@@ -204,8 +227,11 @@ struct Tc32 {
         }
     }
 
-    // TA form of dft32: split into TMEM, 12 MMAs into one accumulator.  Every
-    // thread of the group calls it; no CTA barrier, no shared memory.
+    // TA form of dft32: split into TMEM, then the even/odd product: 12 MMAs
+    // of N = 32 (one accumulator, each diagonal block of the table into its
+    // own half of D), and the radix-2 recombination y_k = E_k + O_k,
+    // y_{k+16} = E_k - O_k in float32.  Every thread of the group calls it;
+    // no CTA barrier, no shared memory.
     __device__ __forceinline__ void dft32_ta(float2 (&v)[kT32E]) {
         float m = 0.f;
 #pragma unroll
@@ -215,15 +241,15 @@ struct Tc32 {
         const float up = __int_as_float((264 - eb) << 23);   // 2048 / s
         const float down = __int_as_float((eb - 10) << 23);  // s / 2048
         const uint32_t lane = (uint32_t)(threadIdx.x & 96) << 16;
-        // halves [16q, 16q + 16) of the row: q = 0, 1 real parts, q = 2, 3 imaginary
+        // A row, 16 halves per chunk q: Re x_even, Im x_even, Re x_odd, Im x_odd
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t wh[8], wl[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
-                const int k0 = (q & 1) * 16 + 2 * p;
-                const float x0 = ((q & 2) ? v[k0].y : v[k0].x) * up;
-                const float x1 = ((q & 2) ? v[k0 + 1].y : v[k0 + 1].x) * up;
+                const int k0 = 4 * p + (q >> 1);  // x_{2j} (q < 2) or x_{2j+1}, j = 2p and 2p + 1
+                const float x0 = ((q & 1) ? v[k0].y : v[k0].x) * up;
+                const float x1 = ((q & 1) ? v[k0 + 2].y : v[k0 + 2].x) * up;
                 const float h0 = __int_as_float(__float_as_int(x0) & 0xFFFFE000);
                 const float h1 = __int_as_float(__float_as_int(x1) & 0xFFFFE000);
                 wh[p] = f2h2_bits(h0, h1);
@@ -238,17 +264,29 @@ struct Tc32 {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (row == 0) {
             const uint32_t b_hi = smem_u32(bsm), b_lo = b_hi + kT32BBytes;
-            // K = 64 as four K = 16 steps (8 TMEM columns of A each).  The
-            // small correction products accumulate first, at their own scale;
-            // the large B_hi hi terms come last, so only those four additions
-            // round at the scale of the result (as a separate accumulator and
-            // a final float32 add would)
+            // block e (0: even, 1: odd): K steps 2e, 2e + 1 (A columns 16e ..),
+            // table rows 32e .. (4 core-matrix groups of 1024 bytes), D
+            // columns 32e ..  The small correction products accumulate
+            // first, at their own scale; the large B_hi hi terms come last.
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 96 + 8 * ks, t32_desc(b_hi + ks * 256), ks);
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t d = tmem + 32 * e, bo = 4096 * e;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 64 + 8 * ks, t32_desc(b_lo + ks * 256), 1);
+                for (int j = 0; j < 2; ++j) {
+                    const int ks = 2 * e + j;
+                    t32_mma_ts(d, tmem + 96 + 8 * ks, t32_desc(b_hi + bo + ks * 256), j, kT32IdescN32);
+                }
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) t32_mma_ts(tmem, tmem + 64 + 8 * ks, t32_desc(b_hi + ks * 256), 1);
+                for (int j = 0; j < 2; ++j) {
+                    const int ks = 2 * e + j;
+                    t32_mma_ts(d, tmem + 64 + 8 * ks, t32_desc(b_lo + bo + ks * 256), 1, kT32IdescN32);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int ks = 2 * e + j;
+                    t32_mma_ts(d, tmem + 64 + 8 * ks, t32_desc(b_hi + bo + ks * 256), 1, kT32IdescN32);
+                }
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(bar))
                          : "memory");
@@ -256,18 +294,24 @@ struct Tc32 {
         if (!t32_wait(bar, phase)) record_status(status, kStatusTimeout);
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // D columns: 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O
+        uint32_t de[16], dof[16];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            uint32_t d[16];
-            t32_ld16(tmem + lane + h * 16, d);
+        for (int part = 0; part < 2; ++part) {  // real, then imaginary
+            t32_ld16(tmem + lane + 16 * part, de);
+            t32_ld16(tmem + lane + 32 + 16 * part, dof);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const float y = __int_as_float(d[k]) * down;
-                if (h < 2)
-                    v[(h & 1) * 16 + k].x = y;
-                else
-                    v[(h & 1) * 16 + k].y = y;
+                const float ev = __int_as_float(de[k]), ov = __int_as_float(dof[k]);
+                const float y0 = (ev + ov) * down, y1 = (ev - ov) * down;
+                if (part == 0) {
+                    v[k].x = y0;
+                    v[k + 16].x = y1;
+                } else {
+                    v[k].y = y0;
+                    v[k + 16].y = y1;
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -382,11 +426,14 @@ struct T32RowShape {
     static_assert(S >= 2 && (R0 == E || R0 < E), "stage 0 radix");
 };
 
-template <int N, int P, bool TA>
-__global__ void __launch_bounds__(256, 2)
-    k_rows_tc32(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
-                const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nrows, int ny, int conj_in,
-                int conj_out, int *status) {
+// Stages 0 .. S-1 of one N-point row held as v (stage-0 operands, already
+// loaded) by thread tt of its row's T threads, exchanging through sm (the
+// row's padded span).  sync_first: a CTA barrier precedes the first exchange
+// write (the span may still be read as input).  after_reads() runs, on every
+// thread, once the last stage has read its operands from the exchange.
+template <int N, bool TA, class AfterReads>
+__device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E], float2 *sm, const float2 *tw, int tt,
+                                               bool sync_first, AfterReads after_reads) {
     using Sh = T32RowShape<N>;
     using Eng = typename Sh::Eng;
     using Sc = Sched<N, kT32E>;
@@ -394,6 +441,54 @@ __global__ void __launch_bounds__(256, 2)
     constexpr int T = Sh::T;
     constexpr int R0 = Sh::R0;
     constexpr int S = Sh::S;
+    auto none = [] {};
+    // stage 0
+    if constexpr (R0 == E) {
+        tc.dft32(v, false, none);
+    } else {
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) dft<R0>(&v[b * R0]);
+    }
+    // stages 1 .. S-1: exchange, twiddles, tensor-core radix-32
+#pragma unroll
+    for (int s = 1; s < S; ++s) {
+        const int Rp = (s == 1) ? R0 : E;
+        const int Nsp = Sc::ns(s - 1);
+        if (s > 1 || R0 == E || sync_first) __syncthreads();  // the previous staging / exchange reads are done
+#pragma unroll
+        for (int b = 0; b < E / Rp; ++b) {
+            const int j = tt + b * T;
+            const int m = j & (Nsp - 1);
+#pragma unroll
+            for (int k = 0; k < Rp; ++k) sm[Eng::pad_s((j - m) * Rp + m + k * Nsp, s)] = v[b * Rp + k];
+        }
+        __syncthreads();
+        const int Ns = Sc::ns(s);
+        const int m = tt & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = sm[Eng::pad_s(tt + r * T, s)];
+        if (s == S - 1) after_reads();
+        const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) {
+            const float4 w2 = __ldg(tws + k * Ns);
+            v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w2.x, w2.y));
+            if (2 * k + 2 < E) v[2 * k + 2] = cmul(v[2 * k + 2], make_float2(w2.z, w2.w));
+        }
+        tc.dft32(v, false, none);
+    }
+}
+
+template <int N, int P, bool TA>
+__global__ void __launch_bounds__(256, 2)
+    k_rows_tc32(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
+                const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nrows, int ny, int conj_in,
+                int conj_out, int *status) {
+    using Sh = T32RowShape<N>;
+    using Eng = typename Sh::Eng;
+    constexpr int E = kT32E;
+    constexpr int T = Sh::T;
+    constexpr int R0 = Sh::R0;
     static_assert(P == 1 || P == 2, "pre-split of 1 or 2");
     extern __shared__ __align__(1024) unsigned char raw[];
     float2 *ex = reinterpret_cast<float2 *>(raw);
@@ -441,44 +536,159 @@ __global__ void __launch_bounds__(256, 2)
             for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
         }
     }
-    auto none = [] {};
-    float2 *sm = ex + g * Eng::SMEM_ELEMS;
-    // stage 0
-    if constexpr (R0 == E) {
-        tc.dft32(v, false, none);
-    } else {
-#pragma unroll
-        for (int b = 0; b < E / R0; ++b) dft<R0>(&v[b * R0]);
-    }
-    // stages 1 .. S-1: exchange, twiddles, tensor-core radix-32
-#pragma unroll
-    for (int s = 1; s < S; ++s) {
-        const int Rp = (s == 1) ? R0 : E;
-        const int Nsp = Sc::ns(s - 1);
-        if (s > 1 || R0 == E) __syncthreads();  // the previous stage's staging / exchange reads are done
-#pragma unroll
-        for (int b = 0; b < E / Rp; ++b) {
-            const int j = tt + b * T;
-            const int m = j & (Nsp - 1);
-#pragma unroll
-            for (int k = 0; k < Rp; ++k) sm[Eng::pad_s((j - m) * Rp + m + k * Nsp, s)] = v[b * Rp + k];
-        }
-        __syncthreads();
-        const int Ns = Sc::ns(s);
-        const int m = tt & (Ns - 1);
-#pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = sm[Eng::pad_s(tt + r * T, s)];
-        const float4 *tws = reinterpret_cast<const float4 *>(tw + Sc::tw_off(s)) + m;
-#pragma unroll
-        for (int k = 0; k < E / 2; ++k) {
-            const float4 w2 = __ldg(tws + k * Ns);
-            v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w2.x, w2.y));
-            if (2 * k + 2 < E) v[2 * k + 2] = cmul(v[2 * k + 2], make_float2(w2.z, w2.w));
-        }
-        tc.dft32(v, false, none);
-    }
+    t32_row_stages<N, TA>(tc, v, ex + g * Eng::SMEM_ELEMS, tw, tt, false, [] {});
     if (active) {
         float2 *dst = out + row * N;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            float2 x = v[k];
+            x.y *= so;
+            dst[tt + k * T] = x;
+        }
+    }
+    tc.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Row pass from landed rows: one persistent 512-thread CTA per SM (four MMA
+// groups, all 512 TMEM columns), L = 512 / T output rows per unit.  The unit's
+// input rows land in shared memory through bulk copies on one mbarrier (P = 1:
+// L consecutive rows, one copy; P = 2: L/2 consecutive pairs q, q + ny/2, two
+// copies, each input row crossing HBM once for both of its output rows).
+// Output h of the unit is formed by threads [h*T, (h+1)*T) and transformed in
+// its own padded span of the same buffer, which the landed rows no longer
+// need by then; the next unit's copies start as soon as every thread has read
+// its last-stage operands, so they run under the last stage's products and
+// the stores.  Arithmetic per output row: the plain tensor-core row pass's.
+// ---------------------------------------------------------------------------
+template <int N>
+struct T32LandShape {
+    static constexpr int T = N / kT32E;
+    static constexpr int THREADS = 512;
+    static constexpr int L = THREADS / T;  // output rows per unit
+    using Eng = typename T32RowShape<N>::Eng;
+    static constexpr size_t LAND_BYTES = (size_t)L * N * sizeof(float2);
+    static constexpr size_t XBYTES = (size_t)L * Eng::SMEM_ELEMS * sizeof(float2);
+    static constexpr size_t BUF = XBYTES > LAND_BYTES ? XBYTES : LAND_BYTES;
+    static constexpr size_t B_OFF = (BUF + 1023) / 1024 * 1024;
+    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;  // 4 group barriers, the landing barrier, TMEM slot
+    static constexpr size_t SMEM = BAR_OFF + 64;
+    static_assert(L >= 2 && L % 2 == 0, "pairs of outputs per unit");
+    static_assert(LAND_BYTES < (1u << 20), "one mbarrier transaction count");
+};
+
+template <int N, int P>
+__global__ void __launch_bounds__(512, 1)
+    k_rows_tc32_land(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
+                     const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nunits, int ny,
+                     int conj_in, int conj_out, int *status) {
+    using Sh = T32LandShape<N>;
+    using Eng = typename Sh::Eng;
+    constexpr int E = kT32E;
+    constexpr int T = Sh::T;
+    constexpr int L = Sh::L;
+    constexpr int R0 = T32RowShape<N>::R0;
+    static_assert(P == 1 || P == 2, "pre-split of 1 or 2");
+    extern __shared__ __align__(1024) unsigned char raw[];
+    float2 *land = reinterpret_cast<float2 *>(raw);  // [L][N]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    uint64_t *lbar = bars + 4;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::BAR_OFF + 48);
+    __shared__ int s_ok;
+    Tc32<true> tc;
+    tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
+    const int t = threadIdx.x;
+    const int h = t / T;  // output row of the unit
+    const int tt = t - h * T;
+    const float si = conj_in ? -1.f : 1.f;
+    const float so = conj_out ? -1.f : 1.f;
+    const int Q = ny / P;
+    constexpr int UQ = L / P;        // input rows per copy (P = 2: pairs per unit)
+    const int upb = Q / UQ;          // units per slice
+    // first input row of unit u's (first) copy
+    auto first_row = [&](long long u) -> long long {
+        if constexpr (P == 1) return u * L;
+        const long long b = u / upb;
+        return b * ny + (long long)(u - b * upb) * UQ;
+    };
+    auto issue = [&](long long u) {  // thread 0: the unit's copies
+        const long long r0 = first_row(u);
+        mbar_expect_tx(lbar, (uint32_t)Sh::LAND_BYTES);
+        constexpr uint32_t CB = (uint32_t)UQ * N * sizeof(float2);
+        bulk_load(land, in + r0 * N, CB, lbar);
+        if constexpr (P == 2) bulk_load(land + UQ * N, in + (r0 + Q) * N, CB, lbar);
+    };
+    auto prefetch = [&](long long u) {
+        const long long r0 = first_row(u);
+        constexpr uint32_t CB = (uint32_t)UQ * N * sizeof(float2);
+        bulk_prefetch_l2(in + r0 * N, CB);
+        if constexpr (P == 2) bulk_prefetch_l2(in + (r0 + Q) * N, CB);
+    };
+    if (t == 0) {
+        mbar_init(lbar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long u = blockIdx.x;
+    uint32_t phase = 0;
+    if (t == 0 && u < nunits) issue(u);
+    for (; u < nunits; u += gridDim.x) {
+        if (t == 0 && u + gridDim.x < nunits) prefetch(u + gridDim.x);
+        if (t == 0) s_ok = mbar_wait_bounded(lbar, phase) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (t == 0) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(lbar, phase);  // give the copies in flight a last chance to land
+            }
+            break;  // leave through finish(): the TMEM columns must be freed
+        }
+        phase ^= 1;
+        const long long next = u + gridDim.x;
+        const long long r0 = first_row(u);
+        // output h: P = 1, row r0 + h; P = 2, pair i = h / 2 (rows r0 + i and
+        // r0 + i + Q landed at i and UQ + i), kp = h % 2, stored at row
+        // (slice) + 2 q + kp with q = (r0 - slice) + i
+        const int i = P == 2 ? h >> 1 : h;
+        const int kp = P == 2 ? h & 1 : 0;
+        float2 v[E];
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) {
+            const int j = tt + b * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int e = j + r * (N / R0);
+                float2 x = land[i * N + e];
+                x.y *= si;
+                if constexpr (P == 2) {
+                    float2 y = land[(UQ + i) * N + e];
+                    y.y *= si;
+                    x = kp ? csub(x, y) : cadd(x, y);
+                }
+                v[b * R0 + r] = x;
+            }
+        }
+        long long orow = r0 + h;
+        if constexpr (P == 2) {
+            const long long b = r0 / ny;
+            const int q = (int)(r0 - b * ny) + i;
+            if (kp) {
+                const float2 w = __ldg(twp + q);
+#pragma unroll
+                for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
+            }
+            orow = b * ny + 2LL * q + kp;
+        }
+        auto after_reads = [&] {
+            __syncthreads();
+            if (t == 0 && next < nunits) {
+                fence_proxy_async_smem();
+                issue(next);
+            }
+        };
+        t32_row_stages<N, true>(tc, v, land + h * Eng::SMEM_ELEMS, tw, tt, true, after_reads);
+        float2 *dst = out + orow * N;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             float2 x = v[k];
@@ -652,12 +862,18 @@ struct T32RowEntry {
     int rows_per_cta = 0;
     size_t smem = 0;
 };
+struct T32LandEntry {
+    const void *fn[2] = {nullptr, nullptr};  // [P = 1, 2]
+    int rows_per_unit = 0;
+    size_t smem = 0;
+};
 struct T32ColEntry {
     const void *fn[2] = {nullptr, nullptr};  // [A in TMEM]
     int threads = 0, w = 0;
     size_t smem = 0;
 };
 T32RowEntry g_t32_rows[kMaxLog2 + 1];
+T32LandEntry g_t32_land[kMaxLog2 + 1];
 T32ColEntry g_t32_cols[kMaxLog2 + 1][4];  // W slot: 2, 4, 8, 16
 std::once_flag g_t32_once;
 
@@ -672,6 +888,15 @@ void reg_t32_row() {
     en.fn[1][0] = (const void *)k_rows_tc32<N, 1, true>;
     en.fn[1][1] = (const void *)k_rows_tc32<N, 2, true>;
     en.rows_per_cta = Sh::ROWS;
+    en.smem = Sh::SMEM;
+}
+template <int N>
+void reg_t32_land() {
+    using Sh = T32LandShape<N>;
+    T32LandEntry &en = g_t32_land[ilog2(N)];
+    en.fn[0] = (const void *)k_rows_tc32_land<N, 1>;
+    en.fn[1] = (const void *)k_rows_tc32_land<N, 2>;
+    en.rows_per_unit = Sh::L;
     en.smem = Sh::SMEM;
 }
 template <int N, int W>
@@ -690,8 +915,10 @@ void init_t32() {
         reg_t32_row<2048>();
         reg_t32_row<4096>();
         reg_t32_row<8192>();
-        // 512-thread tiles (the split form's rows are at least 16 long, so
-        // every 2D shape has nx >= 16 columns to fill them)
+        reg_t32_land<1024>();
+        reg_t32_land<2048>();
+        reg_t32_land<4096>();
+        reg_t32_land<8192>();
         // 512-thread tiles (the split form's rows are at least 16 long, so
         // every 2D shape has nx >= 16 columns to fill them)
         reg_t32_col<1024, 16>();
@@ -750,6 +977,39 @@ cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, c
     void *args[] = {(void *)&in,    (void *)&out, (void *)&tw,      (void *)&twp,      (void *)&w,
                     (void *)&nrows, (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&status};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(256), args, en.smem, s);
+}
+
+// Landed-row form: whether it covers nrows rows of n points (P = 1) or the
+// pre-split rows of ny-row slices (P = 2); 0 if not.
+int tc32_land_rows(int n) {
+    init_t32();
+    if (n < 1024 || n > 8192 || (n & (n - 1))) return 0;
+    return g_t32_land[ilog2(n)].fn[0] ? g_t32_land[ilog2(n)].rows_per_unit : 0;
+}
+
+bool tc32_land_available(int n, long long nrows, int ny, int split) {
+    const int L = tc32_land_rows(n);
+    if (L == 0 || (split != 1 && split != 2)) return false;
+    if (split == 1) return nrows % L == 0;
+    return ny % 2 == 0 && (ny / 2) % (L / 2) == 0;
+}
+
+cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
+                                  const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
+                                  int *status, int num_sms, cudaStream_t s) {
+    init_t32();
+    if (!tc32_land_available(n, nrows, ny, split)) return cudaErrorInvalidValue;
+    if (nrows <= 0) return cudaSuccess;
+    const T32LandEntry &en = g_t32_land[ilog2(n)];
+    const void *fn = en.fn[split == 2 ? 1 : 0];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
+    if (e != cudaSuccess) return e;
+    long long nunits = nrows / en.rows_per_unit;
+    long long grid = num_sms < nunits ? num_sms : nunits;  // one CTA per SM: it holds all 512 TMEM columns
+    const __half *w = static_cast<const __half *>(w32);
+    void *args[] = {(void *)&in,     (void *)&out, (void *)&tw,      (void *)&twp,      (void *)&w,
+                    (void *)&nunits, (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&status};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, en.smem, s);
 }
 
 cudaError_t launch_cols_tc32(int n, int w, int tmem_a, const CUtensorMap &map, float2 *out, const float2 *tw,

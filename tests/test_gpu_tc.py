@@ -144,17 +144,22 @@ def test_split_tc_default_is_tcgen05(g):
 
 @pytest.mark.parametrize("ny,nx,batch", [(1024, 1024, 1), (2048, 2048, 1), (4096, 4096, 1), (1024, 16, 3),
                                          (2048, 16, 2), (4096, 16, 2), (8192, 16, 1), (32, 8192, 2),
-                                         (8192, 64, 1), (16, 1024, 5), (8192, 1024, 1), (4096, 2048, 2)])
+                                         (8192, 64, 1), (16, 1024, 5), (8192, 1024, 1), (4096, 2048, 2),
+                                         (1, 1024, 7), (1, 8192, 3), (1, 4096, 3), (1, 2048, 40)])
 @pytest.mark.parametrize("inverse", [False, True])
-@pytest.mark.parametrize("tmem_a", ["1", "0"])
-def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, tmem_a):
+@pytest.mark.parametrize("form", ["land", "tmem", "smem"])
+def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, form):
     """Radix-32 tcgen05 stages on every compiled row length and column tile
     (rows of 1024..8192 points; columns of 1024, 2048, 4096, 8192 points in
     16-, 8-, 4- and 2-column tiles; the column pre-split at ny = 8192), both
-    directions, against the oracle."""
+    directions, against the oracle.  Forms: rows from landed units (where the
+    rows divide into whole units; the rest fall back), A in tensor memory, A
+    in shared memory."""
     monkeypatch.setenv("GB300FFT_TC_MMA", "tcgen05")
     monkeypatch.setenv("GB300FFT_TC_RADIX", "32")
-    monkeypatch.setenv("GB300FFT_TC_TMEM_A", tmem_a)  # A operand in tensor memory or in shared memory
+    monkeypatch.setenv("GB300FFT_TC_TMEM_A", "0" if form == "smem" else "1")
+    monkeypatch.setenv("GB300FFT_TC_LAND", "1" if form == "land" else "0")
+    tmem_a = "0" if form == "smem" else "1"
     plan = g.Plan(nx, ny, batch, inverse=inverse, precision="split_tc")
     d = plan.describe()
     x = synth.uniform_complex((batch, ny, nx), seed=7 * ny + nx + batch)
@@ -169,6 +174,10 @@ def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, tmem
     assert err <= tol_split_tc(N)
     if nx >= 1024:
         assert d["rows"]["kernel"].startswith("k_rows_tc32")
+        nrows = ny * batch
+        units = 512 // (nx // 32)
+        land = form == "land" and (nrows % units == 0 if d["split"] == 1 else (ny // 2) % (units // 2) == 0)
+        assert d["rows"]["kernel"].startswith("k_rows_tc32_land") == land
     if ny >= 1024 and nx > 1:
         assert d["cols"]["kernel"].startswith("k_cols_tc32")
 
