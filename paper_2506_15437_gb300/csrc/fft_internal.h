@@ -94,13 +94,22 @@ int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
 cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
                              int *status, cudaStream_t s);
+// Streaming split-FP16 tensor-core column pass (fft_tc_stream.cu): 4096-point
+// column blocks, tiles of tc_stream_width() columns, E = 64 twiddles; the
+// row pass stores the permutation tc_stream_perm() gives.
+bool tc_stream_available(int n, int nx);
+void tc_stream_perm(int *perm_t, int *perm_g);
+int tc_stream_width();
+int tc_stream_twiddle_e();
+cudaError_t launch_cols_tc_stream(const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32, int nx,
+                                  int batch, int split, int conj_out, int *status, int num_sms, cudaStream_t s);
 // Landed-row form (persistent, 512 threads, all TMEM columns of the SM):
 // rows per unit (0: not compiled), and whether a call is covered.
 int tc32_land_rows(int n);
 bool tc32_land_available(int n, long long nrows, int ny, int split);
 cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                                   const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
-                                  int *status, int num_sms, cudaStream_t s);
+                                  int perm_t, int perm_g, int *status, int num_sms, cudaStream_t s);
 cudaError_t launch_cols_tc32(int n, int w, int tmem_a, const CUtensorMap &map, float2 *out, const float2 *tw,
                              const void *w32, int nx, int batch, int split, int conj_out, int *status, int grid,
                              cudaStream_t s);
@@ -217,6 +226,7 @@ struct AxisPlan {
     int tc_w = 0;  // tensor-core column pass: tile width
     int tcg = 0;   // tensor-core column pass: 1 tcgen05 butterflies, 0 mma.sync
     int tc32 = 0;  // tensor-core pass with radix-32 tcgen05 stages (rows: the plan's rows axis)
+    int tcs = 0;   // tensor-core column pass also available streaming (out-of-place calls; E = 64 twiddles)
     int pair_e = 0;  // >0: column pass by 2-CTA clusters with this E (length n/2 sub-FFTs)
     int cl_c = 0, cl_e = 0;  // >0: column pass by cl_c-CTA DSMEM clusters with E = cl_e
     float2 *roots = nullptr;  // pair column pass: exp(-2*pi*i*k/n), k < n
@@ -395,6 +405,7 @@ struct fft_plan_s {
     int tc_radix = 32;      // split-FP16 plans: largest tensor-core radix allowed (32, or 16)
     int tc_tmem_a = 1;      // radix-32 tensor-core stages: A operand in tensor memory (0: shared memory)
     int tc_land = 1;        // radix-32 tensor-core rows from landed rows where the shape allows (A in TMEM)
+    int tc_stream = 1;      // tensor-core columns of 4096 points: streaming radix-64 pass where allowed
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events

@@ -237,7 +237,21 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
             if (build_twiddles(ax.tw, n, 32, 0) != cudaSuccess) return FFT_ERR_CUDA;
         }
         ax.grid = tc32_cols_grid(n, ax.tc_w, tiles_per_w / ax.tc_w, p->num_sms);
-        return ax.grid > 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
+        if (ax.grid <= 0) return FFT_ERR_UNSUPPORTED;
+        // streaming form for out-of-place calls (same tile width, its own
+        // E = 64 twiddle table, a row permutation the row pass applies)
+        if (p->tc_stream && p->tc_tmem_a && tc_stream_available(n, nx) && ax.tc_w == tc_stream_width()) {
+            const int e64 = tc_stream_twiddle_e();
+            const int sz64 = twiddle_table_size(n, e64);
+            if (sz64 > 0) {
+                ax.stream_tw = dev_alloc<float2>(p, sz64);
+                if (!ax.stream_tw) return FFT_ERR_ALLOC;
+                if (build_twiddles(ax.stream_tw, n, e64, 0) != cudaSuccess) return FFT_ERR_CUDA;
+                tc_stream_perm(&ax.perm_t, &ax.perm_g);
+                ax.tcs = 1;
+            }
+        }
+        return FFT_OK;
     }
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         ax.tc_w = tc_col_width(n, nx);
@@ -408,6 +422,7 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         if (const char *ev = getenv("GB300FFT_TC_RADIX")) p->tc_radix = atoi(ev) >= 32 ? 32 : 16;
         if (const char *ev = getenv("GB300FFT_TC_TMEM_A")) p->tc_tmem_a = atoi(ev) != 0;
         if (const char *ev = getenv("GB300FFT_TC_LAND")) p->tc_land = atoi(ev) != 0;
+        if (const char *ev = getenv("GB300FFT_TC_STREAM")) p->tc_stream = atoi(ev) != 0;
         p->w16 = dev_alloc<unsigned char>(p, 4 * 256 * 2);
         if (!p->w16) rc = FFT_ERR_ALLOC;
         else if (build_w16_table(p->w16, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
@@ -804,9 +819,13 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (weight) return FFT_ERR_UNSUPPORTED;
         if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
         const bool land = p->rows.tc32 && tc32_land_used(p, nrows, P);
+        // streaming tensor-core columns: out of place, rows from landed units
+        // stored in the permuted order
+        const bool tstream = two_pass && land && src != dst && cp.tcs;
         const cudaError_t er =
             land ? launch_rows_tc32_land(p->rows.n, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P, inv ? 1 : 0,
-                                         (inv && !two_pass) ? 1 : 0, p->status, p->num_sms, s)
+                                         (inv && !two_pass) ? 1 : 0, tstream ? cp.perm_t : 0, tstream ? cp.perm_g : 0,
+                                         p->status, p->num_sms, s)
             : p->rows.tc32 ? launch_rows_tc32(p->rows.n, p->tc_tmem_a, src, dst, p->rows.tw, p->twp, p->w32, nrows, p->ny, P,
                                             inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s)
                          : launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P,
@@ -821,7 +840,9 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                 cp.map_base = out;
             }
             const cudaError_t ec =
-                cp.tc32 ? launch_cols_tc32(cp.n, cp.tc_w, p->tc_tmem_a, cp.map, dst, cp.tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
+                tstream ? launch_cols_tc_stream(cp.map, dst, cp.stream_tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
+                                                p->status, p->num_sms, s)
+                : cp.tc32 ? launch_cols_tc32(cp.n, cp.tc_w, p->tc_tmem_a, cp.map, dst, cp.tw, p->w32, p->nx, p->batch, P, inv ? 1 : 0,
                                            p->status, cp.grid, s)
                         : launch_cols_tc(cp.n, cp.tc_w, cp.tcg, cp.map, dst, cp.tw, p->w16, p->nx, p->batch, P,
                                          inv ? 1 : 0, p->status, cp.grid, s);
@@ -1357,6 +1378,9 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
         const int re = p->rows.row ? (tc ? (p->rows.tc32 ? 32 : 16) : p->rows.row->e) : 1;
         if (p->rows.row) rad(p->rows.n, re, r1, sizeof r1);
         const gb300fft::AxisPlan &cp = p->split > 1 ? p->cols_split : p->cols;
+        // an out-of-place split-FP16 call streams the columns when the rows land
+        const bool tcs = tc && cp.tcs && p->rows.tc32 &&
+                         tc32_land_used(p, (long long)p->nx * p->ny * p->batch / p->rows.n, p->split);
         if (cp.cl_c > 0) {
             char r3[96];
             rad(cp.n / cp.cl_c, cp.cl_e, r3, sizeof r3);
@@ -1366,7 +1390,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
             rad(cp.n / 2, cp.pair_e, r3, sizeof r3);
             snprintf(r2, sizeof r2, "[2,%s", r3 + 1);
         } else if (cp.col) {
-            rad(cp.n, tc ? (cp.tc32 ? 32 : 16) : cp.col->e, r2, sizeof r2);
+            rad(cp.n, tc ? (tcs ? 64 : cp.tc32 ? 32 : 16) : cp.col->e, r2, sizeof r2);
         }
         k = snprintf(tmp, sizeof tmp,
                      "{\"kind\": \"dense\", \"precision\": \"%s\", \"rows\": {\"kernel\": \"%s<%d,%d,split%d>\", "
@@ -1375,10 +1399,10 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d}",
                      tc ? "split_fp16_tc" : "fp32", tc ? (p->rows.tc32 ? (tc32_land_used(p, (long long)p->nx * p->ny * p->batch / p->rows.n, p->split) ? "k_rows_tc32_land" : "k_rows_tc32") : p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
-                     !cp.col ? "none" : tc ? (cp.tc32 ? "k_cols_tc32" : cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
-                     cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (cp.tc32 ? 32 : 16) : cp.col->e) : 0,
+                     !cp.col ? "none" : tc ? (tcs ? "k_cols_tc_stream" : cp.tc32 ? "k_cols_tc32" : cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
+                     cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (tcs ? 64 : cp.tc32 ? 32 : 16) : cp.col->e) : 0,
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
-                     cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (cp.tc32 ? 32 : 16) : cp.col->e) : 0,
+                     cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (tcs ? 64 : cp.tc32 ? 32 : 16) : cp.col->e) : 0,
                      cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0, r2,
                      cp.grid, p->split, (!tc && cp.stream && !p->ring && stream_tstore(*cp.stream)) ? 1 : 0);
     }

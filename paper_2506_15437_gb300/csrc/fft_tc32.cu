@@ -22,21 +22,12 @@
 // so a row CTA needs only its exchange, the 16 KiB B and no extra staging.
 // A 8192-point transform is then radix 8 (float32) + two radix-32 tensor-core
 // stages; 4096 is 4 + 32 + 32, 2048 is 2 + 32 + 32, 1024 is 32 + 32.
-#include <cuda_fp16.h>
-
 #include <mutex>
 
-#include "fft_common.cuh"
 #include "fft_internal.h"
+#include "fft_tc32.cuh"
 
 namespace gb300fft {
-
-constexpr int kT32E = 32;                 // elements per thread = the tensor-core radix
-constexpr int kT32Group = 128;            // threads (butterflies) per MMA group
-constexpr int kT32ABytes = 128 * 64 * 2;  // one float16 A operand of a group: 128 rows x 64 halves (16 KiB)
-constexpr int kT32GroupStage = 2 * kT32ABytes;  // A_hi + A_lo of a group: 32 KiB
-constexpr int kT32BBytes = 64 * 64 * 2;   // one float16 B operand (8 KiB)
-static_assert(kT32GroupStage == 32768, "A_hi + A_lo of a group");
 
 // Two B tables, each B_hi then B_lo (64 x 64 float16) in the canonical
 // K-major layout of the tensor-core descriptors: element (n, k) at byte
@@ -80,85 +71,6 @@ __global__ void k_w32_table(__half *t) {
 cudaError_t build_w32_table(void *t, cudaStream_t s) {
     k_w32_table<<<32, 256, 0, s>>>(static_cast<__half *>(t));
     return cudaGetLastError();
-}
-
-// Shared-memory descriptor of a K-major operand without swizzle: core
-// matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes apart, 8-row
-// groups 1024 bytes apart (K = 64 halves).
-__device__ __forceinline__ uint64_t t32_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46);
-}
-// kind::f16: D = F32 (bit 4), A = B = F16, both K-major, N = 64, M = 128
-constexpr uint32_t kT32Idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-// the same with N = 32 (one diagonal block of the even/odd table)
-constexpr uint32_t kT32IdescN32 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void t32_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kT32Idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void t32_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ void t32_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-// MMA with A read from tensor memory (rows = lanes, two float16 per column).
-__device__ __forceinline__ void t32_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate,
-                                           uint32_t idesc = kT32Idesc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// try_wait that may suspend the thread up to `ns` nanoseconds in hardware
-// instead of returning at once, so waiting threads do not spin.
-__device__ __forceinline__ bool t32_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (~limit_ns of global time, at most 2^20 suspended polls).
-__device__ __forceinline__ bool t32_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
-        if (t32_try_wait_sleep(bar, parity, 20000)) return true;
-        if (globaltimer_ns() - t0 > limit_ns) break;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-__device__ __forceinline__ uint32_t f2h2_bits(float lo_elem, float hi_elem) {
-    const __half2 h = __floats2half2_rn(lo_elem, hi_elem);  // .x (low half) = lo_elem
-    uint32_t u;
-    memcpy(&u, &h, 4);
-    return u;
 }
 
 // Per-CTA tensor-core state of the radix-32 butterflies.  TA: the A operand
@@ -581,7 +493,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(512, 1)
     k_rows_tc32_land(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
                      const float2 *__restrict__ twp, const __half *__restrict__ w32, long long nunits, int ny,
-                     int conj_in, int conj_out, int *status) {
+                     int conj_in, int conj_out, int perm_t, int perm_g, int *status) {
     using Sh = T32LandShape<N>;
     using Eng = typename Sh::Eng;
     constexpr int E = kT32E;
@@ -669,17 +581,25 @@ __global__ void __launch_bounds__(512, 1)
                 v[b * R0 + r] = x;
             }
         }
-        long long orow = r0 + h;
+        // output row: element q of column block kp of slice b, stored at
+        // block row pos (permuted for the streaming column pass if perm_t:
+        // q = j + perm_t r goes to (j / perm_g) perm_g (Q / perm_t) + r perm_g
+        // + j % perm_g)
+        const long long b = r0 / ny;
+        const int q = (int)(r0 - b * ny) + (P == 2 ? i : h);
         if constexpr (P == 2) {
-            const long long b = r0 / ny;
-            const int q = (int)(r0 - b * ny) + i;
             if (kp) {
                 const float2 w = __ldg(twp + q);
 #pragma unroll
                 for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
             }
-            orow = b * ny + 2LL * q + kp;
         }
+        int pos = q;
+        if (perm_t) {
+            const int j = q & (perm_t - 1), r = q / perm_t;
+            pos = (j / perm_g) * perm_g * (Q / perm_t) + r * perm_g + (j & (perm_g - 1));
+        }
+        const long long orow = b * ny + (long long)P * pos + kp;
         auto after_reads = [&] {
             __syncthreads();
             if (t == 0 && next < nunits) {
@@ -996,9 +916,12 @@ bool tc32_land_available(int n, long long nrows, int ny, int split) {
 
 cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                                   const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
-                                  int *status, int num_sms, cudaStream_t s) {
+                                  int perm_t, int perm_g, int *status, int num_sms, cudaStream_t s) {
     init_t32();
     if (!tc32_land_available(n, nrows, ny, split)) return cudaErrorInvalidValue;
+    if (perm_t && (perm_g < 1 || (perm_g & (perm_g - 1)) || (perm_t & (perm_t - 1)) || (ny / split) % perm_t ||
+                   perm_t % perm_g))
+        return cudaErrorInvalidValue;
     if (nrows <= 0) return cudaSuccess;
     const T32LandEntry &en = g_t32_land[ilog2(n)];
     const void *fn = en.fn[split == 2 ? 1 : 0];
@@ -1007,8 +930,9 @@ cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const fl
     long long nunits = nrows / en.rows_per_unit;
     long long grid = num_sms < nunits ? num_sms : nunits;  // one CTA per SM: it holds all 512 TMEM columns
     const __half *w = static_cast<const __half *>(w32);
-    void *args[] = {(void *)&in,     (void *)&out, (void *)&tw,      (void *)&twp,      (void *)&w,
-                    (void *)&nunits, (void *)&ny,  (void *)&conj_in, (void *)&conj_out, (void *)&status};
+    void *args[] = {(void *)&in,       (void *)&out,     (void *)&tw,     (void *)&twp,
+                    (void *)&w,        (void *)&nunits,  (void *)&ny,     (void *)&conj_in,
+                    (void *)&conj_out, (void *)&perm_t,  (void *)&perm_g, (void *)&status};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, en.smem, s);
 }
 

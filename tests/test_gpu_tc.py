@@ -135,10 +135,11 @@ def test_split_tc_default_is_tcgen05(g):
     # lengths 1024..8192: radix-32 tensor-core stages
     plan = g.Plan(8192, 8192, 1, precision="split_tc")
     d = plan.describe()
-    assert d["rows"]["kernel"].startswith("k_rows_tc32") and d["rows"]["radices"] == [8, 32, 32]
-    # the rows pre-split the columns by 2: 4096-point column blocks
+    assert d["rows"]["kernel"].startswith("k_rows_tc32_land") and d["rows"]["radices"] == [8, 32, 32]
+    # the rows pre-split the columns by 2: 4096-point column blocks, streamed
+    # as two radix-64 stages (each a radix-2 level and two radix-32 products)
     assert d["split"] == 2
-    assert d["cols"]["kernel"].startswith("k_cols_tc32") and d["cols"]["radices"] == [4, 32, 32]
+    assert d["cols"]["kernel"].startswith("k_cols_tc_stream") and d["cols"]["radices"] == [64, 64]
     plan.close()
 
 
@@ -172,6 +173,7 @@ def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, form
     print(f"tc32 A@{'tmem' if tmem_a == '1' else 'smem'} {ny}x{nx}x{batch} inv={inverse} rows={d['rows']['kernel']} "
           f"cols={d['cols']['kernel']}: {err:.3e}")
     assert err <= tol_split_tc(N)
+    land = False
     if nx >= 1024:
         assert d["rows"]["kernel"].startswith("k_rows_tc32")
         nrows = ny * batch
@@ -179,7 +181,45 @@ def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, form
         land = form == "land" and (nrows % units == 0 if d["split"] == 1 else (ny // 2) % (units // 2) == 0)
         assert d["rows"]["kernel"].startswith("k_rows_tc32_land") == land
     if ny >= 1024 and nx > 1:
-        assert d["cols"]["kernel"].startswith("k_cols_tc32")
+        stream = land and d["cols"]["n"] == 4096 and nx % 4 == 0
+        assert d["cols"]["kernel"].startswith("k_cols_tc_stream" if stream else "k_cols_tc32")
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(8192, 8192, 1), (4096, 1024, 2), (8192, 1024, 2), (4096, 4096, 1),
+                                         (8192, 2048, 1)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_streaming_tensor_core_columns(g, monkeypatch, ny, nx, batch, inverse):
+    """Streaming split-FP16 column pass (4096-point blocks, two radix-64
+    stages of a float32 radix-2 level and two radix-32 tensor-core products,
+    rows stored permuted by the landed row pass): out of place against the
+    oracle, element by element over every slice; in place (unsplit, no
+    permutation, the radix-32 column pass) too; the result agrees with the
+    non-streaming pass within the bound."""
+    monkeypatch.setenv("GB300FFT_TC_MMA", "tcgen05")
+    monkeypatch.setenv("GB300FFT_TC_RADIX", "32")
+    plan = g.Plan(nx, ny, batch, inverse=inverse, precision="split_tc")
+    monkeypatch.setenv("GB300FFT_TC_STREAM", "0")
+    plain = g.Plan(nx, ny, batch, inverse=inverse, precision="split_tc")
+    monkeypatch.delenv("GB300FFT_TC_STREAM")
+    d = plan.describe()
+    assert d["cols"]["kernel"].startswith("k_cols_tc_stream") and d["cols"]["radices"] == [64, 64]
+    assert plain.describe()["cols"]["kernel"].startswith("k_cols_tc32")
+    x = synth.uniform_complex((batch, ny, nx), seed=5 * ny + nx + batch)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    xd = torch.from_numpy(x).cuda()
+    got = plan.execute(xd).cpu().numpy()
+    assert plan.status() == 0
+    N = nx * ny
+    err = worst_rel_l2(got, ref, N)
+    print(f"tc stream {ny}x{nx}x{batch} inv={inverse}: {err:.3e}")
+    assert err <= tol_split_tc(N)
+    other = plain.execute(xd).cpu().numpy()
+    assert worst_rel_l2(other, ref, N) <= tol_split_tc(N)
+    plan.execute(xd, out=xd)  # in place: no permuted intermediate
+    assert plan.status() == 0
+    assert worst_rel_l2(xd.cpu().numpy(), ref, N) <= tol_split_tc(N)
+    plan.close()
+    plain.close()
 
 
 @pytest.mark.parametrize("ny,nx,split", [(8192, 1024, "2"), (8192, 1024, "1"), (4096, 4096, "2"), (4096, 1024, "1")])
