@@ -206,25 +206,18 @@ struct Tc32 {
         if (!t32_wait(bar, phase)) record_status(status, kStatusTimeout);
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // D columns: 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O
-        uint32_t de[16], dof[16];
+        // D columns: 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O (all four
+        // loads in flight before the one wait)
+        uint32_t d[4][16];
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {  // real, then imaginary
-            t32_ld16(tmem + lane + 16 * part, de);
-            t32_ld16(tmem + lane + 32 + 16 * part, dof);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int q = 0; q < 4; ++q) t32_ld16(tmem + lane + 16 * q, d[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float ev = __int_as_float(de[k]), ov = __int_as_float(dof[k]);
-                const float y0 = (ev + ov) * down, y1 = (ev - ov) * down;
-                if (part == 0) {
-                    v[k].x = y0;
-                    v[k + 16].x = y1;
-                } else {
-                    v[k].y = y0;
-                    v[k + 16].y = y1;
-                }
-            }
+        for (int k = 0; k < 16; ++k) {
+            const float er = __int_as_float(d[0][k]), ei = __int_as_float(d[1][k]);
+            const float orr = __int_as_float(d[2][k]), oi = __int_as_float(d[3][k]);
+            v[k] = make_float2((er + orr) * down, (ei + oi) * down);
+            v[k + 16] = make_float2((er - orr) * down, (ei - oi) * down);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
@@ -338,14 +331,29 @@ struct T32RowShape {
     static_assert(S >= 2 && (R0 == E || R0 < E), "stage 0 radix");
 };
 
+// Barrier over the T threads of one row (row h of the CTA): a named barrier
+// (ids 5 and up; 1-4 are the MMA groups'), or the warp for 32-thread rows.
+template <int T>
+struct RowSync {
+    int h;
+    __device__ __forceinline__ void operator()() const {
+        if constexpr (T == 32)
+            __syncwarp();
+        else
+            named_sync(5 + h, T);
+    }
+};
+
 // Stages 0 .. S-1 of one N-point row held as v (stage-0 operands, already
 // loaded) by thread tt of its row's T threads, exchanging through sm (the
 // row's padded span).  sync_first: a CTA barrier precedes the first exchange
-// write (the span may still be read as input).  after_reads() runs, on every
-// thread, once the last stage has read its operands from the exchange.
-template <int N, bool TA, class AfterReads>
+// write (the span may still be read as input).  `sync` orders the accesses to
+// the row's own span (a CTA barrier, or one over the row's threads when the
+// span is the row's alone).  after_reads() runs, on every thread, once the
+// last stage has read its operands from the exchange.
+template <int N, bool TA, class Sync, class AfterReads>
 __device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E], float2 *sm, const float2 *tw, int tt,
-                                               bool sync_first, AfterReads after_reads) {
+                                               bool sync_first, Sync sync, AfterReads after_reads) {
     using Sh = T32RowShape<N>;
     using Eng = typename Sh::Eng;
     using Sc = Sched<N, kT32E>;
@@ -366,7 +374,12 @@ __device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E],
     for (int s = 1; s < S; ++s) {
         const int Rp = (s == 1) ? R0 : E;
         const int Nsp = Sc::ns(s - 1);
-        if (s > 1 || R0 == E || sync_first) __syncthreads();  // the previous staging / exchange reads are done
+        // the previous staging / exchange reads are done (the first exchange
+        // may alias input every row of the CTA reads)
+        if (s == 1 && sync_first)
+            __syncthreads();
+        else if (s > 1 || R0 == E)
+            sync();
 #pragma unroll
         for (int b = 0; b < E / Rp; ++b) {
             const int j = tt + b * T;
@@ -374,7 +387,7 @@ __device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E],
 #pragma unroll
             for (int k = 0; k < Rp; ++k) sm[Eng::pad_s((j - m) * Rp + m + k * Nsp, s)] = v[b * Rp + k];
         }
-        __syncthreads();
+        sync();
         const int Ns = Sc::ns(s);
         const int m = tt & (Ns - 1);
 #pragma unroll
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(256, 2)
             for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
         }
     }
-    t32_row_stages<N, TA>(tc, v, ex + g * Eng::SMEM_ELEMS, tw, tt, false, [] {});
+    t32_row_stages<N, TA>(tc, v, ex + g * Eng::SMEM_ELEMS, tw, tt, false, SyncBlock{}, [] {});
     if (active) {
         float2 *dst = out + row * N;
 #pragma unroll
@@ -607,7 +620,7 @@ __global__ void __launch_bounds__(512, 1)
                 issue(next);
             }
         };
-        t32_row_stages<N, true>(tc, v, land + h * Eng::SMEM_ELEMS, tw, tt, true, after_reads);
+        t32_row_stages<N, true>(tc, v, land + h * Eng::SMEM_ELEMS, tw, tt, true, RowSync<T>{h}, after_reads);
         float2 *dst = out + orow * N;
 #pragma unroll
         for (int k = 0; k < E; ++k) {

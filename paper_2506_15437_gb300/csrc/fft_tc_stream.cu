@@ -45,8 +45,8 @@ struct TcStreamShape {
     static constexpr int xch_seg(int w) { return Eng::pad(w * SEG_ELEMS); }
     static constexpr size_t RING_OFF = ((size_t)Eng::SMEM_ELEMS * sizeof(float2) + 127) / 128 * 128;
     static constexpr size_t B_OFF = (RING_OFF + (size_t)S * SEG_BYTES + 1023) / 1024 * 1024;
-    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;  // WARPS segment barriers, GROUPS MMA barriers
-    static constexpr size_t SLOT_OFF = BAR_OFF + 8 * (WARPS + GROUPS);
+    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;  // WARPS segment barriers, 2 MMA barriers per group
+    static constexpr size_t SLOT_OFF = BAR_OFF + 8 * (WARPS + 2 * GROUPS);
     static constexpr size_t SMEM = SLOT_OFF + 16;
     static_assert(GROUPS * 256 <= 512, "256 TMEM columns per group");
     static_assert(WARPS * G == T, "one warp per G butterflies");
@@ -60,7 +60,7 @@ struct TcStreamShape {
 struct Tc64Group {
     uint32_t tmem;   // group base column, lane field 0
     uint32_t b_hi;   // shared address of B_hi (B_lo follows)
-    uint64_t *bar;
+    uint64_t *bar;   // two: the products of half a, of half b
     uint32_t phase;
     int group, row;
     int *status;
@@ -94,8 +94,66 @@ struct Tc64Group {
         return __int_as_float((eb - 10) << 23);  // s / 2048
     }
 
+    // Half h's twelve products (even/odd table, small corrections first), on
+    // the elected thread, committed to barrier h.
+    __device__ __forceinline__ void issue_half(int h) {
+        const uint32_t b_lo = b_hi + kT32BBytes;
+        const uint32_t a = tmem + 128 + 64 * h;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {  // diagonal block e of the even/odd table
+            const uint32_t d = tmem + 64 * h + 32 * e, bo = 4096 * e;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int ks = 2 * e + j;
+                t32_mma_ts(d, a + 32 + 8 * ks, t32_desc(b_hi + bo + ks * 256), j, kT32IdescN32);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int ks = 2 * e + j;
+                t32_mma_ts(d, a + 8 * ks, t32_desc(b_lo + bo + ks * 256), 1, kT32IdescN32);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int ks = 2 * e + j;
+                t32_mma_ts(d, a + 8 * ks, t32_desc(b_hi + bo + ks * 256), 1, kT32IdescN32);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar + h))
+                     : "memory");
+    }
+
+    // All of the group's A rows of half h are in TMEM: one thread issues.
+    __device__ __forceinline__ void rows_written_issue(int h) {
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        named_sync(1 + group, kT32Group);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (row == 0) issue_half(h);
+    }
+
+    // Half h's products are complete: X_{2k + h} = E_k + O_k, X_{2k + 32 + h}
+    // = E_k - O_k (D columns 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O).
+    template <int H>
+    __device__ __forceinline__ void read_half(float2 (&v)[64], float down, uint32_t lane) {
+        if (!t32_wait(bar + H, phase)) record_status(status, kStatusTimeout);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t d[4][16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t32_ld16(tmem + lane + 64 * H + 16 * q, d[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float er = __int_as_float(d[0][k]), ei = __int_as_float(d[1][k]);
+            const float orr = __int_as_float(d[2][k]), oi = __int_as_float(d[3][k]);
+            v[2 * k + H] = make_float2((er + orr) * down, (ei + oi) * down);
+            v[2 * (k + 16) + H] = make_float2((er - orr) * down, (ei - oi) * down);
+        }
+    }
+
     // The calling thread's length-64 DFT (forward sign) of v, natural order
-    // in and out.  Every thread of the group calls it.
+    // in and out.  Every thread of the group calls it.  Half a's products
+    // run while half b is split, half b's while half a is read back.
     __device__ __forceinline__ void dft64(float2 (&v)[64]) {
 #pragma unroll
         for (int n = 0; n < 32; ++n) {
@@ -106,68 +164,14 @@ struct Tc64Group {
         const uint32_t lane = (uint32_t)(threadIdx.x & 96) << 16;
         // TMEM of the group: D_a [0, 64), D_b [64, 128), A_a [128, 192), A_b [192, 256)
         const float down_a = split_half<0>(v, tmem + 128, lane);
+        rows_written_issue(0);
         const float down_b = split_half<32>(v, tmem + 192, lane);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        named_sync(1 + group, kT32Group);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (row == 0) {
-            const uint32_t b_lo = b_hi + kT32BBytes;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t a = tmem + 128 + 64 * h;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {  // diagonal block e of the even/odd table
-                    const uint32_t d = tmem + 64 * h + 32 * e, bo = 4096 * e;
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int ks = 2 * e + j;
-                        t32_mma_ts(d, a + 32 + 8 * ks, t32_desc(b_hi + bo + ks * 256), j, kT32IdescN32);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int ks = 2 * e + j;
-                        t32_mma_ts(d, a + 8 * ks, t32_desc(b_lo + bo + ks * 256), 1, kT32IdescN32);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int ks = 2 * e + j;
-                        t32_mma_ts(d, a + 8 * ks, t32_desc(b_hi + bo + ks * 256), 1, kT32IdescN32);
-                    }
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(bar))
-                         : "memory");
-        }
-        if (!t32_wait(bar, phase)) record_status(status, kStatusTimeout);
+        rows_written_issue(1);
+        // X_{2k} from half a lands in even registers, which half b's inputs
+        // (v[32..63], already in TMEM) no longer need
+        read_half<0>(v, down_a, lane);
+        read_half<1>(v, down_b, lane);
         phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // D of half h: columns 0-15 Re E, 16-31 Im E, 32-47 Re O, 48-63 Im O;
-        // DFT32 output k of half h is X_{2k + h}
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float down = h ? down_b : down_a;
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                uint32_t de[16], dof[16];
-                t32_ld16(tmem + lane + 64 * h + 16 * part, de);
-                t32_ld16(tmem + lane + 64 * h + 32 + 16 * part, dof);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float ev = __int_as_float(de[k]), ov = __int_as_float(dof[k]);
-                    const float y0 = (ev + ov) * down, y1 = (ev - ov) * down;
-                    if (part == 0) {
-                        v[2 * k + h].x = y0;
-                        v[2 * (k + 16) + h].x = y1;
-                    } else {
-                        v[2 * k + h].y = y0;
-                        v[2 * (k + 16) + h].y = y1;
-                    }
-                }
-            }
-        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
 };
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(TcStreamShape<N, W, S>::THREADS, 1)
     float2 *xch = reinterpret_cast<float2 *>(raw);
     float2 *ring = reinterpret_cast<float2 *>(raw + Sh::RING_OFF);
     uint64_t *full = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);  // one per warp
-    uint64_t *mbar = full + WARPS;                                       // one per group
+    uint64_t *mbar = full + WARPS;                                       // two per group (halves a, b)
     uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::SLOT_OFF);
     __shared__ int s_fail;
     __shared__ int s_armed[WARPS];
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(TcStreamShape<N, W, S>::THREADS, 1)
             mbar_init(full + w, 1);
             s_armed[w] = 0;
         }
-        for (int gi = 0; gi < Sh::GROUPS; ++gi) mbar_init(mbar + gi, 1);
+        for (int gi = 0; gi < 2 * Sh::GROUPS; ++gi) mbar_init(mbar + gi, 1);
         fence_mbar_init();
         fence_proxy_async_smem();
         if (mt > 0)
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(TcStreamShape<N, W, S>::THREADS, 1)
     tc.row = t % kT32Group;
     tc.tmem = *slot + (uint32_t)(tc.group * 256);
     tc.b_hi = smem_u32(raw + Sh::B_OFF);
-    tc.bar = mbar + tc.group;
+    tc.bar = mbar + 2 * tc.group;
     tc.phase = 0;
     tc.status = status;
 
