@@ -20,6 +20,7 @@
 // the x axis over all rows, a tiled transpose, the y axis over the rows of
 // the transposed array, and the transpose back.
 #include <mutex>
+#include <type_traits>
 
 #include "fft_common.cuh"
 #include "fft_internal.h"
@@ -118,7 +119,12 @@ __global__ void __launch_bounds__(256) k_transpose(const float2 *__restrict__ in
 // the filter product as the transform is stored.  Phase 1: out[r][k] =
 // c[k] * F^-1(A[r])[k] for k < n, the inverse as conj(F(conj(.))) and the
 // chirp product and truncation applied as it is stored.  Two HBM passes over
-// the padded rows instead of five.
+// the padded rows instead of five.  Phase 2 does both in one pass: the
+// forward transform's outputs stay in registers -- thread tt holds elements
+// tt + m*T (m < E) in the last stage's order, exactly the elements its
+// stage-0 inputs of the inverse transform are, in another register order --
+// so the filter product, the conjugation and that compile-time register
+// permutation connect the two transforms without touching HBM.
 template <int N, int E>
 struct BluShape {
     static constexpr int T = N / E;
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(BluShape<N, E>::THREADS, BluShape<N, E>::MINB)
         for (int r = 0; r < R0; ++r) {
             const int i = j + r * (N / R0);
             float2 x = make_float2(0.f, 0.f);
-            if constexpr (PHASE == 0) {
+            if constexpr (PHASE != 1) {
                 if (active && i < n) x = cmul(__ldg(src + row * n + i), __ldg(chirp + i));
             } else {
                 if (active) {
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(BluShape<N, E>::THREADS, BluShape<N, E>::MINB)
     auto store = [&](int i, int, float2 x) {
         if constexpr (PHASE == 0) {
             if (active) dst[row * N + i] = cmul(x, __ldg(H + i));
-        } else {
+        } else {  // phases 1 and 2: the inverse's outputs
             if (active && i < n) {
                 x.y = -x.y;
                 dst[row * n + i] = cmul(x, __ldg(chirp + i));
@@ -173,10 +179,56 @@ __global__ void __launch_bounds__(BluShape<N, E>::THREADS, BluShape<N, E>::MINB)
         }
     };
     auto none = [] {};
-    if constexpr (Eng::NT >= 32)
-        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncBlock{}, none, store);
-    else
-        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, SyncWarp{}, none, store);
+    using Sync = typename std::conditional<(Eng::NT >= 32), SyncBlock, SyncWarp>::type;
+    if constexpr (PHASE < 2) {
+        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, Sync{}, none, store);
+    } else if constexpr (Eng::S == 1) {
+        // one in-register stage (N = E, one thread per row, no shared
+        // memory): v[k] is element k both as the forward's output and as the
+        // inverse's input
+        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, Sync{}, none, [](int, int, float2) {});
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            float2 y = cmul(v[k], __ldg(H + k));
+            y.y = -y.y;
+            v[k] = y;
+        }
+        Eng::template run<FftPolicy, false>(v, sm, tw, tt, 0, Sync{}, none, store);
+    } else {
+        // forward transform; its natural-order outputs, times the filter and
+        // conjugated, go back into the exchange once every thread has read
+        // its last-stage operands, and the inverse loads its stage-0 inputs
+        // from there.  The two transforms are one loop body run twice (not
+        // unrolled): two inlined copies of the engine would be scheduled into
+        // each other and spill.
+        static_assert(Eng::SMEM_ELEMS >= N, "the exchange holds the whole padded row");
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ++ph) {
+            if (ph == 1) {
+                Sync{}();  // every forward output is in the exchange
+#pragma unroll
+                for (int b = 0; b < E / R0; ++b) {
+                    const int j = tt + b * T;
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) v[b * R0 + r] = sm[Eng::pad(j + r * (N / R0))];
+                }
+            }
+            auto reads_done = [&] {
+                if (ph == 0) Sync{}();  // the forward's outputs overwrite the exchange
+            };
+            auto out = [&](int i, int c, float2 x) {
+                if (ph == 0) {
+                    float2 y = cmul(x, __ldg(H + i));
+                    y.y = -y.y;
+                    sm[Eng::pad(i)] = y;
+                } else {
+                    store(i, c, x);
+                }
+            };
+            // (ph = 1: the stage-0 reads above precede the first exchange writes)
+            Eng::template run<FftPolicy, true>(v, sm, tw, tt, 0, Sync{}, reads_done, out);
+        }
+    }
 }
 
 namespace {
@@ -190,6 +242,7 @@ void reg_blu() {
     BluVariant &v = g_blu[ilog2(N)];
     v.fn[0] = (const void *)k_blu<N, E, 0>;
     v.fn[1] = (const void *)k_blu<N, E, 1>;
+    v.fn[2] = (const void *)k_blu<N, E, 2>;
     v.n = N;
     v.e = E;
     v.threads = Sh::THREADS;
@@ -229,7 +282,7 @@ const BluVariant *blu_variant(int M) {
 
 cudaError_t launch_blu(const BluVariant &v, int phase, const float2 *src, float2 *dst, const float2 *tw,
                        const float2 *chirp, const float2 *H, int n, long long rows, cudaStream_t s) {
-    if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
+    if (phase < 0 || phase > 2) return cudaErrorInvalidValue;
     if (v.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(v.fn[phase], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return e;

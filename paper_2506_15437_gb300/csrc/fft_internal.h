@@ -265,7 +265,8 @@ struct FourStepPlan {
 // power-of-two sub-plan (M == 0) or by Bluestein over a length-M sub-plan.
 // Fused Bluestein kernels for one padded length M (fft_bluestein.cu).
 struct BluVariant {
-    const void *fn[2] = {nullptr, nullptr};  // phase 0 (forward, chirp in, filter out), 1 (inverse, chirp out)
+    // phase 0 (forward, chirp in, filter out), 1 (inverse, chirp out), 2 (both in one pass)
+    const void *fn[3] = {nullptr, nullptr, nullptr};
     int n = 0, e = 0, threads = 0, rows_per_cta = 0;
     size_t smem = 0;
 };
@@ -333,12 +334,13 @@ struct AnyAxis {
     float2 *mtwa = nullptr, *mtwb = nullptr, *fs_hi = nullptr, *fs_lo = nullptr, *fs_work = nullptr;
     float2 *mtw = nullptr;              // mixed-radix twiddles (forward)
     const BluVariant *fused = nullptr;  // M <= 8192: fused kernels (same E as the sub-plan's row pass)
+    bool fused_one = false;             // the fused transform in one pass (no padded workspace)
     int n = 1, M = 0;
     long long rows = 0;
     fft_plan_s *sub = nullptr;           // (n or M, 1, rows), run forward and inverse
     float2 *chirp[2] = {nullptr, nullptr};  // [0] forward exp(-pi i j^2/n), [1] its conjugate
     float2 *H[2] = {nullptr, nullptr};      // F(filter)/M for each direction
-    float2 *A = nullptr;                    // rows * M workspace
+    float2 *A = nullptr;                    // rows * M workspace (not with the one-pass form)
 };
 // A plan whose sizes are not all powers of two: x axis over the rows, then
 // (2D) transpose, y axis over the rows of the transposed array, transpose back.

@@ -575,16 +575,16 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_n
         ax.H[d] = dev_alloc<float2>(p, ax.M);
         if (!ax.chirp[d] || !ax.H[d]) return FFT_ERR_ALLOC;
     }
-    ax.A = dev_alloc<float2>(p, (size_t)rows * ax.M);
-    if (!ax.A) return FFT_ERR_ALLOC;
+    float2 *filt = dev_alloc<float2>(p, ax.M);
+    if (!filt) return FFT_ERR_ALLOC;
     // H[d] = F(filter of chirp d) / M through a one-row plan of length M
     fft_plan_s *one = create_dense(ax.M, 1, 1, FFT_FORWARD, FFT_PREC_FP32, default_schedule(ax.M, 1), &rc);
     if (!one) return rc;
     for (int d = 0; d < 2 && rc == FFT_OK; ++d) {
         if (build_chirp(ax.chirp[d], n, d == 0 ? -1 : 1, 0) != cudaSuccess ||
-            build_chirp_filter(ax.A, ax.chirp[d], n, ax.M, 0) != cudaSuccess)
+            build_chirp_filter(filt, ax.chirp[d], n, ax.M, 0) != cudaSuccess)
             rc = FFT_ERR_CUDA;
-        if (rc == FFT_OK) rc = run_dense(one, ax.A, ax.H[d], FFT_FORWARD, nullptr, 1.f, 0);
+        if (rc == FFT_OK) rc = run_dense(one, filt, ax.H[d], FFT_FORWARD, nullptr, 1.f, 0);
         if (rc == FFT_OK && launch_scale(ax.H[d], ax.M, 1.0f / (float)ax.M, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
     }
     if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
@@ -596,6 +596,16 @@ int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_n
     if (rc == FFT_OK && fv && ax.sub->rows.row && ax.sub->fs.n1 == 0 && !ax.sub->any &&
         fv->e == ax.sub->rows.row->e && (ax.sub->rows.tw || ax.sub->rows.row->tw_size == 0))
         ax.fused = fv;
+    // the one-pass fused kernel needs no padded workspace; it is the faster
+    // form up to M = 2048 (measured: 0.37 against 0.43 ms for 65536 rows of
+    // 500 points, M = 1024), the two-pass one from M = 4096 (0.96 against
+    // 0.81 ms for 32768 rows of 2047 points)
+    const char *e1 = getenv("GB300FFT_BLUESTEIN_ONEPASS");  // 0 / 1 forces the form
+    ax.fused_one = ax.fused && ax.fused->fn[2] && (e1 ? atoi(e1) != 0 : ax.M <= 2048);
+    if (rc == FFT_OK && !ax.fused_one) {
+        ax.A = dev_alloc<float2>(p, (size_t)rows * ax.M);
+        if (!ax.A) return FFT_ERR_ALLOC;
+    }
     return rc;
 }
 
@@ -700,6 +710,13 @@ int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStrea
     if (!ax.M) return run_dense(ax.sub, in, out, sign, nullptr, 1.f, s);
     const int d = sign > 0 ? 1 : 0;
     if (ax.fused) {
+        // one pass (each CTA reads its rows before it writes them, so in
+        // place is fine), or the two-pass form through the padded rows
+        if (ax.fused_one)
+            return launch_blu(*ax.fused, 2, in, out, ax.sub->rows.tw, ax.chirp[d], ax.H[d], ax.n, ax.rows, s) ==
+                           cudaSuccess
+                       ? FFT_OK
+                       : FFT_ERR_CUDA;
         if (launch_blu(*ax.fused, 0, in, ax.A, ax.sub->rows.tw, ax.chirp[d], ax.H[d], ax.n, ax.rows, s) != cudaSuccess ||
             launch_blu(*ax.fused, 1, ax.A, out, ax.sub->rows.tw, ax.chirp[d], nullptr, ax.n, ax.rows, s) != cudaSuccess)
             return FFT_ERR_CUDA;
@@ -1345,8 +1362,8 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "\"fused\": %d, \"mixed\": %d, \"mixed_fourstep\": [%d, %d]}, \"y\": {\"n\": %d, "
                      "\"bluestein_m\": %d, \"fused\": %d, \"mixed\": %d, \"mixed_fourstep\": [%d, %d]}, "
                      "\"transposes\": %d}",
-                     ap.x.n, ap.x.M, ap.x.fused ? 1 : 0, ap.x.mixed ? 1 : 0, ap.x.n1, ap.x.n2, ap.y.n, ap.y.M,
-                     ap.y.fused ? 1 : 0, ap.y.mixed ? 1 : 0, ap.y.n1, ap.y.n2,
+                     ap.x.n, ap.x.M, ap.x.fused ? (ap.x.fused_one ? 2 : 1) : 0, ap.x.mixed ? 1 : 0, ap.x.n1, ap.x.n2,
+                     ap.y.n, ap.y.M, ap.y.fused ? (ap.y.fused_one ? 2 : 1) : 0, ap.y.mixed ? 1 : 0, ap.y.n1, ap.y.n2,
                      (p->nx > 1 && p->ny > 1 && !ap.y_cols) ? 2 : 0);
     } else if (p->fs.n1 > 0) {
         const gb300fft::FourStepPlan &fs = p->fs;

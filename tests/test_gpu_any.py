@@ -130,28 +130,43 @@ def test_mixed_radix_fourstep(g, n, batch, inverse):
     plan.close()
 
 
-@pytest.mark.parametrize("n", [5, 100, 1000, 4095])
-def test_fused_and_unfused_bluestein_agree(g, monkeypatch, n):
-    """Padded lengths up to 8192 run the fused kernels (chirp and filter
-    products inside the two transforms); both forms meet the bound and agree
-    closely (the same arithmetic in a different grouping of passes)."""
+@pytest.mark.parametrize("n", [5, 100, 1000, 4095, 2049, 3])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fused_and_unfused_bluestein_agree(g, monkeypatch, n, inverse):
+    """Padded lengths up to 8192 run the fused kernels: by default one pass
+    (the forward transform's outputs stay in registers, times the filter,
+    into the inverse), else two passes through the padded rows (chirp and
+    filter products inside the two transforms), else five.  Every form meets
+    the bound against the oracle; the one-pass form also in place."""
     x = synth.uniform_complex((3, n), seed=77 + n)
     monkeypatch.setenv("GB300FFT_MIXED", "0")  # smooth lengths take Bluestein too
-    fused = g.Plan(n, 1, 3)
-    assert fused.describe()["x"]["fused"] == 1
+    default = g.Plan(n, 1, 3, inverse=inverse)
+    M = default.describe()["x"]["bluestein_m"]
+    assert default.describe()["x"]["fused"] == (2 if M <= 2048 else 1)  # the faster form per padded length
+    default.close()
+    monkeypatch.setenv("GB300FFT_BLUESTEIN_ONEPASS", "1")
+    one = g.Plan(n, 1, 3, inverse=inverse)
+    assert one.describe()["x"]["fused"] == 2
+    monkeypatch.setenv("GB300FFT_BLUESTEIN_ONEPASS", "0")
+    two = g.Plan(n, 1, 3, inverse=inverse)
+    monkeypatch.delenv("GB300FFT_BLUESTEIN_ONEPASS")
+    assert two.describe()["x"]["fused"] == 1
     monkeypatch.setenv("GB300FFT_BLUESTEIN_FUSED", "0")
-    plain = g.Plan(n, 1, 3)
+    plain = g.Plan(n, 1, 3, inverse=inverse)
     monkeypatch.delenv("GB300FFT_BLUESTEIN_FUSED")
     monkeypatch.delenv("GB300FFT_MIXED")
     assert plain.describe()["x"]["fused"] == 0
     d = torch.from_numpy(x).cuda()
-    a = fused.execute(d).cpu().numpy()
-    b = plain.execute(d).cpu().numpy()
-    ref = oracle.fft1d_any(x, threads=ORACLE_THREADS)
-    assert worst_rel_l2(a, ref, n) <= tol_any(n, 1, mixed=False)
-    assert worst_rel_l2(b, ref, n) <= tol_any(n, 1, mixed=False)
-    fused.close()
-    plain.close()
+    ref = oracle.fft1d_any(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    for plan in (one, two, plain):
+        got = plan.execute(d).cpu().numpy()
+        assert plan.status() == 0
+        assert worst_rel_l2(got, ref, n) <= tol_any(n, 1, mixed=False), plan.describe()["x"]["fused"]
+    a = one.execute(d).cpu().numpy()
+    one.execute(d, out=d)  # in place: each CTA reads its rows before it writes them
+    assert np.array_equal(d.cpu().numpy(), a)
+    for plan in (one, two, plain):
+        plan.close()
 
 
 def test_describe_and_unsupported(g):
