@@ -346,14 +346,14 @@ struct RowSync {
 
 // Stages 0 .. S-1 of one N-point row held as v (stage-0 operands, already
 // loaded) by thread tt of its row's T threads, exchanging through sm (the
-// row's padded span).  sync_first: a CTA barrier precedes the first exchange
-// write (the span may still be read as input).  `sync` orders the accesses to
-// the row's own span (a CTA barrier, or one over the row's threads when the
-// span is the row's alone).  after_reads() runs, on every thread, once the
-// last stage has read its operands from the exchange.
-template <int N, bool TA, class Sync, class AfterReads>
+// row's padded span).  first() runs before the first exchange write (a
+// barrier when the span may still be read as input).  `sync` orders the
+// accesses to the row's own span (a CTA barrier, or one over the row's
+// threads when the span is the row's alone).  after_reads() runs, on every
+// thread, once the last stage has read its operands from the exchange.
+template <int N, bool TA, class First, class Sync, class AfterReads>
 __device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E], float2 *sm, const float2 *tw, int tt,
-                                               bool sync_first, Sync sync, AfterReads after_reads) {
+                                               First first, Sync sync, AfterReads after_reads) {
     using Sh = T32RowShape<N>;
     using Eng = typename Sh::Eng;
     using Sc = Sched<N, kT32E>;
@@ -374,12 +374,11 @@ __device__ __forceinline__ void t32_row_stages(Tc32<TA> &tc, float2 (&v)[kT32E],
     for (int s = 1; s < S; ++s) {
         const int Rp = (s == 1) ? R0 : E;
         const int Nsp = Sc::ns(s - 1);
-        // the previous staging / exchange reads are done (the first exchange
-        // may alias input every row of the CTA reads)
-        if (s == 1 && sync_first)
-            __syncthreads();
-        else if (s > 1 || R0 == E)
-            sync();
+        // the previous staging / exchange reads are done; before the first
+        // exchange write, first() orders it after the reads of whatever input
+        // the span aliases (a no-op if none)
+        if (s == 1) first();
+        if (s > 1 || R0 == E) sync();
 #pragma unroll
         for (int b = 0; b < E / Rp; ++b) {
             const int j = tt + b * T;
@@ -461,7 +460,7 @@ __global__ void __launch_bounds__(256, 2)
             for (int k = 0; k < E; ++k) v[k] = cmul(v[k], w);
         }
     }
-    t32_row_stages<N, TA>(tc, v, ex + g * Eng::SMEM_ELEMS, tw, tt, false, SyncBlock{}, [] {});
+    t32_row_stages<N, TA>(tc, v, ex + g * Eng::SMEM_ELEMS, tw, tt, [] {}, SyncBlock{}, [] {});
     if (active) {
         float2 *dst = out + row * N;
 #pragma unroll
@@ -476,7 +475,8 @@ __global__ void __launch_bounds__(256, 2)
 
 // ---------------------------------------------------------------------------
 // Row pass from landed rows: one persistent 512-thread CTA per SM (four MMA
-// groups, all 512 TMEM columns), L = 512 / T output rows per unit.  The unit's
+// groups, all 512 TMEM columns), L = 512 / T output rows per unit.  Compiled
+// for the pre-split rows (P = 2); unsplit rows take k_rows_tc32_land1 below.  The unit's
 // input rows land in shared memory through bulk copies on one mbarrier (P = 1:
 // L consecutive rows, one copy; P = 2: L/2 consecutive pairs q, q + ny/2, two
 // copies, each input row crossing HBM once for both of its output rows).
@@ -620,13 +620,147 @@ __global__ void __launch_bounds__(512, 1)
                 issue(next);
             }
         };
-        t32_row_stages<N, true>(tc, v, land + h * Eng::SMEM_ELEMS, tw, tt, true, RowSync<T>{h}, after_reads);
+        t32_row_stages<N, true>(tc, v, land + h * Eng::SMEM_ELEMS, tw, tt, [] { __syncthreads(); }, RowSync<T>{h},
+                                after_reads);
         float2 *dst = out + orow * N;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             float2 x = v[k];
             x.y *= so;
             dst[tt + k * T] = x;
+        }
+    }
+    tc.finish();
+}
+
+// Unsplit rows from landed rows in independent sub-units: without the
+// pre-split no output row needs another row's input, so the CTA's 512 threads
+// form K sub-units of U = RS * T threads (RS rows each, U = 128 or 256), each
+// with its own landing barrier and its own persistent loop over units of RS
+// rows: it lands its rows (one bulk copy per row, into the row's own exchange
+// span), transforms them, and starts its next unit's copies once its rows'
+// last-stage operands are read.  No barrier spans two sub-units, so their
+// tensor-core products and waits interleave instead of running in step.
+template <int N>
+struct T32Land1Shape {
+    static constexpr int T = N / kT32E;
+    static constexpr int THREADS = 512;
+    static constexpr int L = THREADS / T;                // rows in the CTA
+    static constexpr int RS = T >= kT32Group ? 1 : kT32Group / T;  // rows per sub-unit
+    static constexpr int U = RS * T;                     // threads per sub-unit
+    static constexpr int K = THREADS / U;                // sub-units
+    using Eng = typename T32RowShape<N>::Eng;
+    static constexpr int SPAN = (Eng::SMEM_ELEMS + 1) / 2 * 2;  // float2 per row span, 16-byte multiple
+    static constexpr size_t BUF = (size_t)L * SPAN * sizeof(float2);
+    static constexpr size_t B_OFF = (BUF + 1023) / 1024 * 1024;
+    static constexpr size_t BAR_OFF = B_OFF + 2 * kT32BBytes;  // [0, 4) MMA groups, [4, 4 + K) landing
+    static constexpr size_t SLOT_OFF = BAR_OFF + 8 * (4 + K);
+    static constexpr size_t SMEM = SLOT_OFF + 16;
+    static_assert(U == 128 || U == 256, "one or two MMA groups per sub-unit");
+    static_assert(SPAN >= N, "a span holds a landed row");
+};
+
+template <int N>
+__global__ void __launch_bounds__(512, 1)
+    k_rows_tc32_land1(const float2 *__restrict__ in, float2 *out, const float2 *__restrict__ tw,
+                      const __half *__restrict__ w32, long long nrows, int ny, int conj_in, int conj_out, int perm_t,
+                      int perm_g, int *status) {
+    using Sh = T32Land1Shape<N>;
+    constexpr int E = kT32E;
+    constexpr int T = Sh::T;
+    constexpr int RS = Sh::RS;
+    constexpr int U = Sh::U;
+    constexpr int K = Sh::K;
+    constexpr int R0 = T32RowShape<N>::R0;
+    extern __shared__ __align__(1024) unsigned char raw[];
+    float2 *spans = reinterpret_cast<float2 *>(raw);  // [L][SPAN]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(raw + Sh::SLOT_OFF);
+    __shared__ int s_ok[K];
+    Tc32<true> tc;
+    tc.init(w32, raw + Sh::B_OFF, bars, slot, raw, status);
+    const int t = threadIdx.x;
+    const int h = t / T;  // row of the CTA (its span)
+    const int tt = t - h * T;
+    const int k = t / U;  // sub-unit
+    const bool lead = (t % U) == 0;
+    uint64_t *lbar = bars + 4 + k;
+    const float si = conj_in ? -1.f : 1.f;
+    const float so = conj_out ? -1.f : 1.f;
+    // the sub-unit's barrier: its MMA group (U = 128) or its row (U = 256)
+    auto sub_sync = [&] {
+        if constexpr (U == kT32Group)
+            named_sync(1 + t / kT32Group, kT32Group);
+        else
+            named_sync(5 + k, U);
+    };
+    const long long nsub = nrows / RS;
+    const long long stride = (long long)gridDim.x * K;
+    auto issue = [&](long long su) {  // lead thread: the RS rows of unit su
+        mbar_expect_tx(lbar, (uint32_t)(RS * N * sizeof(float2)));
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+            bulk_load(spans + (size_t)(k * RS + i) * Sh::SPAN, in + (su * RS + i) * N, N * sizeof(float2), lbar);
+    };
+    if (t == 0) {
+        for (int j = 0; j < K; ++j) mbar_init(bars + 4 + j, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long su = (long long)blockIdx.x * K + k;
+    uint32_t phase = 0;
+    if (lead && su < nsub) issue(su);
+    for (; su < nsub; su += stride) {
+        const long long next = su + stride;
+        if (lead && next < nsub) bulk_prefetch_l2(in + next * RS * N, RS * N * sizeof(float2));
+        if (lead) s_ok[k] = mbar_wait_bounded(lbar, phase) ? 1 : 0;
+        sub_sync();
+        if (!s_ok[k]) {
+            if (lead) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(lbar, phase);  // give the copies in flight a last chance to land
+            }
+            break;  // leave through finish(): the TMEM columns must be freed
+        }
+        phase ^= 1;
+        float2 *sm = spans + (size_t)h * Sh::SPAN;
+        float2 v[E];
+#pragma unroll
+        for (int b = 0; b < E / R0; ++b) {
+            const int j = tt + b * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                float2 x = sm[j + r * (N / R0)];
+                x.y *= si;
+                v[b * R0 + r] = x;
+            }
+        }
+        // output row; with perm_t, row y of slice b goes to block row pos
+        // (the streaming column pass's order, as in the pre-split form)
+        long long orow = su * RS + (h - k * RS);
+        if (perm_t) {
+            const long long b = orow / ny;
+            const int y = (int)(orow - b * ny);
+            const int j = y & (perm_t - 1), r = y / perm_t;
+            orow = b * ny + (j / perm_g) * perm_g * (ny / perm_t) + r * perm_g + (j & (perm_g - 1));
+        }
+        auto after_reads = [&] {
+            sub_sync();
+            if (lead && next < nsub) {
+                fence_proxy_async_smem();
+                issue(next);
+            }
+        };
+        // the row's span is its own landed row: a row barrier orders the
+        // stage-0 reads before the first exchange write
+        t32_row_stages<N, true>(tc, v, sm, tw, tt, RowSync<T>{h}, RowSync<T>{h}, after_reads);
+        float2 *dst = out + orow * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            float2 x = v[e];
+            x.y *= so;
+            dst[tt + e * T] = x;
         }
     }
     tc.finish();
@@ -796,9 +930,12 @@ struct T32RowEntry {
     size_t smem = 0;
 };
 struct T32LandEntry {
-    const void *fn[2] = {nullptr, nullptr};  // [P = 1, 2]
+    const void *fn2 = nullptr;  // pre-split rows (P = 2), landed in row pairs
     int rows_per_unit = 0;
     size_t smem = 0;
+    const void *fn1 = nullptr;  // unsplit rows (P = 1) in independent sub-units
+    int rows_per_sub = 0, subs = 0;
+    size_t smem1 = 0;
 };
 struct T32ColEntry {
     const void *fn[2] = {nullptr, nullptr};  // [A in TMEM]
@@ -827,10 +964,14 @@ template <int N>
 void reg_t32_land() {
     using Sh = T32LandShape<N>;
     T32LandEntry &en = g_t32_land[ilog2(N)];
-    en.fn[0] = (const void *)k_rows_tc32_land<N, 1>;
-    en.fn[1] = (const void *)k_rows_tc32_land<N, 2>;
+    en.fn2 = (const void *)k_rows_tc32_land<N, 2>;
     en.rows_per_unit = Sh::L;
     en.smem = Sh::SMEM;
+    using S1 = T32Land1Shape<N>;
+    en.fn1 = (const void *)k_rows_tc32_land1<N>;
+    en.rows_per_sub = S1::RS;
+    en.subs = S1::K;
+    en.smem1 = S1::SMEM;
 }
 template <int N, int W>
 void reg_t32_col() {
@@ -917,13 +1058,13 @@ cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, c
 int tc32_land_rows(int n) {
     init_t32();
     if (n < 1024 || n > 8192 || (n & (n - 1))) return 0;
-    return g_t32_land[ilog2(n)].fn[0] ? g_t32_land[ilog2(n)].rows_per_unit : 0;
+    return g_t32_land[ilog2(n)].fn2 ? g_t32_land[ilog2(n)].rows_per_unit : 0;
 }
 
 bool tc32_land_available(int n, long long nrows, int ny, int split) {
     const int L = tc32_land_rows(n);
     if (L == 0 || (split != 1 && split != 2)) return false;
-    if (split == 1) return nrows % L == 0;
+    if (split == 1) return nrows % g_t32_land[ilog2(n)].rows_per_sub == 0;
     return ny % 2 == 0 && (ny / 2) % (L / 2) == 0;
 }
 
@@ -937,12 +1078,24 @@ cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const fl
         return cudaErrorInvalidValue;
     if (nrows <= 0) return cudaSuccess;
     const T32LandEntry &en = g_t32_land[ilog2(n)];
-    const void *fn = en.fn[split == 2 ? 1 : 0];
+    const __half *w = static_cast<const __half *>(w32);
+    if (split == 1) {
+        // independent sub-units of rows_per_sub rows, subs per CTA, one CTA per SM
+        cudaError_t e = cudaFuncSetAttribute(en.fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem1);
+        if (e != cudaSuccess) return e;
+        const long long nsub = nrows / en.rows_per_sub;
+        const long long ctas = (nsub + en.subs - 1) / en.subs;
+        const long long grid = num_sms < ctas ? num_sms : ctas;
+        void *args[] = {(void *)&in,      (void *)&out,      (void *)&tw,     (void *)&w,
+                        (void *)&nrows,   (void *)&ny,       (void *)&conj_in, (void *)&conj_out,
+                        (void *)&perm_t,  (void *)&perm_g,   (void *)&status};
+        return cudaLaunchKernel(en.fn1, dim3((unsigned)grid), dim3(512), args, en.smem1, s);
+    }
+    const void *fn = en.fn2;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)en.smem);
     if (e != cudaSuccess) return e;
     long long nunits = nrows / en.rows_per_unit;
     long long grid = num_sms < nunits ? num_sms : nunits;  // one CTA per SM: it holds all 512 TMEM columns
-    const __half *w = static_cast<const __half *>(w32);
     void *args[] = {(void *)&in,       (void *)&out,     (void *)&tw,     (void *)&twp,
                     (void *)&w,        (void *)&nunits,  (void *)&ny,     (void *)&conj_in,
                     (void *)&conj_out, (void *)&perm_t,  (void *)&perm_g, (void *)&status};

@@ -177,8 +177,9 @@ def test_radix32_tensor_core_shapes(g, monkeypatch, ny, nx, batch, inverse, form
     if nx >= 1024:
         assert d["rows"]["kernel"].startswith("k_rows_tc32")
         nrows = ny * batch
-        units = 512 // (nx // 32)
-        land = form == "land" and (nrows % units == 0 if d["split"] == 1 else (ny // 2) % (units // 2) == 0)
+        units = 512 // (nx // 32)  # rows per landed unit of the pre-split form
+        rs = max(1, 128 // (nx // 32))  # rows per sub-unit of the unsplit form
+        land = form == "land" and (nrows % rs == 0 if d["split"] == 1 else (ny // 2) % (units // 2) == 0)
         assert d["rows"]["kernel"].startswith("k_rows_tc32_land") == land
     if ny >= 1024 and nx > 1:
         stream = land and d["cols"]["n"] == 4096 and nx % 4 == 0
