@@ -509,6 +509,12 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(8192, 8192, 1)
         y = torch.empty_like(x)
         run = lambda: plan.execute(x, out=y)  # noqa: E731
+    elif name == "bluestein_1001":
+        # 32768 signals of 1001 = 7 11 13 points: one-pass fused Bluestein over M = 2048
+        x = torch.from_numpy(synth.uniform_complex((32768, 1001), seed=SEED)).to(dev)
+        plan = g.Plan(1001, 1, 32768)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     elif name == "bluestein_4095":
         # 8192 signals of 4095 = 3^2 5 7 13 points: fused Bluestein over M = 8192
         x = torch.from_numpy(synth.uniform_complex((8192, 4095), seed=SEED)).to(dev)
@@ -560,7 +566,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
-                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff",
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001",
                              "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
