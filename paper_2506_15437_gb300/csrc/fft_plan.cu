@@ -299,6 +299,9 @@ int setup_col_axis(fft_plan_s *p, AxisPlan &ax, int n, int nx, long long tiles_p
         }
     }
     int w = default_col_w(n, nx);
+    // small arrays: narrower tiles (down to 32-byte tile rows) until there is
+    // a tile per SM (1024^2: 0.0144 -> 0.0120 ms; 512^2: 0.0105 -> 0.0084)
+    while (w > 4 && tiles_per_w / w < p->num_sms && col_variant(ilog2(n), preferred_col_e(n, w / 2), w / 2)) w /= 2;
     int e = preferred_col_e(n, w);
     if (sc.col_kind == kColTile && sc.col_e > 0 && col_variant(ilog2(n), sc.col_e, w)) e = sc.col_e;
     if (sc.col_kind == kColTile && sc.col_w >= 2 && sc.col_w <= nx && col_variant(ilog2(n), e, sc.col_w)) w = sc.col_w;
