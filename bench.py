@@ -564,6 +564,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--eager", action="store_true", help="enqueue the timed steps one by one (no CUDA graph)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
                     choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001",
@@ -615,17 +616,48 @@ def main():
     torch.cuda.synchronize()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    # The K timed steps are captured once into a CUDA graph (each step: its
+    # three pass events as event-record nodes, the row and column kernels)
+    # and replayed as one launch, so a slow or busy host cannot starve the
+    # GPU between steps; --eager enqueues them one by one instead.
+    graph = None
+    timing = "eager"
+    if not args.eager:
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                for k in range(args.steps):
+                    plan.set_pass_events(*evs[k])
+                    plan.execute(x, out=out)
+            plan.set_pass_events(None, None, None)
+            graph.replay()  # untimed
+            torch.cuda.synchronize()
+            timing = "cuda_graph"
+        except Exception as exc:  # capture refused: time eagerly
+            plan.set_pass_events(None, None, None)
+            torch.cuda.synchronize()
+            graph = None
+            timing = f"eager (graph capture failed: {type(exc).__name__})"
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
     clocks.mark()
     start.record()
-    for k in range(args.steps):
-        plan.set_pass_events(*evs[k])
-        plan.execute(x, out=out)
+    t_host = time.perf_counter()
+    if graph is not None:
+        graph.replay()
+    else:
+        for k in range(args.steps):
+            plan.set_pass_events(*evs[k])
+            plan.execute(x, out=out)
     end.record()
+    host_ms = (time.perf_counter() - t_host) * 1e3 / args.steps  # enqueue time per step (diagnostic)
     torch.cuda.synchronize()
     clocks.mark()
     if pg:
         pg.barrier()
     plan.set_pass_events(None, None, None)
+    del graph  # the replayed graph is not needed again
     ms = max_over_ranks(pg, start.elapsed_time(end) / args.steps, dev)
     status = plan.status()
     rows_ms = sum(t[0].elapsed_time(t[1]) for t in evs) / args.steps
@@ -681,7 +713,8 @@ def main():
             "e2e": {"value": job_gflops(world, flops_2d(NX, NY), e2e_ms), "unit": "GFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": 2 * args.steps,
-            "clocks": clk, "status": status}
+            "clocks": clk, "status": status, "timing": timing,
+            "host_enqueue_ms_per_step": host_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x_host.numpy())
     if rank == 0 and world == 1 and not args.no_forms:

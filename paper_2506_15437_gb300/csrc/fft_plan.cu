@@ -735,13 +735,24 @@ int run_any_axis(AnyAxis &ax, const float2 *in, float2 *out, int sign, cudaStrea
     return FFT_OK;
 }
 
+// Records pass event i on s.  Under stream capture it is recorded as an
+// event-record node (cudaEventRecordExternal), so a captured step still
+// time-stamps its passes when the graph runs (a plain record there would only
+// order work inside the graph); the flag is not accepted outside capture.
+static cudaError_t pass_event(const fft_plan_s *p, int i, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cudaErrorUnknown;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(p->ev[i], s, cudaEventRecordExternal)
+                                               : cudaEventRecord(p->ev[i], s);
+}
+
 // out = DFT_sign(in) for an any-size plan
 int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_t s) {
     AnyPlan &ap = *p->any;
-    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
     int rc = run_any_axis(ap.x, src, dst, sign, s);
     if (rc != FFT_OK) return rc;
-    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[1] && pass_event(p, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
     if (ap.y_cols) {
         if (launch_mixed(ap.y.ml, ap.y.mtw, dst, dst, p->batch, sign > 0 ? 1 : 0, s) != cudaSuccess)
             return FFT_ERR_CUDA;
@@ -752,7 +763,7 @@ int run_any(fft_plan_s *p, const float2 *src, float2 *dst, int sign, cudaStream_
         if (rc != FFT_OK) return rc;
         if (launch_transpose(ap.t, dst, p->nx, p->ny, batch, s) != cudaSuccess) return FFT_ERR_CUDA;
     }
-    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
 
@@ -769,17 +780,17 @@ int run_fourstep(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaSt
             return FFT_ERR_CUDA;
         fs.map_base = src;
     }
-    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
     if (launch_cols(*fs.a, fs.map, fs.work, fs.tw_a, fs.n2, p->batch, 1, 0, p->status, fs.grid_a, 0, s) !=
         cudaSuccess)
         return FFT_ERR_CUDA;
-    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[1] && pass_event(p, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
     if (fs.m > 1 && launch_fs_mid(fs.work, fs.lohi, fs.n1, fs.m, fs.n2 / fs.m, p->batch, s) != cudaSuccess)
         return FFT_ERR_CUDA;
     if (launch_rows_fourstep(*fs.b, fs.work, dst, fs.tw_b, fs.lohi, fs.n1, p->batch, inv ? 1 : 0, p->status, s,
                              fs.m) != cudaSuccess)
         return FFT_ERR_CUDA;
-    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
 
@@ -800,12 +811,12 @@ int run_columns(fft_plan_s *p, const float2 *src, float2 *dst, bool inv, cudaStr
             return FFT_ERR_CUDA;
         cp.map_base = src;
     }
-    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[1] && pass_event(p, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
     if (launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, 1, inv ? 3 : 0, p->status, cp.grid, p->col_pf, s) !=
         cudaSuccess)
         return FFT_ERR_CUDA;
-    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
 
@@ -837,7 +848,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     const long long nrows = total / p->rows.n;
     if (p->prec == FFT_PREC_SPLIT_FP16_TC) {
         if (weight) return FFT_ERR_UNSUPPORTED;
-        if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
         const bool land = p->rows.tc32 && tc32_land_used(p, nrows, P);
         // streaming tensor-core columns: out of place, rows from landed units
         // stored in the permuted order
@@ -851,7 +862,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                          : launch_rows_tc(p->rows.n, p->tcg, src, dst, p->rows.tw, p->twp, p->w16, nrows, p->ny, P,
                                           inv ? 1 : 0, (inv && !two_pass) ? 1 : 0, p->status, s);
         if (er != cudaSuccess) return FFT_ERR_CUDA;
-        if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[1] && pass_event(p, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
         if (two_pass) {
             if (cp.map_base != out) {
                 if (encode_col_map(&cp.map, out, p->nx, (long long)p->ny * p->batch, P, cp.tc_w,
@@ -868,7 +879,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                                          inv ? 1 : 0, p->status, cp.grid, s);
             if (ec != cudaSuccess) return FFT_ERR_CUDA;
         }
-        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
     // out of place: the row pass may store its rows permuted for the
@@ -882,7 +893,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         grid = p->ring ? ring_rows_grid(p->rows.n, nrows, P, p->num_sms, weight != nullptr)
                        : row_grid(*p->rows.row, nrows, p->num_sms, weight != nullptr, P,
                                   p->row_persist < 0 ? P > 1 : p->row_persist != 0);
-    if (p->ev[0] && cudaEventRecord(p->ev[0], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
     const bool land = P == 2 && !weight && !p->ring && p->sched.row_land &&
                       land_rows_available(p->rows.n, p->rows.row->e);
     const cudaError_t er =
@@ -896,9 +907,9 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                               stream ? cp.perm_t : 0,
                               stream ? cp.perm_g : 0, planar ? 1 : 0, s);
     if (er != cudaSuccess) return FFT_ERR_CUDA;
-    if (p->ev[1] && cudaEventRecord(p->ev[1], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[1] && pass_event(p, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
     if (!two_pass) {
-        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
     if (cp.cl_c > 0) {
@@ -912,13 +923,13 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
         if (launch_cols_cluster(cp.n, cp.cl_e, cp.cl_c, cp.map, dst, cp.tw, cp.roots, p->nx, p->batch, P, inv ? 1 : 0,
                                 p->status, s) != cudaSuccess)
             return FFT_ERR_CUDA;
-        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
     if (cp.pair_e > 0) {
         if (launch_cols_pair(cp.n, cp.pair_e, dst, cp.tw, cp.roots, p->nx, p->batch, P, inv ? 1 : 0, s) != cudaSuccess)
             return FFT_ERR_CUDA;
-        if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
         return FFT_OK;
     }
     if (stream && stream_tstore(*cp.stream) && cp.omap_base != out) {
@@ -938,7 +949,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
                : launch_cols(*cp.col, cp.map, dst, cp.tw, p->nx, p->batch, P, inv ? 1 : 0, p->status, cp.grid,
                              p->col_pf, s);
     if (ec != cudaSuccess) return FFT_ERR_CUDA;
-    if (p->ev[2] && cudaEventRecord(p->ev[2], s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
 

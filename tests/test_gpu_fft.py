@@ -347,3 +347,49 @@ def test_streaming_column_pass_is_bit_identical(g, monkeypatch, ny, nx, batch, i
         assert worst_rel_l2(a.cpu().numpy(), ref, nx * ny) <= tol_fp32(nx * ny)
     ps.close()
     pp.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(8192, 8192), (1024, 1024)])
+def test_pass_events_inside_a_captured_graph(g, nx, ny):
+    """Steps captured into a CUDA graph (as bench.py times them) give the same
+    result as eager calls, and their pass events, recorded as event-record
+    nodes, time-stamp every replay: both passes take positive time and add
+    up to no more than the whole replay."""
+    x = torch.from_numpy(synth.normal_complex((ny, nx), seed=41)).cuda()
+    plan = g.Plan(nx, ny, 1)
+    ref = plan.execute(x).clone()
+    out = torch.empty_like(x)
+    plan.execute(x, out=out)  # warm-up: tensor maps cached before capture
+    eager = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in eager:
+        e.record()  # torch reads elapsed times only of events it has seen recorded
+    plan.set_pass_events(*eager)  # outside capture: plain event records
+    plan.execute(x, out=out)
+    plan.set_pass_events(None, None, None)
+    torch.cuda.synchronize()
+    assert eager[0].elapsed_time(eager[1]) > 0 and eager[1].elapsed_time(eager[2]) > 0
+    steps = 3
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for trip in evs:
+        for e in trip:
+            e.record()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for k in range(steps):
+            plan.set_pass_events(*evs[k])
+            plan.execute(x, out=out)
+    plan.set_pass_events(None, None, None)
+    out.zero_()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(out, ref)
+    total = a.elapsed_time(b)
+    rows = [t[0].elapsed_time(t[1]) for t in evs]
+    cols = [t[1].elapsed_time(t[2]) for t in evs]
+    assert min(rows) > 0 and min(cols) > 0
+    assert sum(rows) + sum(cols) <= total * 1.001
