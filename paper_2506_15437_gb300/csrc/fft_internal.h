@@ -159,9 +159,9 @@ cudaError_t build_roots_strided(float2 *t, int count, long long n, long long str
 // Pre-split row pass from a landed pair of rows (fft_rows_land.cu): one CTA
 // per pair q, both output rows kp = 0, 1, stored like launch_rows stores them.
 bool land_rows_available(int n, int e);
-cudaError_t launch_rows_land(const float2 *in, float2 *out, const float2 *tw, const float2 *twp, int ny, int batch,
-                             int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms, int pf,
-                             cudaStream_t s);
+cudaError_t launch_rows_land(int e, const float2 *in, float2 *out, const float2 *tw, const float2 *twp, int ny,
+                             int batch, int conj_in, int perm_t, int perm_g, int planar, int *status, int num_sms,
+                             int pf, cudaStream_t s);
 
 // Streaming column pass (fft_cols_stream.cu) over a row-permuted
 // intermediate: the variant for column length n and row length nx, or

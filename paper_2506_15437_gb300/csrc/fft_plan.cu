@@ -897,7 +897,7 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
     const bool land = P == 2 && !weight && !p->ring && p->sched.row_land &&
                       land_rows_available(p->rows.n, p->rows.row->e);
     const cudaError_t er =
-        land ? launch_rows_land(src, row_dst, p->rows.tw, p->twp, p->ny, p->batch, inv ? 1 : 0,
+        land ? launch_rows_land(p->rows.row->e, src, row_dst, p->rows.tw, p->twp, p->ny, p->batch, inv ? 1 : 0,
                                 stream ? cp.perm_t : 0, stream ? cp.perm_g : 0, planar ? 1 : 0, p->status,
                                 p->num_sms, p->sched.land_pf, s)
         : p->ring ? launch_rows_ring(p->rows.n, src, dst, p->rows.tw, p->twp, nrows, p->ny, P, inv ? 1 : 0,
