@@ -10,18 +10,22 @@
 // has |xs| < 2048, and split as xs = hi + lo: hi keeps the top 11 significant
 // bits of xs (mask of the float32 mantissa, exact in float16), lo = xs - hi
 // (exact in float32, rounded once to float16).  Three products are kept,
-//     D1 = B_hi hi,   D2 = B_hi lo + B_lo hi,   y = (D1 + D2) * s / 2048,
-// accumulated in float32 in two TMEM accumulators (after Ootomo & Yokota's
-// error-corrected tensor-core GEMM; B_lo lo is below 2^-21 relative).
+// B_hi hi, B_hi lo and B_lo hi, accumulated in float32 (after Ootomo &
+// Yokota's error-corrected tensor-core GEMM; B_lo lo is below 2^-21
+// relative), the small corrections first.
 //
 // One 128-thread group holds 128 butterflies, one per thread and one per row
-// of A: the M = 128 x N = 64 x K = 64 product is 4 K-steps x 3 products =
-// 12 tcgen05.mma (kind::f16, f32 accumulate) issued by one thread and
-// committed to the group's mbarrier.  The A operand is staged in the same
-// shared memory the stage's exchange uses (its reads are complete by then),
-// so a row CTA needs only its exchange, the 16 KiB B and no extra staging.
-// A 8192-point transform is then radix 8 (float32) + two radix-32 tensor-core
-// stages; 4096 is 4 + 32 + 32, 2048 is 2 + 32 + 32, 1024 is 32 + 32.
+// of A.  Default (A in TMEM): each thread writes its row's hi / lo halves into
+// its TMEM lane, and B is the even/odd table -- two 32 x 32 diagonal blocks,
+// E_k = sum_m W16^(km) x_{2m} and O_k = sum_m W32^(k(2m+1)) x_{2m+1} -- so the
+// product is 12 tcgen05.mma of M = 128, N = 32, K = 16 (kind::f16, f32
+// accumulate) into one accumulator, issued by one thread and committed to
+// the group's mbarrier, and y_k = E_k + O_k, y_{k+16} = E_k - O_k are formed
+// in float32 on the way out of TMEM.  With A staged in shared memory (the
+// stage's exchange, whose reads are complete by then) the full table and two
+// accumulators are used instead.  A 8192-point transform is radix 8 (float32)
+// + two radix-32 tensor-core stages; 4096 is 4 + 32 + 32, 2048 is 2 + 32 +
+// 32, 1024 is 32 + 32.
 #include <mutex>
 
 #include "fft_internal.h"
