@@ -355,6 +355,30 @@ int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2);
  */
 int fft_debug_row_variant(int n, int e, int split, int *info);
 
+/*
+ * fft_debug_tc_layout -- compile-time layout of the split-FP16 tensor-core
+ * kernels (the radix-32 stages of Section 2.2's butterflies on tcgen05),
+ * written to the host array info[32] of long long:
+ *   kind 0, the landed pre-split row-pair kernel for rows of n points
+ *     (1024..8192): threads, threads per row T, output rows per unit L,
+ *     exchange float2 elements per row, buffer bytes, B-table offset,
+ *     barrier offset, dynamic shared-memory bytes, landing bytes per unit;
+ *   kind 1, the landed unsplit sub-unit kernel: threads, T, rows per CTA L,
+ *     exchange elements per row, rows per sub-unit RS, threads per sub-unit
+ *     U, sub-units K, row-span stride SPAN (float2), buffer bytes, B-table
+ *     offset, barrier offset, TMEM-slot offset, shared-memory bytes;
+ *   kind 2 (n = 4096), the streaming column kernel: n, tile width W, ring
+ *     slots S, threads, warps, MMA groups, butterflies per warp G, rows per
+ *     segment, float2 per segment, rows per TMA box, bytes per segment,
+ *     exchange float2 elements, ring offset, B-table offset, barrier offset,
+ *     TMEM-slot offset, shared-memory bytes, then each warp's landing span
+ *     offset in the exchange (float2).
+ * FFT_ERR_UNSUPPORTED for a length or kind not compiled, FFT_ERR_INVALID_ARG
+ * for a NULL info.  Host only: no device call (the tests check the spans,
+ * offsets and barrier ids on the CPU from these values).
+ */
+int fft_debug_tc_layout(int n, int kind, long long *info);
+
 /* cos(2 pi m / r) and sin(2 pi m / r) as the float constants the composite
  * mixed-radix DFTs use (evaluated at compile time from an integer quadrant
  * split and Taylor series in double, rounded once): written to *c and *s.

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("fft_debug_reorder_map", _I, [_I, _I, _P, _P]),
     ("fft_debug_radices", _I, [_I, _I, ctypes.POINTER(_I)]),
     ("fft_debug_row_variant", _I, [_I, _I, _I, ctypes.POINTER(_I)]),
+    ("fft_debug_tc_layout", _I, [_I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     ("fft_debug_mixed_plan", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("fft_debug_root", _I, [_I, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     ("fft_version", ctypes.c_char_p, []),

@@ -98,6 +98,7 @@ cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, c
 // column blocks, tiles of tc_stream_width() columns, E = 64 twiddles; the
 // row pass stores the permutation tc_stream_perm() gives.
 bool tc_stream_available(int n, int nx);
+int tc_stream_layout(long long *v);  // compile-time layout (host only)
 void tc_stream_perm(int *perm_t, int *perm_g);
 int tc_stream_width();
 int tc_stream_twiddle_e();
@@ -106,6 +107,7 @@ cudaError_t launch_cols_tc_stream(const CUtensorMap &map, float2 *out, const flo
 // Landed-row form (persistent, 512 threads, all TMEM columns of the SM):
 // rows per unit (0: not compiled), and whether a call is covered.
 int tc32_land_rows(int n);
+int tc32_land_layout(int n, int kind, long long *v);  // compile-time layout (host only)
 bool tc32_land_available(int n, long long nrows, int ny, int split);
 cudaError_t launch_rows_tc32_land(int n, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                                   const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,

@@ -1451,6 +1451,12 @@ int fft_debug_radices(int n, int axis, int *radices) {
     return schedule_radices(n, e, radices);
 }
 
+int fft_debug_tc_layout(int n, int kind, long long *info) {
+    if (!info) return FFT_ERR_INVALID_ARG;
+    if (kind == 2) return n == 4096 && gb300fft::tc_stream_layout(info) == 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
+    return gb300fft::tc32_land_layout(n, kind, info) == 0 ? FFT_OK : FFT_ERR_UNSUPPORTED;
+}
+
 int fft_debug_row_variant(int n, int e, int split, int *info) {
     if (!info) return FFT_ERR_INVALID_ARG;
     if (!is_pow2(n) || n < 2 || n > 8192) return FFT_ERR_INVALID_SIZE;

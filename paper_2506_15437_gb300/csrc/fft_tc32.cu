@@ -1012,6 +1012,35 @@ bool tc32_rows_available(int n) {
     return n >= 1024 && n <= 8192 && (n & (n - 1)) == 0 && g_t32_rows[ilog2(n)].fn[0][0] != nullptr;
 }
 
+// Compile-time layout of the landed tensor-core row kernels (host only):
+// kind 0, the pre-split pair form; kind 1, the unsplit sub-unit form.
+template <int N>
+static void land_layout(int kind, long long *v) {
+    if (kind == 0) {
+        using Sh = T32LandShape<N>;
+        const long long a[] = {Sh::THREADS, Sh::T, Sh::L, Sh::Eng::SMEM_ELEMS, (long long)Sh::BUF,
+                               (long long)Sh::B_OFF, (long long)Sh::BAR_OFF, (long long)Sh::SMEM, (long long)Sh::LAND_BYTES};
+        for (int i = 0; i < 9; ++i) v[i] = a[i];
+    } else {
+        using Sh = T32Land1Shape<N>;
+        const long long a[] = {Sh::THREADS, Sh::T,          Sh::L,           Sh::Eng::SMEM_ELEMS, Sh::RS,
+                               Sh::U,       Sh::K,          Sh::SPAN,        (long long)Sh::BUF,  (long long)Sh::B_OFF,
+                               (long long)Sh::BAR_OFF, (long long)Sh::SLOT_OFF, (long long)Sh::SMEM};
+        for (int i = 0; i < 13; ++i) v[i] = a[i];
+    }
+}
+
+int tc32_land_layout(int n, int kind, long long *v) {
+    if (kind != 0 && kind != 1) return -1;
+    switch (n) {
+        case 1024: land_layout<1024>(kind, v); return 0;
+        case 2048: land_layout<2048>(kind, v); return 0;
+        case 4096: land_layout<4096>(kind, v); return 0;
+        case 8192: land_layout<8192>(kind, v); return 0;
+        default: return -1;
+    }
+}
+
 // Widest compiled tile (at most 512 threads) that fits nx columns; 0 if none.
 int tc32_col_width(int n, int nx) {
     init_t32();

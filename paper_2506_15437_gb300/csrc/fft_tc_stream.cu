@@ -356,6 +356,18 @@ int tc_stream_width() { return kTcsW; }
 
 int tc_stream_twiddle_e() { return TcStreamShape<kTcsN, kTcsW, kTcsS>::E; }
 
+// Compile-time layout of the streaming tensor-core column kernel (host only).
+int tc_stream_layout(long long *v) {
+    using Sh = TcStreamShape<kTcsN, kTcsW, kTcsS>;
+    const long long a[] = {kTcsN,       kTcsW,          kTcsS,        Sh::THREADS,           Sh::WARPS,
+                           Sh::GROUPS,  Sh::G,          Sh::SEG_ROWS, Sh::SEG_ELEMS,         Sh::BOXR,
+                           Sh::SEG_BYTES, Sh::Eng::SMEM_ELEMS, (long long)Sh::RING_OFF, (long long)Sh::B_OFF,
+                           (long long)Sh::BAR_OFF, (long long)Sh::SLOT_OFF, (long long)Sh::SMEM};
+    for (int i = 0; i < 17; ++i) v[i] = a[i];
+    for (int w = 0; w < Sh::WARPS && w < 16; ++w) v[17 + w] = Sh::xch_seg(w);
+    return 0;
+}
+
 cudaError_t launch_cols_tc_stream(const CUtensorMap &map, float2 *out, const float2 *tw, const void *w32, int nx,
                                   int batch, int split, int conj_out, int *status, int num_sms, cudaStream_t s) {
     init_tcs();
