@@ -52,7 +52,9 @@ struct TcStreamShape {
     static_assert(WARPS * G == T, "one warp per G butterflies");
     static_assert(S >= 1 && S <= WARPS, "ring slots");
     static_assert(Eng::pad((WARPS - 1) * SEG_ELEMS) + SEG_ELEMS <= Eng::SMEM_ELEMS, "landing span");
-    static_assert(SMEM <= 232448, "dynamic shared memory of one CTA");
+    // the kernel's static shared memory (status words, the 1024-byte
+    // alignment of the dynamic buffer) takes 1 KiB of the CTA's 227 KiB
+    static_assert(SMEM + 1024 <= 232448, "shared memory of one CTA");
 };
 
 // Tensor-core state of one 128-thread group: its TMEM columns, its MMA

@@ -19,7 +19,7 @@ import ctypes
 import numpy as np
 import pytest
 
-SMEM_MAX = 232448  # dynamic shared memory of one CTA (227 KiB)
+SMEM_MAX = 232448 - 1024  # shared memory of one CTA (227 KiB) less 1 KiB static (status words, alignment)
 
 
 @pytest.fixture(scope="module")
