@@ -94,6 +94,13 @@ int tc32_cols_grid(int n, int w, long long ntiles, int num_sms);
 cudaError_t launch_rows_tc32(int n, int tmem_a, const float2 *in, float2 *out, const float2 *tw, const float2 *twp,
                              const void *w32, long long nrows, int ny, int split, int conj_in, int conj_out,
                              int *status, cudaStream_t s);
+// Small square 2D transforms in one cooperative launch (fft_small2d.cu):
+// n x n, n = 256..1024, at most 2^20 points, rows with E = 16 (the plan's row
+// twiddle table).
+bool small2d_available(int nx, int ny, int batch, int row_e);
+int small2d_grid(int n, int batch, int num_sms);  // 0 if it cannot launch
+cudaError_t launch_small2d(int n, const float2 *in, float2 *out, const float2 *tw, int batch, int conj,
+                           unsigned *bar, int *status, int grid, cudaStream_t s);
 // Streaming split-FP16 tensor-core column pass (fft_tc_stream.cu): 4096-point
 // column blocks, tiles of tc_stream_width() columns, E = 64 twiddles; the
 // row pass stores the permutation tc_stream_perm() gives.
@@ -409,6 +416,8 @@ struct fft_plan_s {
     int tc_radix = 32;      // split-FP16 plans: largest tensor-core radix allowed (32, or 16)
     int tc_tmem_a = 1;      // radix-32 tensor-core stages: A operand in tensor memory (0: shared memory)
     int tc_land = 1;        // radix-32 tensor-core rows from landed rows where the shape allows (A in TMEM)
+    int small_grid = 0;     // > 0: n x n FP32 plans of n <= 2048 run both passes in one cooperative launch
+    unsigned *small_bar = nullptr;  // its grid barrier (arrivals, generation)
     int tc_stream = 1;      // tensor-core columns of 4096 points: streaming radix-64 pass where allowed
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;

@@ -459,6 +459,18 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
                 if ((v == 1 || v == 2) && ny % v == 0 && ny / v >= 16) split = v;
             }
         }
+        // small square FP32 arrays: one cooperative launch for both passes
+        const char *esm = getenv("GB300FFT_SMALL2D");  // 0: separate row and column launches
+        if (rc == FFT_OK && precision == FFT_PREC_FP32 && !(esm && atoi(esm) == 0) && p->rows.row &&
+            small2d_available(nx, ny, batch, p->rows.row->e)) {
+            const int grid = small2d_grid(nx, batch, p->num_sms);
+            if (grid > 0) {
+                p->small_bar = dev_alloc<unsigned>(p, 2);
+                if (!p->small_bar) rc = FFT_ERR_ALLOC;
+                else if (cudaMemset(p->small_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) rc = FFT_ERR_CUDA;
+                else p->small_grid = grid;
+            }
+        }
         if (rc == FFT_OK && split > 1) {
             // TMA stores for the pre-split blocks only when asked for (2):
             // their output rows lie P apart and plain stores measured faster
@@ -880,6 +892,17 @@ int run_dense(fft_plan_s *p, const void *in, void *out, int sign, const float *w
             if (ec != cudaSuccess) return FFT_ERR_CUDA;
         }
         if (p->ev[2] && pass_event(p, 2, s) != cudaSuccess) return FFT_ERR_CUDA;
+        return FFT_OK;
+    }
+    // small square arrays: both passes in one cooperative launch (the pass
+    // events then time the whole transform as the row pass)
+    if (p->small_grid > 0 && !weight && two_pass && P == 1) {
+        if (p->ev[0] && pass_event(p, 0, s) != cudaSuccess) return FFT_ERR_CUDA;
+        if (launch_small2d(p->nx, src, dst, p->rows.tw, p->batch, inv ? 1 : 0, p->small_bar, p->status, p->small_grid,
+                           s) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        if (p->ev[1] && (pass_event(p, 1, s) != cudaSuccess || pass_event(p, 2, s) != cudaSuccess))
+            return FFT_ERR_CUDA;
         return FFT_OK;
     }
     // out of place: the row pass may store its rows permuted for the
@@ -1427,7 +1450,7 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      "{\"kind\": \"dense\", \"precision\": \"%s\", \"rows\": {\"kernel\": \"%s<%d,%d,split%d>\", "
                      "\"n\": %d, \"e\": %d, \"radices\": %s, \"persistent\": %d}, "
                      "\"cols\": {\"kernel\": \"%s<%d,%d,%d>\", \"n\": %d, \"e\": %d, \"w\": %d, \"radices\": %s, "
-                     "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d}",
+                     "\"grid\": %d}, \"split\": %d, \"col_tma_store\": %d, \"one_launch\": %d}",
                      tc ? "split_fp16_tc" : "fp32", tc ? (p->rows.tc32 ? (tc32_land_used(p, (long long)p->nx * p->ny * p->batch / p->rows.n, p->split) ? "k_rows_tc32_land" : "k_rows_tc32") : p->tcg ? "k_rows_tcgen05" : "k_rows_mmasync") : (p->ring ? "k_rows_ring" : (p->split == 2 && p->sched.row_land && p->rows.row && land_rows_available(p->rows.n, p->rows.row->e)) ? "k_rows_land" : "k_rows"), p->rows.n, re,
                      p->split, p->rows.n, re, r1, p->row_persist < 0 ? (p->split > 1) : p->row_persist,
                      !cp.col ? "none" : tc ? (tcs ? "k_cols_tc_stream" : cp.tc32 ? "k_cols_tc32" : cp.tcg ? "k_cols_tcgen05" : "k_cols_mmasync") : (cp.cl_c > 0 ? "k_cols_cluster" : cp.pair_e > 0 ? "k_cols_pair" : (cp.stream && !p->ring) ? "k_cols_stream" : "k_cols"), cp.n,
@@ -1435,7 +1458,8 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len) {
                      cp.cl_c > 0 ? cp.cl_c : cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0,
                      cp.n, cp.cl_c > 0 ? cp.cl_e : cp.pair_e > 0 ? cp.pair_e : cp.col ? (tc ? (tcs ? 64 : cp.tc32 ? 32 : 16) : cp.col->e) : 0,
                      cp.pair_e > 0 ? pair_cols_width(cp.n, cp.pair_e, p->nx) : cp.col ? (tc ? cp.tc_w : cp.col->w) : 0, r2,
-                     cp.grid, p->split, (!tc && cp.stream && !p->ring && stream_tstore(*cp.stream)) ? 1 : 0);
+                     cp.grid, p->split, (!tc && cp.stream && !p->ring && stream_tstore(*cp.stream)) ? 1 : 0,
+                     p->small_grid > 0 ? 1 : 0);
     }
     if (len > 0) {
         const int c = k < len - 1 ? k : len - 1;

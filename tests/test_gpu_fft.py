@@ -393,3 +393,42 @@ def test_pass_events_inside_a_captured_graph(g, nx, ny):
     cols = [t[1].elapsed_time(t[2]) for t in evs]
     assert min(rows) > 0 and min(cols) > 0
     assert sum(rows) + sum(cols) <= total * 1.001
+
+
+@pytest.mark.parametrize("n,batch", [(256, 1), (512, 1), (1024, 1), (512, 4), (256, 16)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_one_launch_small_arrays(g, monkeypatch, n, batch, inverse):
+    """Small square arrays run rows and columns in one cooperative launch
+    (grid barrier between the phases): against the oracle out of place and
+    in place, equal to the two-launch form within the bound, and again when
+    the calls are captured in a CUDA graph and replayed (the barrier resets
+    itself each launch)."""
+    plan = g.Plan(n, n, batch, inverse=inverse)
+    assert plan.describe()["one_launch"] == 1
+    monkeypatch.setenv("GB300FFT_SMALL2D", "0")
+    two = g.Plan(n, n, batch, inverse=inverse)
+    monkeypatch.delenv("GB300FFT_SMALL2D")
+    assert two.describe()["one_launch"] == 0
+    x = synth.uniform_complex((batch, n, n), seed=19 * n + batch)
+    ref = oracle.fft2d(x, dir=1 if inverse else -1, threads=ORACLE_THREADS)
+    d = torch.from_numpy(x).cuda()
+    a = plan.execute(d).cpu().numpy()
+    assert plan.status() == 0
+    assert worst_rel_l2(a, ref, n * n) <= tol_fp32(n * n)
+    assert worst_rel_l2(two.execute(d).cpu().numpy(), ref, n * n) <= tol_fp32(n * n)
+    dd = d.clone()
+    plan.execute(dd, out=dd)
+    assert np.array_equal(dd.cpu().numpy(), a)
+    out = torch.empty_like(d)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(3):
+            plan.execute(d, out=out)
+    for _ in range(2):
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), a)
+    assert plan.status() == 0
+    plan.close()
+    two.close()
