@@ -195,6 +195,10 @@ __device__ __forceinline__ int fdiv(int x, int d, uint32_t m) {
     return d == 1 ? x : (int)__umulhi((uint32_t)x, m);
 }
 
+// Twiddle-table entries per butterfly of a radix-R stage: R - 1 rounded up
+// to even, so each butterfly's row starts on a 16-byte boundary.
+__host__ __device__ constexpr int mixed_tw_stride(int R) { return (R - 1 + 1) & ~1; }
+
 struct StageArgs {
     int nb, Ns;  // butterflies per transform, product of the earlier radices
     uint32_t mag_nb, mag_ns;
@@ -247,9 +251,15 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
             }
         }
         if (!FIRST) {
-            const float2 *w = tws + k * (R - 1);
+            // twiddles r, r + 1 of butterfly k as one 16-byte load (rows of
+            // the table padded to an even count)
+            const float4 *w = reinterpret_cast<const float4 *>(tws + k * mixed_tw_stride(R));
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(w + r - 1));
+            for (int r = 1; r < R; r += 2) {
+                const float4 w2 = __ldg(w + (r - 1) / 2);
+                v[r] = cmul(v[r], make_float2(w2.x, w2.y));
+                if (r + 1 < R) v[r + 1] = cmul(v[r + 1], make_float2(w2.z, w2.w));
+            }
         }
         dft_any<R>(v);
         const int o0 = (j - k) * R + k;
@@ -354,12 +364,18 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
     }
 }
 
-// stage s's table: entry k (R - 1) + r - 1 = w_{Ns R}^{k r}, k < Ns, 1 <= r < R,
+// stage s's table: entry k M + r - 1 = w_{Ns R}^{k r}, k < Ns, 1 <= r < R,
+// M = mixed_tw_stride(R) (R - 1 rounded up to even; the pad entry is zero),
 // from the FP64 root, rounded once
 __global__ void k_mixed_twiddles(float2 *t, int Ns, int R) {
+    const int M = mixed_tw_stride(R);
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= Ns * (R - 1)) return;
-    const int k = e / (R - 1), r = e % (R - 1) + 1;
+    if (e >= Ns * M) return;
+    const int k = e / M, r = e % M + 1;
+    if (r >= R) {
+        t[e] = make_float2(0.f, 0.f);
+        return;
+    }
     const int L = Ns * R;
     double sv, cv;
     sincospi(2.0 * (double)((k * r) % L) / (double)L, &sv, &cv);
@@ -506,7 +522,7 @@ bool mixed_factor(int n, MixedStages *st) {
         m.tw_off[s] = off;
         m.ns[s] = Ns;
         m.nb[s] = n / m.radix[s];
-        off += Ns * (m.radix[s] - 1);
+        off += Ns * mixed_tw_stride(m.radix[s]);
         Ns *= m.radix[s];
     }
     m.tw_size = off;
@@ -517,7 +533,7 @@ bool mixed_factor(int n, MixedStages *st) {
 cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s) {
     int Ns = 1;
     for (int i = 0; i < st.S; ++i) {
-        const int R = st.radix[i], count = Ns * (R - 1);
+        const int R = st.radix[i], count = Ns * mixed_tw_stride(R);
         k_mixed_twiddles<<<(count + 255) / 256, 256, 0, s>>>(tw + st.tw_off[i], Ns, R);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
