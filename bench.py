@@ -509,6 +509,12 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(8192, 8192, 1)
         y = torch.empty_like(x)
         run = lambda: plan.execute(x, out=y)  # noqa: E731
+    elif name == "small_1024":
+        # one 1024 x 1024 array: rows and columns in one cooperative launch
+        x = torch.from_numpy(synth.normal_complex((1024, 1024), seed=SEED)).to(dev)
+        plan = g.Plan(1024, 1024, 1)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     elif name == "bluestein_1001":
         # 32768 signals of 1001 = 7 11 13 points: one-pass fused Bluestein over M = 2048
         x = torch.from_numpy(synth.uniform_complex((32768, 1001), seed=SEED)).to(dev)
@@ -567,7 +573,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="enqueue the timed steps one by one (no CUDA graph)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
-                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001",
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001", "small_1024",
                              "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
