@@ -509,6 +509,12 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(8192, 8192, 1)
         y = torch.empty_like(x)
         run = lambda: plan.execute(x, out=y)  # noqa: E731
+    elif name == "mixed_fourstep_1e6":
+        # 32 signals of 10^6 = 1000 x 1000 points: mixed-radix four-step (two passes)
+        x = torch.from_numpy(synth.uniform_complex((32, 1_000_000), seed=SEED)).to(dev)
+        plan = g.Plan(1_000_000, 1, 32)
+        y = torch.empty_like(x)
+        run = lambda: plan.execute(x, out=y)  # noqa: E731
     elif name == "small_1024":
         # one 1024 x 1024 array: rows and columns in one cooperative launch
         x = torch.from_numpy(synth.normal_complex((1024, 1024), seed=SEED)).to(dev)
@@ -574,6 +580,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
                     choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001", "small_1024",
+                             "mixed_fourstep_1e6",
                              "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()
