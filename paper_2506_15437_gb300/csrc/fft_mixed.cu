@@ -2,9 +2,11 @@
 //
 // The paper's kernels take powers of two only and name uneven sizes as
 // further work (Sections 6 and 7).  Smooth lengths up to kMixedMaxN run here
-// as a Stockham autosort transform whose stages have radix 16, 8, 4, 2, 15,
-// 9, 3, 5 or 7, chosen at plan time (15 and 9 are two-level DFTs in
-// registers with compile-time inner twiddles).  Stage s of radix R, with Ns
+// as a Stockham autosort transform whose stages have radix 16, 15, 14, 12,
+// 10, 9, 8, 7, 6, 5, 4, 3 or 2, chosen at plan time (15, 14, 12, 10, 9 and 6
+// are two-level DFTs in registers with compile-time inner twiddles): the
+// fewest stages these radices allow, since each stage is one pass through
+// shared memory and one barrier.  Stage s of radix R, with Ns
 // the product of the radices before it, takes butterfly j (k = j mod Ns)
 // from elements j + r n/R, multiplies leg r by w_{Ns R}^{k r}, runs an
 // R-point DFT and writes leg r to element (j - k) R + k + r Ns.  After the
@@ -176,7 +178,11 @@ __device__ __forceinline__ void dft_2lvl(float2 *a) {
 template <int R>
 __device__ __forceinline__ void dft_any(float2 *a) {
     if constexpr ((R & (R - 1)) == 0) dft<R>(a);
+    else if constexpr (R == 6) dft_2lvl<2, 3>(a);
     else if constexpr (R == 9) dft_2lvl<3, 3>(a);
+    else if constexpr (R == 10) dft_2lvl<2, 5>(a);
+    else if constexpr (R == 12) dft_2lvl<4, 3>(a);
+    else if constexpr (R == 14) dft_2lvl<2, 7>(a);
     else if constexpr (R == 15) dft_2lvl<3, 5>(a);
     else dft_odd<R>(a);
 }
@@ -288,9 +294,13 @@ __device__ __forceinline__ void mixed_dispatch(int R, const MixedGeom &g, const 
         case 3: mixed_stage<3, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 4: mixed_stage<4, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 5: mixed_stage<5, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 6: mixed_stage<6, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 7: mixed_stage<7, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 8: mixed_stage<8, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 9: mixed_stage<9, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 10: mixed_stage<10, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 12: mixed_stage<12, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 14: mixed_stage<14, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 15: mixed_stage<15, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         default: mixed_stage<16, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
     }
@@ -482,6 +492,24 @@ MixedStages with_group(const MixedStages &st, int W, bool cols, int T) {
     return m;
 }
 
+// the compiled radices, largest first
+constexpr int kMixedRadices[] = {16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+
+// rest as a product of exactly `left` compiled radices, none larger than
+// `cap` (non-increasing, so each multiset is tried once), into out[]
+bool factor_exact(int rest, int left, int cap, int *out) {
+    if (left == 0) return rest == 1;
+    long long reach = 1;
+    for (int i = 0; i < left; ++i) reach *= cap;
+    if (reach < rest) return false;
+    for (int R : kMixedRadices) {
+        if (R > cap || rest % R) continue;
+        out[0] = R;
+        if (factor_exact(rest / R, left - 1, R, out + 1)) return true;
+    }
+    return false;
+}
+
 }  // namespace
 
 bool mixed_factor(int n, MixedStages *st) {
@@ -495,8 +523,8 @@ bool mixed_factor(int n, MixedStages *st) {
         rest /= R;
         return true;
     };
-    // powers of two: 16s, then one 8, 4 or 2; odd part: 3 * 5 and 3 * 3 in
-    // one register stage each, then single 3, 5, 7 (a 25-point stage needs
+    // greedy: powers of two: 16s, then one 8, 4 or 2; odd part: 3 * 5 and 3 * 3
+    // in one register stage each, then single 3, 5, 7 (a 25-point stage needs
     // twice the registers of a 16-point one and halves the CTAs per SM:
     // measured slower than two 5-point stages)
     int e3 = 0, e5 = 0;
@@ -516,6 +544,18 @@ bool mixed_factor(int n, MixedStages *st) {
     while (rest % 7 == 0)
         if (!push(7)) return false;
     if (rest != 1) return false;
+    // the greedy schedule above is kept where no schedule has fewer stages
+    // (e.g. 3000 = 8 15 5 5); otherwise the first of the fewest, radices
+    // non-increasing (1000 = 10 10 10 in place of 8 5 5 5, 1728 = 16 12 9 in
+    // place of 16 4 9 3, 96 = 16 6 in place of 16 2 3)
+    for (int d = 1; d < S; ++d) {
+        int r[kMixedMaxStages];
+        if (factor_exact(n, d, 16, r)) {
+            for (int i = 0; i < d; ++i) m.radix[i] = r[i];
+            S = d;
+            break;
+        }
+    }
     m.S = S;
     int off = 0, Ns = 1;
     for (int s = 0; s < S; ++s) {
@@ -579,6 +619,14 @@ int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, in
     }
     if (cols && (nx <= 0 || nx % L.W)) return -1;
     L.T = mixed_threads(L.W * st.n);
+    // no more threads than the widest stage has butterflies: for short
+    // transforms the idle ones would hold registers and block slots (measured
+    // 100 x 100 x 2048: 0.259 -> 0.154 ms).  More threads than the default,
+    // to run a stage in one round, measured slower where they cost resident
+    // blocks (96-point rows 0.152 -> 0.194 ms, 1920 x 1080 x 8: 0.183 -> 0.197)
+    int most = 0;
+    for (int s = 0; s < st.S; ++s) most = L.W * st.nb[s] > most ? L.W * st.nb[s] : most;
+    if (((most + 31) & ~31) < L.T) L.T = (most + 31) & ~31;
     L.m = with_group(st, L.W, cols, L.T);
     if (fs && L.m.buf_elems < L.W * L.fs.stride) L.m.buf_elems = L.W * L.fs.stride;
     L.smem = (size_t)2 * L.m.buf_elems * sizeof(float2);

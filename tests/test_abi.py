@@ -121,13 +121,29 @@ def _smooth7(n):
     return n == 1
 
 
+MIXED_RADICES = {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16}
+
+
+def _fewest_stages(limit):
+    """fewest[m]: the fewest factors from MIXED_RADICES whose product is m
+    (dynamic programming over m; None where m has another prime factor)."""
+    fewest = [None] * (limit + 1)
+    fewest[1] = 0
+    for m in range(2, limit + 1):
+        c = [fewest[m // r] for r in MIXED_RADICES if m % r == 0 and fewest[m // r] is not None]
+        fewest[m] = 1 + min(c) if c else None
+    return fewest
+
+
 def test_mixed_radix_schedules(lib):
     """Host-side mixed-radix planning, without a GPU: every length up to
-    3000 and the longest one-CTA length factor into the compiled radices
-    (16s, then one of 8/4/2, then 15s/9s, single 3/5/7) whose product is n;
+    3000 and the longest one-CTA lengths factor into the compiled radices
+    with product n and no more stages than the fewest possible (found here
+    by brute force); the greedy schedules of the tuned lengths are kept;
     other lengths are refused."""
     buf = (ctypes.c_int * 16)()
     n1, n2 = ctypes.c_int(), ctypes.c_int()
+    fewest = _fewest_stages(14336)
     for n in list(range(2, 3001)) + [14336, 14335, 12288, 10000]:
         k = lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2))
         if not _smooth7(n):
@@ -136,10 +152,13 @@ def test_mixed_radix_schedules(lib):
         assert 1 <= k <= 16 and n1.value == 0 and n2.value == 0, n
         rad = [buf[i] for i in range(k)]
         assert int(np.prod(rad)) == n, (n, rad)
-        assert set(rad) <= {2, 3, 4, 5, 7, 8, 9, 15, 16}, (n, rad)
-        pow2 = [r for r in rad if r in (2, 4, 8, 16)]
-        assert pow2 == rad[:len(pow2)] and sum(r != 16 for r in pow2) <= 1, (n, rad)  # 16s, then one of 8/4/2
-        assert not (3 in rad and 5 in rad) and rad.count(3) <= 1, (n, rad)  # 3 x 5 -> 15, 3 x 3 -> 9
+        assert set(rad) <= MIXED_RADICES, (n, rad)
+        assert k == fewest[n], (n, rad, fewest[n])
+    expect = {3000: [8, 15, 5, 5], 1080: [8, 15, 9], 1920: [16, 8, 15], 14336: [16, 16, 8, 7],
+              1000: [10, 10, 10], 10000: [10, 10, 10, 10], 96: [16, 6], 1728: [16, 12, 9], 210: [15, 14]}
+    for n, rad in expect.items():
+        k = lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2))
+        assert [buf[i] for i in range(k)] == rad, n
 
 
 def test_mixed_fourstep_splits(lib):

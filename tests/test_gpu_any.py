@@ -186,10 +186,11 @@ def test_describe_and_unsupported(g):
 
 
 # Mixed-radix lengths: every radix alone and in combination (16, 8, 4, 2,
-# the two-level 15 and 9, the single 3, 5, 7), prime powers, the longest
-# length, and short rows packed several to a CTA.
-MIXED_1D = [3, 5, 6, 7, 9, 10, 14, 15, 21, 24, 25, 35, 45, 49, 60, 96, 105, 120, 135, 210, 225, 343, 360, 405,
-            625, 1080, 1125, 1920, 2025, 2187, 3125, 3375, 6000, 7168, 10000, 12288, 14336]
+# the two-level 15, 14, 12, 10, 9 and 6, the single 3, 5, 7), prime powers,
+# the longest length, and short rows packed several to a CTA.
+MIXED_1D = [3, 5, 6, 7, 9, 10, 12, 14, 15, 21, 24, 25, 35, 45, 49, 60, 96, 100, 105, 120, 135, 196, 210, 225, 343,
+            360, 405, 625, 1000, 1080, 1125, 1728, 1920, 2025, 2187, 2744, 3125, 3375, 6000, 7168, 10000, 12288,
+            14336]
 
 
 @pytest.mark.parametrize("n", MIXED_1D)
