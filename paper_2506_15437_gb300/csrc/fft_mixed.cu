@@ -239,6 +239,17 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
         }
         const int k = j - fdiv(j, Ns, a.mag_ns) * Ns;
         float2 v[R];
+        // four-step: element i2 = j + r nb of row m = k1 + c times w_n^{i2 m}
+        // = w_n^{j m} w_n^{r nb m}, each from the two factor tables w_n^a =
+        // hi[a >> L] lo[a & (2^L - 1)].  The first factor is one gather per
+        // thread; the second is the same for every lane of a row, so its
+        // loads are broadcasts (one gather per element, lanes m entries
+        // apart, cost a cache line each)
+        float2 wj = make_float2(1.f, 0.f);
+        if (FIRST && FS) {
+            const int e = j * (fs.k1 + c);
+            wj = cmul(__ldg(fs.hi + (e >> fs.lshift)), __ldg(fs.lo + (e & fs.lmask)));
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = j + r * nb;
@@ -246,10 +257,12 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
                 float2 x = gin[c * g.tstride + i * g.estride];
                 x.y *= si;
                 if (FS) {
-                    // four-step: element i2 = i of row k1 times w_n^{i2 k1}, from
-                    // the two factor tables w_n^a = hi[a >> L] lo[a & (2^L - 1)]
-                    const int e = i * (fs.k1 + c);
-                    x = cmul(x, cmul(__ldg(fs.hi + (e >> fs.lshift)), __ldg(fs.lo + (e & fs.lmask))));
+                    float2 w = wj;
+                    if (r > 0) {
+                        const int e = r * nb * (fs.k1 + c);
+                        w = cmul(w, cmul(__ldg(fs.hi + (e >> fs.lshift)), __ldg(fs.lo + (e & fs.lmask))));
+                    }
+                    x = cmul(x, w);
                 }
                 v[r] = x;
             } else {
@@ -604,16 +617,21 @@ int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, in
     L.nx = cols ? nx : 0;
     const bool fs = !cols && fs_n1 > 0;
     if (fs) {
-        // W rows of one transform per CTA (W divides n1), staged with an odd
-        // row stride so the transposed reads spread over the banks
+        // W rows of one transform per CTA (W divides n1), staged with a row
+        // stride of 16 / W mod 16 words: a half-warp of the transposed store
+        // reads 16 / W outputs of each of the W rows, which then fall on 16
+        // distinct 8-byte bank pairs
         L.fs.n1 = fs_n1;
-        L.fs.stride = st.n | 1;
+        L.fs.stride = st.n;
         L.W = 1;
-        for (int W : {8, 4, 2})
-            if (fs_n1 % W == 0 && (size_t)2 * W * L.fs.stride * sizeof(float2) <= 72 * 1024) {
+        for (int W : {8, 4, 2}) {
+            const int stride = st.n + ((16 / W - st.n % 16) % 16 + 16) % 16;
+            if (fs_n1 % W == 0 && (size_t)2 * W * stride * sizeof(float2) <= 72 * 1024) {
                 L.W = W;
+                L.fs.stride = stride;
                 break;
             }
+        }
     } else {
         L.W = cols ? mixed_cols_width(st.n, nx) : mixed_rows_per_cta(st.n);
     }
