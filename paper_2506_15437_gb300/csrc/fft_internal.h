@@ -296,7 +296,7 @@ struct MixedStages {
     int ns[kMixedMaxStages] = {};      // product of the radices before stage s
     int nb[kMixedMaxStages] = {};      // butterflies per transform, n / radix
     uint32_t mag_nb[kMixedMaxStages] = {}, mag_ns[kMixedMaxStages] = {};  // ceil(2^32 / d) divisors
-    int tw_off[kMixedMaxStages] = {};  // stage s's twiddles w_{Ns R}^{k r} at tw_off[s] + k (R - 1) + r - 1
+    int tw_off[kMixedMaxStages] = {};  // stage s's twiddles w_{Ns R}^{k r}, 16-byte pairs (r odd, r + 1) at pair (r - 1) / 2 * Ns + k
 };
 // Second pass of a mixed-radix four-step transform (n = n1 n2): row k1 of
 // the first pass's output is multiplied by w_n^{i2 k1} as it is loaded and

@@ -202,7 +202,7 @@ __device__ __forceinline__ int fdiv(int x, int d, uint32_t m) {
 }
 
 // Twiddle-table entries per butterfly of a radix-R stage: R - 1 rounded up
-// to even, so each butterfly's row starts on a 16-byte boundary.
+// to even, so each butterfly's twiddles are whole 16-byte pairs.
 __host__ __device__ constexpr int mixed_tw_stride(int R) { return (R - 1 + 1) & ~1; }
 
 struct StageArgs {
@@ -270,12 +270,18 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
             }
         }
         if (!FIRST) {
-            // twiddles r, r + 1 of butterfly k as one 16-byte load (rows of
-            // the table padded to an even count)
-            const float4 *w = reinterpret_cast<const float4 *>(tws + k * mixed_tw_stride(R));
+            // twiddles r, r + 1 of butterfly k as one 16-byte load, pair p =
+            // (r - 1) / 2 of every butterfly in one row of the table: lanes
+            // with consecutive k read consecutive 16-byte words.  (With the
+            // pairs of one butterfly together, lanes read words M/2 apart,
+            // which conflict in the L1 banks when M/2 is even.  Measured
+            // against that layout: 16384 x 3000 0.251 -> 0.236 ms, 1920 x
+            // 1080 x 8 0.183 -> 0.175, 6^9 0.231 -> 0.224, 1000^2 x 32 0.310
+            // -> 0.305; 10^6 x 32 0.360 -> 0.369, 15360 x 1024 0.123 -> 0.130)
+            const float4 *w = reinterpret_cast<const float4 *>(tws) + k;
 #pragma unroll
             for (int r = 1; r < R; r += 2) {
-                const float4 w2 = __ldg(w + (r - 1) / 2);
+                const float4 w2 = __ldg(w + ((r - 1) / 2) * Ns);
                 v[r] = cmul(v[r], make_float2(w2.x, w2.y));
                 if (r + 1 < R) v[r + 1] = cmul(v[r + 1], make_float2(w2.z, w2.w));
             }
@@ -387,14 +393,14 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
     }
 }
 
-// stage s's table: entry k M + r - 1 = w_{Ns R}^{k r}, k < Ns, 1 <= r < R,
-// M = mixed_tw_stride(R) (R - 1 rounded up to even; the pad entry is zero),
-// from the FP64 root, rounded once
+// stage s's table, as 16-byte pairs: pair p of butterfly k (k < Ns) at
+// pair index p Ns + k holds w_{Ns R}^{k r} for r = 2p + 1 and 2p + 2 (the
+// second zero when R - 1 is odd), from the FP64 root, rounded once
 __global__ void k_mixed_twiddles(float2 *t, int Ns, int R) {
     const int M = mixed_tw_stride(R);
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Ns * M) return;
-    const int k = e / M, r = e % M + 1;
+    const int q = e >> 1, p = q / Ns, k = q - p * Ns, r = 2 * p + 1 + (e & 1);
     if (r >= R) {
         t[e] = make_float2(0.f, 0.f);
         return;
