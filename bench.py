@@ -360,18 +360,20 @@ def energy_form(torch, g, dev):
 
 
 def any_size_form(torch, g, steps, dev):
-    """Sizes that are not powers of two.  7-smooth lengths take the
+    """Sizes that are not powers of two.  13-smooth lengths take the
     mixed-radix kernel (one HBM pass per axis: 1000 x 1000 beside the
-    paper's 1024 x 1024, 1920 x 1080, 16384 signals of 3000 points), or,
-    longer than one CTA holds, its four-step form (two passes: 32 signals
-    of 10^6 points); other lengths Bluestein over the power-of-two path
-    (16384 signals of 4095 = 3^2 5 7 13 points).  GFLOP/s uses the nominal
-    5 N log2 N of the transform's own size; the HBM figure counts one read
-    and one write per axis or pass."""
+    paper's 1024 x 1024, 1920 x 1080, 16384 signals of 3000 points, 16384
+    signals of 4095 = 3^2 5 7 13 points), or, longer than one CTA holds, its
+    four-step form (two passes: 32 signals of 10^6 points); other lengths
+    Bluestein over the power-of-two path (16384 signals of the prime 4093,
+    padded to M = 8192).  GFLOP/s uses the nominal 5 N log2 N of the
+    transform's own size; the HBM figure counts one read and one write per
+    axis or pass."""
     import math
     import synth
     out = {}
-    for nx, ny, b in ((1000, 1000, 1), (1920, 1080, 1), (3000, 1, 16384), (1_000_000, 1, 32), (4095, 1, 16384)):
+    for nx, ny, b in ((1000, 1000, 1), (1920, 1080, 1), (3000, 1, 16384), (1_000_000, 1, 32), (4095, 1, 16384),
+                      (4093, 1, 16384)):
         x = torch.from_numpy(synth.uniform_complex((b, ny, nx), seed=SEED)).to(dev)
         y = torch.empty_like(x)
         plan = g.get_plan(nx, ny, b, False, "fp32", dev)
@@ -521,14 +523,21 @@ def profile_form(torch, name, steps, warmup, dev):
         plan = g.Plan(1024, 1024, 1)
         y = torch.empty_like(x)
         run = lambda: plan.execute(x, out=y)  # noqa: E731
-    elif name == "bluestein_1001":
-        # 32768 signals of 1001 = 7 11 13 points: one-pass fused Bluestein over M = 2048
-        x = torch.from_numpy(synth.uniform_complex((32768, 1001), seed=SEED)).to(dev)
-        plan = g.Plan(1001, 1, 32768)
+    elif name in ("bluestein_1001", "bluestein_4095"):
+        # 32768 signals of 1001 = 7 11 13 points (one-pass fused Bluestein
+        # over M = 2048) or 8192 signals of 4095 = 3^2 5 7 13 (fused, two
+        # passes over M = 8192), planned with the mixed-radix kernel
+        # switched off: both lengths are 13-smooth, so by default they run
+        # mixed radix
+        n, b = (1001, 32768) if name == "bluestein_1001" else (4095, 8192)
+        x = torch.from_numpy(synth.uniform_complex((b, n), seed=SEED)).to(dev)
+        os.environ["GB300FFT_MIXED"] = "0"
+        plan = g.Plan(n, 1, b)
+        del os.environ["GB300FFT_MIXED"]
         y = torch.empty_like(x)
         run = lambda: plan.execute(x, out=y)  # noqa: E731
-    elif name == "bluestein_4095":
-        # 8192 signals of 4095 = 3^2 5 7 13 points: fused Bluestein over M = 8192
+    elif name == "mixed_4095":
+        # 8192 signals of 4095 = 3^2 5 7 13 points: mixed radix 15, 3, 7, 13
         x = torch.from_numpy(synth.uniform_complex((8192, 4095), seed=SEED)).to(dev)
         plan = g.Plan(4095, 1, 8192)
         y = torch.empty_like(x)
@@ -580,7 +589,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
                     choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001", "small_1024",
-                             "mixed_fourstep_1e6",
+                             "mixed_fourstep_1e6", "mixed_4095",
                              "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")
     args = ap.parse_args()

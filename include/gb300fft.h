@@ -82,8 +82,9 @@ enum {
  *              twiddles, so no pass works on a length-8192 axis).  Every
  *              other shape is planned axis
  *              by axis (the paper's uneven sizes, Sections 6 and 7):
- *              lengths 2^a 3^b 5^c 7^d up to 14336 by mixed-radix stages
- *              (radices 16, 8, 4, 2, 15, 9, 3, 5, 7) in one pass, longer such
+ *              lengths 2^a 3^b 5^c 7^d 11^e 13^f up to 14336 by mixed-radix
+ *              stages (every radix from 2 to 16, the fewest stages) in
+ *              one pass, longer such
  *              lengths by a mixed-radix four-step, powers of two by the
  *              dense path, any other length by Bluestein's algorithm over a
  *              power-of-two length M >= 2n - 1; the y axis of a 2D plan runs
@@ -332,11 +333,11 @@ int fft_plan_describe(fft_plan_t p, char *buf, int len);
 int fft_debug_radices(int n, int axis, int *radices);
 
 /* The mixed-radix schedule of length n (2 <= n <= 2^24; Sections 6-7's
- * uneven sizes): for n = 2^a 3^b 5^c 7^d <= 14336 the stage radices of the
+ * uneven sizes): for n = 2^a 3^b 5^c 7^d 11^e 13^f <= 14336 the stage radices of the
  * one-CTA kernel, first stage first, written to `radices` (capacity 16) and
  * their count returned, *n1 = *n2 = 0; for longer such n, 0 returned and the
  * four-step split n = n1 * n2 written (columns of length n1, then rows of
- * length n2); FFT_ERR_INVALID_SIZE when n has a prime factor above 7 or is
+ * length n2); FFT_ERR_INVALID_SIZE when n has a prime factor above 13 or is
  * out of range, FFT_ERR_INVALID_ARG for NULL pointers.  Host only: no
  * device call. */
 int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2);

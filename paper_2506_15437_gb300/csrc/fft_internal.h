@@ -283,7 +283,7 @@ const BluVariant *blu_variant(int M);
 cudaError_t launch_blu(const BluVariant &v, int phase, const float2 *src, float2 *dst, const float2 *tw,
                        const float2 *chirp, const float2 *H, int n, long long rows, cudaStream_t s);
 
-// Mixed-radix stages of a 7-smooth length n <= kMixedMaxN (fft_mixed.cu).
+// Mixed-radix stages of a 13-smooth length n <= kMixedMaxN (fft_mixed.cu).
 constexpr int kMixedMaxN = 14336;           // two float2 buffers of n in one CTA's shared memory
 constexpr size_t kMixedMaxSmem = 227 * 1024;
 constexpr int kMixedMaxStages = 16;
@@ -319,7 +319,7 @@ struct MixedLaunch {
     size_t smem = 0;
     FourStepB fs;
 };
-bool mixed_factor(int n, MixedStages *st);  // false unless n = 2^a 3^b 5^c 7^d <= kMixedMaxN
+bool mixed_factor(int n, MixedStages *st);  // false unless n = 2^a 3^b 5^c 7^d 11^e 13^f <= kMixedMaxN
 cudaError_t build_mixed_twiddles(float2 *tw, const MixedStages &st, cudaStream_t s);
 int mixed_rows_per_cta(int n);
 int mixed_cols_width(int n, int nx);
@@ -334,10 +334,10 @@ cudaError_t launch_mixed(const MixedLaunch &L, const float2 *tw, const float2 *i
                          int conj, cudaStream_t s);
 
 struct AnyAxis {
-    bool mixed = false;                 // 7-smooth n: the mixed-radix kernel, no padding
+    bool mixed = false;                 // 13-smooth n: the mixed-radix kernel, no padding
     MixedStages mst;
     MixedLaunch ml;                     // rows, or (the y axis of a 2D plan) columns
-    bool mfs = false;                   // 7-smooth n > kMixedMaxN: mixed-radix four-step
+    bool mfs = false;                   // 13-smooth n > kMixedMaxN: mixed-radix four-step
     int n1 = 0, n2 = 0;                 // n = n1 n2: columns of length n1, then rows of n2
     MixedLaunch mla, mlb;               // the two passes
     float2 *mtwa = nullptr, *mtwb = nullptr, *fs_hi = nullptr, *fs_lo = nullptr, *fs_work = nullptr;

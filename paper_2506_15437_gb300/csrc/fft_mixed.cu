@@ -1,10 +1,11 @@
-// Mixed-radix transforms for lengths of the form 2^a 3^b 5^c 7^d.
+// Mixed-radix transforms for lengths of the form 2^a 3^b 5^c 7^d 11^e 13^f.
 //
 // The paper's kernels take powers of two only and name uneven sizes as
 // further work (Sections 6 and 7).  Smooth lengths up to kMixedMaxN run here
-// as a Stockham autosort transform whose stages have radix 16, 15, 14, 12,
-// 10, 9, 8, 7, 6, 5, 4, 3 or 2, chosen at plan time (15, 14, 12, 10, 9 and 6
-// are two-level DFTs in registers with compile-time inner twiddles): the
+// as a Stockham autosort transform whose stages have radix 16, 15, 14, 13,
+// 12, 11, 10, 9, 8, 7, 6, 5, 4, 3 or 2, chosen at plan time (15, 14, 12, 10,
+// 9 and 6 are two-level DFTs in registers with compile-time inner twiddles;
+// the odd primes 3 .. 13 one symmetric-pair DFT each): the
 // fewest stages these radices allow, since each stage is one pass through
 // shared memory and one barrier.  Stage s of radix R, with Ns
 // the product of the radices before it, takes butterfly j (k = j mod Ns)
@@ -318,7 +319,9 @@ __device__ __forceinline__ void mixed_dispatch(int R, const MixedGeom &g, const 
         case 8: mixed_stage<8, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 9: mixed_stage<9, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 10: mixed_stage<10, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 11: mixed_stage<11, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 12: mixed_stage<12, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
+        case 13: mixed_stage<13, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 14: mixed_stage<14, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         case 15: mixed_stage<15, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
         default: mixed_stage<16, COLS, FIRST, LAST, FS>(g, a, src, dst, gin, gout, tws, si, fs); break;
@@ -512,7 +515,7 @@ MixedStages with_group(const MixedStages &st, int W, bool cols, int T) {
 }
 
 // the compiled radices, largest first
-constexpr int kMixedRadices[] = {16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+constexpr int kMixedRadices[] = {16, 15, 14, 13, 12, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2};
 
 // rest as a product of exactly `left` compiled radices, none larger than
 // `cap` (non-increasing, so each multiset is tried once), into out[]
@@ -543,7 +546,7 @@ bool mixed_factor(int n, MixedStages *st) {
         return true;
     };
     // greedy: powers of two: 16s, then one 8, 4 or 2; odd part: 3 * 5 and 3 * 3
-    // in one register stage each, then single 3, 5, 7 (a 25-point stage needs
+    // in one register stage each, then single 3, 5, 7, 11, 13 (a 25-point stage needs
     // twice the registers of a 16-point one and halves the CTAs per SM:
     // measured slower than two 5-point stages)
     int e3 = 0, e5 = 0;
@@ -560,8 +563,9 @@ bool mixed_factor(int n, MixedStages *st) {
     if (e3 == 1 && !push(3)) return false;
     for (; e5 >= 1; --e5)
         if (!push(5)) return false;
-    while (rest % 7 == 0)
-        if (!push(7)) return false;
+    for (int R : {7, 11, 13})
+        while (rest % R == 0)
+            if (!push(R)) return false;
     if (rest != 1) return false;
     // the greedy schedule above is kept where no schedule has fewer stages
     // (e.g. 3000 = 8 15 5 5); otherwise the first of the fewest, radices

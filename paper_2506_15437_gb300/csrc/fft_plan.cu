@@ -526,7 +526,7 @@ bool use_mixed(int n, MixedStages *st) {
     return !is_pow2(n) && mixed_factor(n, st);
 }
 
-// a 7-smooth length beyond one CTA that splits into two mixed-radix lengths,
+// a 13-smooth length beyond one CTA that splits into two mixed-radix lengths,
 // unless GB300FFT_MIXED=0
 bool use_mixed_fourstep(int n, int *n1, int *n2) {
     const char *ev = getenv("GB300FFT_MIXED");
@@ -535,7 +535,7 @@ bool use_mixed_fourstep(int n, int *n1, int *n2) {
 }
 
 // One axis of an any-size plan: rows transforms of length n.  A power of two
-// gets a dense sub-plan of its own; a 7-smooth n up to kMixedMaxN the
+// gets a dense sub-plan of its own; a 13-smooth n up to kMixedMaxN the
 // mixed-radix kernel; any other n Bluestein over a length-M power-of-two
 // sub-plan, M >= 2n - 1, with the chirps and the filter transforms built here.
 int setup_any_axis(fft_plan_s *p, AnyAxis &ax, int n, long long rows, int cols_nx = 0) {

@@ -59,10 +59,10 @@ MIXED_MAX_N = 14336  # longest mixed-radix length (two float2 buffers in one CTA
 
 
 def odd_factors(n: int) -> int:
-    """Number of prime factors 3, 5, 7 of n (with multiplicity) if n is
-    7-smooth, else -1."""
+    """Number of prime factors 3, 5, 7, 11, 13 of n (with multiplicity) if n
+    is 13-smooth, else -1."""
     k = 0
-    for p in (3, 5, 7):
+    for p in (3, 5, 7, 11, 13):
         while n % p == 0:
             n //= p
             k += 1
@@ -72,7 +72,7 @@ def odd_factors(n: int) -> int:
 
 
 def mixed_eligible(n: int) -> bool:
-    """Lengths the mixed-radix kernel takes: 7-smooth, not a power of two,
+    """Lengths the mixed-radix kernel takes: 13-smooth, not a power of two,
     at most MIXED_MAX_N."""
     return n & (n - 1) != 0 and n <= MIXED_MAX_N and odd_factors(n) >= 0
 
@@ -91,7 +91,7 @@ def tol_mixed_axis(n: int) -> float:
 
 
 def mixed_fourstep_eligible(n: int) -> bool:
-    """Longer 7-smooth lengths (not powers of two): two mixed-radix passes
+    """Longer 13-smooth lengths (not powers of two): two mixed-radix passes
     of a four-step split (every such length up to 2^24 has a divisor
     between n / MIXED_MAX_N and MIXED_MAX_N)."""
     return n & (n - 1) != 0 and MIXED_MAX_N < n <= (1 << 24) and odd_factors(n) >= 0
@@ -99,7 +99,7 @@ def mixed_fourstep_eligible(n: int) -> bool:
 
 def tol_any_axis(n: int, mixed: bool = True) -> float:
     """FP32 bound for one axis of any length: a power of two is the plain
-    path (2e-7 * log2 n); a 7-smooth length up to MIXED_MAX_N the mixed-radix
+    path (2e-7 * log2 n); a 13-smooth length up to MIXED_MAX_N the mixed-radix
     kernel and a longer one its four-step form, both held to the same
     2e-7 * log2 n, unless `mixed` is False (the plan was made with it switched
     off); any other length Bluestein."""

@@ -114,14 +114,14 @@ def test_stage_schedules(lib, axis):
     assert lib.fft_debug_radices(12, axis, buf) < 0
 
 
-def _smooth7(n):
-    for p in (2, 3, 5, 7):
+def _smooth13(n):
+    for p in (2, 3, 5, 7, 11, 13):
         while n % p == 0:
             n //= p
     return n == 1
 
 
-MIXED_RADICES = {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16}
+MIXED_RADICES = set(range(2, 17))
 
 
 def _fewest_stages(limit):
@@ -146,7 +146,7 @@ def test_mixed_radix_schedules(lib):
     fewest = _fewest_stages(14336)
     for n in list(range(2, 3001)) + [14336, 14335, 12288, 10000]:
         k = lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2))
-        if not _smooth7(n):
+        if not _smooth13(n):
             assert k == -1, n
             continue
         assert 1 <= k <= 16 and n1.value == 0 and n2.value == 0, n
@@ -155,7 +155,8 @@ def test_mixed_radix_schedules(lib):
         assert set(rad) <= MIXED_RADICES, (n, rad)
         assert k == fewest[n], (n, rad, fewest[n])
     expect = {3000: [8, 15, 5, 5], 1080: [8, 15, 9], 1920: [16, 8, 15], 14336: [16, 16, 8, 7],
-              1000: [10, 10, 10], 10000: [10, 10, 10, 10], 96: [16, 6], 1728: [16, 12, 9], 210: [15, 14]}
+              1000: [10, 10, 10], 10000: [10, 10, 10, 10], 96: [16, 6], 1728: [16, 12, 9], 210: [15, 14],
+              4095: [15, 3, 7, 13], 1001: [7, 11, 13], 143: [11, 13], 2197: [13, 13, 13]}
     for n, rad in expect.items():
         k = lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2))
         assert [buf[i] for i in range(k)] == rad, n
@@ -169,11 +170,11 @@ def test_mixed_fourstep_splits(lib):
     for n in [15360, 20000, 10 ** 6, 3 << 20, 6 ** 9, 5 ** 10, 7 ** 8, 14337 * 0 + 16384 * 3]:
         assert lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2)) == 0, n
         a, b = n1.value, n2.value
-        assert a * b == n and max(a, b) <= 14336 and _smooth7(a) and _smooth7(b), (n, a, b)
+        assert a * b == n and max(a, b) <= 14336 and _smooth13(a) and _smooth13(b), (n, a, b)
         divs = [d for d in range(2, 14337) if n % d == 0 and n // d <= 14336]
         best = min(divs, key=lambda d: abs(np.log(d) - 0.5 * np.log(n)))
         assert abs(np.log(b) - 0.5 * np.log(n)) <= abs(np.log(best) - 0.5 * np.log(n)) + 1e-12, (n, b, best)
-    for n in (11 * 3000, 1 << 25, 0, 1):
+    for n in (17 * 3000, 1 << 25, 0, 1):
         assert lib.fft_debug_mixed_plan(n, buf, ctypes.byref(n1), ctypes.byref(n2)) < 0, n
 
 

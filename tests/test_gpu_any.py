@@ -1,5 +1,5 @@
 """GPU parity of transforms whose sizes are not powers of two (mixed-radix
-stages for 7-smooth lengths, Bluestein over the power-of-two path for the
+stages for 13-smooth lengths, Bluestein over the power-of-two path for the
 rest) against the FP64 any-length oracle, through the C ABI via the ctypes
 binding.
 
@@ -29,7 +29,7 @@ def g():
     return g
 
 
-LENGTHS_1D = [3, 5, 6, 7, 12, 15, 31, 100, 127, 1000, 1536, 3000, 4095, 8191, 10007, 65535]
+LENGTHS_1D = [3, 5, 6, 7, 12, 15, 17, 31, 100, 127, 1000, 1536, 3000, 4093, 4095, 8191, 10007, 65535]
 
 
 @pytest.mark.parametrize("n", LENGTHS_1D)
@@ -105,9 +105,10 @@ def test_long_1d_million_points(g, monkeypatch):
 
 
 # Smooth lengths beyond one CTA: the mixed-radix four-step.  Prime powers
-# (5^7, 7^6, 3^10), a power of two times 3, 15 and 9 stages, and the
-# longest balanced case below 2^24.
-MIXED_FS = [(15360, 3), (20000, 2), (78125, 2), (117649, 1), (59049, 1), (3 << 20, 1), (2 ** 9 * 3 ** 9, 1)]
+# (5^7, 7^6, 3^10, 13^5), a power of two times 3, 15 and 9 stages, 11 and
+# 13 stages on both passes, and the longest balanced case below 2^24.
+MIXED_FS = [(15360, 3), (20000, 2), (78125, 2), (117649, 1), (59049, 1), (13 ** 5, 1), (1001 * 1000, 1),
+            (3 << 20, 1), (2 ** 9 * 3 ** 9, 1)]
 
 
 @pytest.mark.parametrize("n,batch", MIXED_FS, ids=[f"{a}x{b}" for a, b in MIXED_FS])
@@ -170,12 +171,13 @@ def test_fused_and_unfused_bluestein_agree(g, monkeypatch, n, inverse):
 
 
 def test_describe_and_unsupported(g):
-    plan = g.get_plan(1001, 11, 1, False, "fp32", "cuda")  # 7 * 11 * 13 and 11: Bluestein both ways
+    plan = g.get_plan(1003, 17, 1, False, "fp32", "cuda")  # 17 * 59 and 17: Bluestein both ways
     d = plan.describe()
-    assert d["kind"] == "any" and d["x"]["bluestein_m"] == 2048 and d["y"]["bluestein_m"] == 32
+    assert d["kind"] == "any" and d["x"]["bluestein_m"] == 2048 and d["y"]["bluestein_m"] == 64
     assert d["x"]["mixed"] == 0 and d["transposes"] == 2
-    X = torch.zeros(11011, dtype=torch.complex64, device="cuda")
-    w = torch.zeros(11011, dtype=torch.float32, device="cuda")
+    assert g.get_plan(1001, 11, 1, False, "fp32", "cuda").describe()["x"]["mixed"] == 1  # 7 * 11 * 13
+    X = torch.zeros(17051, dtype=torch.complex64, device="cuda")
+    w = torch.zeros(17051, dtype=torch.float32, device="cuda")
     with pytest.raises(g.FFTError):
         plan.backward_weighted(X, w, 2.0)
     with pytest.raises(g.FFTError):
@@ -186,11 +188,11 @@ def test_describe_and_unsupported(g):
 
 
 # Mixed-radix lengths: every radix alone and in combination (16, 8, 4, 2,
-# the two-level 15, 14, 12, 10, 9 and 6, the single 3, 5, 7), prime powers,
-# the longest length, and short rows packed several to a CTA.
-MIXED_1D = [3, 5, 6, 7, 9, 10, 12, 14, 15, 21, 24, 25, 35, 45, 49, 60, 96, 100, 105, 120, 135, 196, 210, 225, 343,
-            360, 405, 625, 1000, 1080, 1125, 1728, 1920, 2025, 2187, 2744, 3125, 3375, 6000, 7168, 10000, 12288,
-            14336]
+# the two-level 15, 14, 12, 10, 9 and 6, the single 3, 5, 7, 11, 13), prime
+# powers, the longest length, and short rows packed several to a CTA.
+MIXED_1D = [3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 21, 24, 25, 35, 45, 49, 60, 96, 100, 105, 120, 135, 143, 196,
+            210, 225, 343, 360, 405, 625, 1000, 1001, 1080, 1125, 1728, 1920, 2025, 2187, 2197, 2744, 3125, 3375,
+            4095, 6000, 7168, 10000, 12288, 13312, 14080, 14336]
 
 
 @pytest.mark.parametrize("n", MIXED_1D)
@@ -217,7 +219,7 @@ def test_mixed_radix_1d(g, n, inverse):
 # nx), x mixed or a power of two or Bluestein, y longest at 14336; axes
 # longer than 14336 by the four-step form (x directly, y between transposes)
 MIXED_2D = [(1000, 1000), (1080, 1920), (7, 1024), (100, 61), (61, 100), (1024, 7), (14336, 8), (12, 14336),
-            (9, 6), (3, 5), (600, 2), (3, 20000), (15360, 2)]
+            (9, 6), (3, 5), (600, 2), (3, 20000), (15360, 2), (1001, 143), (13, 4095)]
 
 
 @pytest.mark.parametrize("ny,nx", MIXED_2D, ids=[f"{a}x{b}" for a, b in MIXED_2D])
