@@ -260,3 +260,37 @@ def test_mixed_radix_and_bluestein_agree(g, monkeypatch, ny, nx):
     assert worst_rel_l2(blu.execute(d).cpu().numpy(), ref, nx * ny) <= tol_any(nx, ny, mixed=False)
     mixed.close()
     blu.close()
+
+
+# The bench's any-size batches at their full sizes and in their launch
+# configuration (one plan over the whole batch): 64 sampled signals of each
+# against the oracle, the rest through properties that hold at any size.
+BENCH_1D = [(3000, 16384), (4095, 16384), (4093, 16384), (1001, 32768), (1_000_000, 32)]
+
+
+@pytest.mark.parametrize("n,batch", BENCH_1D, ids=[f"{n}x{b}" for n, b in BENCH_1D])
+def test_bench_batches_full_size_sampled(g, n, batch):
+    x = synth.uniform_complex((batch, n), seed=2506 + n)
+    plan = g.Plan(n, 1, batch)
+    d = plan.describe()["x"]
+    assert (d["bluestein_m"] > 0) == (n == 4093)  # the prime takes Bluestein, the smooth lengths mixed radix
+    dx = torch.from_numpy(x).cuda()
+    got = plan.execute(dx)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    rows = np.unique(np.concatenate([[0, batch - 1], np.random.default_rng(n).integers(0, batch, 62 if n < 10 ** 5 else 2)]))
+    ref = oracle.fft1d_any(x[rows], threads=ORACLE_THREADS)
+    err = worst_rel_l2(got[torch.from_numpy(rows).cuda()].cpu().numpy(), ref, n)
+    print(f"bench batch {batch}x{n}: {len(rows)} sampled signals, worst rel L2 {err:.3e} (bound {tol_any(n, 1):.2e})")
+    assert err <= tol_any(n, 1), (n, err)
+    # every signal: Parseval (sum |X|^2 = n sum |x|^2), and the inverse plan
+    # brings back n x
+    e_in = (dx.abs() ** 2).sum(dim=1).double()
+    e_out = (got.abs() ** 2).sum(dim=1).double() / n
+    assert torch.max(torch.abs(e_out / e_in - 1)).item() <= 20 * tol_any(n, 1)
+    inv = g.Plan(n, 1, batch, inverse=True)
+    back = inv.execute(got) / n
+    rt = (torch.linalg.vector_norm(back - dx, dim=1) / torch.linalg.vector_norm(dx, dim=1)).max().item()
+    assert rt <= 2 * tol_any(n, 1), rt
+    for p in (plan, inv):
+        p.close()
