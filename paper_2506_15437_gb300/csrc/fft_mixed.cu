@@ -354,6 +354,21 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
     }
     const float2 *gin = in + base;
     float2 *gout = out + base;
+    // the first stage reads the group's input in rounds of blockDim.x
+    // butterflies: ask L2 for all of it now, so later rounds find it there
+    if (!COLS) {
+        if (threadIdx.x == 0) {
+            // the group's rows are contiguous: one bulk prefetch of the
+            // 16-byte-aligned interior
+            const uintptr_t a0 = reinterpret_cast<uintptr_t>(gin);
+            const uintptr_t a1 = a0 + (uintptr_t)g.nv * st.n * sizeof(float2);
+            const uintptr_t p0 = (a0 + 15) & ~(uintptr_t)15, p1 = a1 & ~(uintptr_t)15;
+            if (p1 > p0) bulk_prefetch_l2(reinterpret_cast<const void *>(p0), (uint32_t)(p1 - p0));
+        }
+    } else {
+        for (int i = threadIdx.x; i < st.n; i += blockDim.x)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(gin + (long long)i * nx));
+    }
     long long fs_out = 0;
     if (FS) {
         // rows t0 .. t0 + W - 1 are rows k1 of one transform b (W divides n1)
