@@ -306,7 +306,6 @@ struct FourStepB {
     int n1 = 0;      // rows per transform (0: not a four-step pass)
     int k1 = 0;      // set per CTA in the kernel
     int lshift = 0, lmask = 0;
-    int stride = 0;  // staged row stride in shared memory (n2 rounded up to 16 / W mod 16)
 };
 
 // Launch configuration of the mixed-radix kernel for one axis, fixed at

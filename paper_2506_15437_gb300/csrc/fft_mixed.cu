@@ -22,8 +22,9 @@
 // of a 2D plan without a transpose.  Longer smooth lengths run as a
 // four-step split n = n1 n2 over both layouts: columns of length n1 into a
 // workspace, then rows of length n2 whose first stage multiplies by the
-// inter-pass twiddle and whose last stage is staged in shared memory and
-// stored transposed (FourStepB).
+// inter-pass twiddle and whose last stage, with its lanes taken transform
+// first, stores the W rows' outputs transposed, W adjacent outputs per row of
+// the result (FourStepB).
 #include <math.h>
 
 #include "fft_common.cuh"
@@ -229,9 +230,13 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
                                             float si, const FourStepB &fs) {
     const int nb = a.nb, Ns = a.Ns;
     const int total = g.nv * nb;
+    // lanes by transform first (c fastest) for the column layout, and for
+    // the last stage of a four-step row pass, whose outputs go to global
+    // memory transposed: W adjacent outputs per row of the result
+    constexpr bool CFAST = COLS || (LAST && FS);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int c, j;
-        if (COLS) {
+        if (CFAST) {
             c = idx & (g.W - 1);
             j = idx >> a.wlog;
         } else {
@@ -293,7 +298,10 @@ __device__ __forceinline__ void mixed_stage(const MixedGeom &g, const StageArgs 
         for (int r = 0; r < R; ++r) {
             const int o = o0 + r * Ns;
             if (LAST && FS) {
-                dst[c * fs.stride + o] = v[r];  // staged: the CTA stores its rows transposed afterwards
+                // output o of row k1 + c goes to k1 + c + n1 o (gout points at k1)
+                float2 x = v[r];
+                x.y *= si;
+                gout[c + (long long)fs.n1 * o] = x;
             } else if (LAST) {
                 float2 x = v[r];
                 x.y *= si;
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
         g.tstride = st.n;
     }
     const float2 *gin = in + base;
-    float2 *gout = out + base;
+    float2 *gout = out + base;  // four-step rows: replaced below by the transposed output origin
     // the first stage reads the group's input in rounds of blockDim.x
     // butterflies: ask L2 for all of it now, so later rounds find it there
     if (!COLS) {
@@ -369,12 +377,11 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
         for (int i = threadIdx.x; i < st.n; i += blockDim.x)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(gin + (long long)i * nx));
     }
-    long long fs_out = 0;
     if (FS) {
         // rows t0 .. t0 + W - 1 are rows k1 of one transform b (W divides n1)
         const long long b = t0 / fs.n1;
         fs.k1 = (int)(t0 - b * fs.n1);
-        fs_out = b * (long long)fs.n1 * st.n + fs.k1;
+        gout = out + b * (long long)fs.n1 * st.n + fs.k1;
     }
     const float si = conj ? -1.f : 1.f;
     float2 *A = mbuf, *B = mbuf + st.buf_elems;
@@ -397,17 +404,6 @@ __global__ void __launch_bounds__(1024) k_mixed(const float2 *in, float2 *out, c
         float2 *tmp = A;
         A = B;
         B = tmp;
-    }
-    if (FS) {
-        // output k2 of row k1 goes to k1 + n1 k2: the W rows' outputs k2 are
-        // W adjacent elements, so a warp stores 32 / W runs of W elements
-        float2 *dstb = out + fs_out;
-        for (int idx = threadIdx.x; idx < W * st.n; idx += blockDim.x) {
-            const int c = idx & (W - 1), k2 = idx >> st.wlog;
-            float2 x = A[c * fs.stride + k2];
-            x.y *= si;
-            dstb[c + (long long)fs.n1 * k2] = x;
-        }
     }
 }
 
@@ -477,7 +473,7 @@ long long half_warp_cost(int lanes, F addr) {
 // Cost of the buffer written by stage s (with shift ps) and read by stage
 // s + 1 (same shift), over the first warps of every round (the patterns
 // repeat with the butterfly index).
-long long boundary_cost(const MixedStages &st, int s, int W, bool cols, int T, int ps) {
+long long boundary_cost(const MixedStages &st, int s, int W, bool cols, bool fs, int T, int ps) {
     auto pad = [ps](int x) { return ps ? x + (x >> ps) : x; };
     long long cost = 0;
     for (int side = 0; side < 2; ++side) {
@@ -490,8 +486,11 @@ long long boundary_cost(const MixedStages &st, int s, int W, bool cols, int T, i
                     cost += half_warp_cost(32, [&](int l) {
                         const int idx = w0 + l;
                         if (idx >= total || idx >= base + T) return -1;
-                        const int c = cols ? idx % W : idx / nb;
-                        const int j = cols ? idx / W : idx % nb;
+                        // lane order of stage t (the four-step row pass's last
+                        // stage takes the transforms fastest, like the columns)
+                        const bool cfast = cols || (fs && t == st.S - 1);
+                        const int c = cfast ? idx % W : idx / nb;
+                        const int j = cfast ? idx / W : idx % nb;
                         const int k = j % Ns;
                         const int e = side ? j + r * nb : (j - k) * R + k + r * Ns;
                         return pad(cols ? e * W + c : c * st.n + e);
@@ -502,7 +501,7 @@ long long boundary_cost(const MixedStages &st, int s, int W, bool cols, int T, i
 
 // the stage constants the kernel reads for a group of W transforms, with a
 // padding shift per stage boundary chosen by the bank model
-MixedStages with_group(const MixedStages &st, int W, bool cols, int T) {
+MixedStages with_group(const MixedStages &st, int W, bool cols, bool fs, int T) {
     MixedStages m = st;
     m.wlog = ilog2(W);
     int elems = W * st.n;
@@ -511,11 +510,11 @@ MixedStages with_group(const MixedStages &st, int W, bool cols, int T) {
         m.mag_ns[s] = magic(st.ns[s]);
         m.pad[s] = 0;
         if (s + 1 < st.S) {
-            long long best = boundary_cost(st, s, W, cols, T, 0);
+            long long best = boundary_cost(st, s, W, cols, fs, T, 0);
             for (int ps : {5, 4, 3}) {
                 // both buffers, padded, within one CTA's shared memory
                 if ((size_t)2 * (W * st.n + ((W * st.n - 1) >> ps)) * sizeof(float2) > kMixedMaxSmem) continue;
-                const long long c = boundary_cost(st, s, W, cols, T, ps);
+                const long long c = boundary_cost(st, s, W, cols, fs, T, ps);
                 if (c < best) {
                     best = c;
                     m.pad[s] = ps;
@@ -642,21 +641,15 @@ int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, in
     L.nx = cols ? nx : 0;
     const bool fs = !cols && fs_n1 > 0;
     if (fs) {
-        // W rows of one transform per CTA (W divides n1), staged with a row
-        // stride of 16 / W mod 16 words: a half-warp of the transposed store
-        // reads 16 / W outputs of each of the W rows, which then fall on 16
-        // distinct 8-byte bank pairs
+        // W rows of one transform per CTA (W divides n1); the last stage
+        // stores W adjacent outputs of the result per row
         L.fs.n1 = fs_n1;
-        L.fs.stride = st.n;
         L.W = 1;
-        for (int W : {8, 4, 2}) {
-            const int stride = st.n + ((16 / W - st.n % 16) % 16 + 16) % 16;
-            if (fs_n1 % W == 0 && (size_t)2 * W * stride * sizeof(float2) <= 72 * 1024) {
+        for (int W : {8, 4, 2})
+            if (fs_n1 % W == 0 && (size_t)2 * W * st.n * sizeof(float2) <= 72 * 1024) {
                 L.W = W;
-                L.fs.stride = stride;
                 break;
             }
-        }
     } else {
         L.W = cols ? mixed_cols_width(st.n, nx) : mixed_rows_per_cta(st.n);
     }
@@ -670,8 +663,7 @@ int mixed_prepare(const MixedStages &st, bool cols, int nx, MixedLaunch *out, in
     int most = 0;
     for (int s = 0; s < st.S; ++s) most = L.W * st.nb[s] > most ? L.W * st.nb[s] : most;
     if (((most + 31) & ~31) < L.T) L.T = (most + 31) & ~31;
-    L.m = with_group(st, L.W, cols, L.T);
-    if (fs && L.m.buf_elems < L.W * L.fs.stride) L.m.buf_elems = L.W * L.fs.stride;
+    L.m = with_group(st, L.W, cols, fs, L.T);
     L.smem = (size_t)2 * L.m.buf_elems * sizeof(float2);
     if (L.smem > kMixedMaxSmem) return -1;
     if (!smem_ok(mixed_fn(cols, fs), L.smem)) return -1;
