@@ -415,7 +415,12 @@ def fourstep_form(torch, g, steps, dev):
 
 def diff_form(torch, g, steps, dev):
     """L = sum w * |FFT2(x)|^2 for x [8][2048][2048], w U[0,1): one step is the
-    forward transform, the loss reduction and the fused adjoint (gradient)."""
+    forward transform, the loss and the adjoint (gradient).  Fused (what
+    weighted_power_loss runs): forward rows; one column pass that sums the
+    loss and runs the adjoint's column half on w (.) X; the adjoint's rows
+    scaled by the upstream gradient read on the device -- 52 B per point
+    (16 + 8 + 4 + 8 + 16).  Unfused, beside it: forward transform, loss
+    reduction over X and w, weighted adjoint -- 76 B per point."""
     import synth
     b, n = 8, 2048
     x = torch.from_numpy(synth.uniform_complex((b, n, n), seed=SEED)).to(dev)
@@ -425,16 +430,26 @@ def diff_form(torch, g, steps, dev):
     G = torch.empty_like(x)
     upstream = torch.ones(1, dtype=torch.float32, device=dev)  # dOut/dL, read on the device
 
-    def step():
+    def step_unfused():
         plan.execute(x, out=X)
         plan.weighted_power(X, w)
         plan.backward_weighted_dev(X, w, upstream, 2.0, out=G)
 
-    ms = time_fn(torch, step, max(10, steps // 4))
+    def step_fused():
+        plan.weighted_power_adjoint(x, w, X)
+        plan.backward_rows_scaled(X, upstream, 2.0, out=G)
+
     fl = 2 * flops_2d(n, n, b)
-    byts = 2 * 32.0 * b * n * n + 12.0 * b * n * n  # two 2-pass transforms, loss read, w read twice
-    return {"diff_8x2048x2048": {"ms": ms, "GFLOP/s_two_transforms": fl / ms / 1e6,
-                                 "HBM_GB/s_algorithmic": byts / ms / 1e6}}
+    ms_u = time_fn(torch, step_unfused, max(10, steps // 4))
+    out = {"ms_unfused": ms_u, "HBM_GB/s_algorithmic_unfused": 76.0 * b * n * n / ms_u / 1e6}
+    if plan.weighted_power_adjoint_parts() > 0:
+        ms = time_fn(torch, step_fused, max(10, steps // 4))
+        out.update({"ms": ms, "form": "fused", "GFLOP/s_two_transforms": fl / ms / 1e6,
+                    "HBM_GB/s_algorithmic": 52.0 * b * n * n / ms / 1e6})
+    else:
+        out.update({"ms": ms_u, "form": "unfused", "GFLOP/s_two_transforms": fl / ms_u / 1e6,
+                    "HBM_GB/s_algorithmic": 76.0 * b * n * n / ms_u / 1e6})
+    return {"diff_8x2048x2048": out}
 
 
 def time_fn(torch, fn, steps, warmup=3):
@@ -505,6 +520,18 @@ def profile_form(torch, name, steps, warmup, dev):
         upstream = torch.ones(1, dtype=torch.float32, device=dev)
         run = lambda: (plan.execute(x, out=X), plan.weighted_power(X, w),  # noqa: E731
                        plan.backward_weighted_dev(X, w, upstream, 2.0))
+    elif name == "diff_fused":
+        # the same step with the loss and the adjoint's column half fused
+        # into the forward's column pass
+        b, n = 8, 2048
+        x = torch.from_numpy(synth.uniform_complex((b, n, n), seed=SEED)).to(dev)
+        w = torch.from_numpy(synth.mask((b, n, n), seed=SEED + 1)).to(dev)
+        plan = g.Plan(n, n, b)
+        Y = torch.empty_like(x)
+        G = torch.empty_like(x)
+        upstream = torch.ones(1, dtype=torch.float32, device=dev)
+        run = lambda: (plan.weighted_power_adjoint(x, w, Y),  # noqa: E731
+                       plan.backward_rows_scaled(Y, upstream, 2.0, out=G))
     elif name == "fp32_8192":
         # the headline transform alone (row pass, column pass)
         x = torch.from_numpy(synth.normal_complex((8192, 8192), seed=SEED)).to(dev)
@@ -588,7 +615,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="enqueue the timed steps one by one (no CUDA graph)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-form", default=None,
-                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "bluestein_1001", "small_1024",
+                    choices=["split_tc_8192", "split_tc_1d", "fp32_1d", "fp32_8192", "ragged", "diff", "diff_fused", "bluestein_1001", "small_1024",
                              "mixed_fourstep_1e6", "mixed_4095",
                              "fourstep_2p24", "fourstep_2p26", "mixed_3000", "bluestein_4095", "transpose_2d"],
                     help="run only this secondary workload for --steps steps (for profilers); prints its schedule, not a metric line")

@@ -211,6 +211,45 @@ int fft_weighted_power(fft_plan_t p, const void *X, const void *w, void *partial
                        void *stream);
 int fft_weighted_power_parts(fft_plan_t p);
 
+/*
+ * fft_weighted_power_adjoint -- the loss L = sum w*|X|^2 of X = F x and
+ * the column half of its adjoint, y = F_cols^H (w (.) X), in two passes.
+ * The gradient dL/dx = 2 F^H (w (.) X) = 2 F_rows^H y, since the 2D F^H is
+ * F_rows^H F_cols^H; fft_backward_rows_scaled finishes it.  The row pass
+ * writes F_rows x into y.  The column pass then runs, for each tile of
+ * columns:
+ *   - the forward column transform, giving X in registers;
+ *   - the tile's partial sum of w*|X|^2 into `partials`;
+ *   - F_cols^H of w (.) X, stored over the tile in y.
+ * X itself is never stored.
+ *   x, y       device complex64, batch*ny*nx elements (may alias).
+ *   w          device float32, batch*ny*nx elements, the layout of X (must
+ *              not alias x or y).
+ *   partials   device float32, fft_weighted_power_adjoint_parts(p)
+ *              entries: one float tree sum per tile, which the caller
+ *              adds, preferably in double.
+ * Covered: dense 2D FP32 forward plans whose column length is at most 2048.
+ * Every other plan returns FFT_ERR_UNSUPPORTED, from both calls, and keeps
+ * the unfused path: fft_execute, fft_weighted_power,
+ * fft_backward_weighted_dev.  FFT_ERR_INVALID_ARG for NULL or misaligned
+ * pointers (16 bytes for x, y, w; 4 for partials).
+ */
+int fft_weighted_power_adjoint(fft_plan_t p, const void *x, const void *w, void *partials, void *y,
+                               void *stream);
+int fft_weighted_power_adjoint_parts(fft_plan_t p);
+
+/*
+ * fft_backward_rows_scaled -- the row half of the adjoint, for the plans
+ * fft_weighted_power_adjoint covers:
+ *   grad_in = scale * scale_dev[0] * F_rows^H y,
+ * the scale applied as the row pass loads.  scale_dev is a device float32
+ * (4-byte aligned), read when the pass runs; NULL means 1.  With
+ * y = fft_weighted_power_adjoint's output, scale = 2 and scale_dev =
+ * &dOut/dL, this gives dOut/dx.  y and grad_in may alias.
+ */
+int fft_backward_rows_scaled(fft_plan_t p, const void *y, const void *scale_dev, float scale, void *grad_in,
+                             void *stream);
+
 /* Destroy a plan and free its device memory (synchronises the device).
  * NULL is a no-op returning FFT_OK. */
 int fft_plan_destroy(fft_plan_t p);

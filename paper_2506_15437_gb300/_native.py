@@ -41,6 +41,9 @@ SIGNATURES = [
     ("fft_backward_weighted_dev", _I, [_P, _P, _P, _P, _F, _P, _P]),
     ("fft_weighted_power", _I, [_P, _P, _P, _P, _P]),
     ("fft_weighted_power_parts", _I, [_P]),
+    ("fft_weighted_power_adjoint", _I, [_P, _P, _P, _P, _P, _P]),
+    ("fft_weighted_power_adjoint_parts", _I, [_P]),
+    ("fft_backward_rows_scaled", _I, [_P, _P, _P, _F, _P, _P]),
     ("fft_plan_destroy", _I, [_P]),
     ("fft_last_error", _I, []),
     ("fft_error_string", ctypes.c_char_p, [_I]),

@@ -136,6 +136,134 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>:
     }
 }
 
+// Differentiation form, column half (P = 1).  For L = sum w |F x|^2 the
+// gradient is 2 F^H (w (.) X) with X = F x, and F^H = F_rows^H F_cols^H.
+// Each tile: the forward column transform X, in registers; the tile's loss
+// partial sum of w |X|^2 (float, one per tile); conj(w (.) X) written into
+// the tile in natural order; the same forward engine over it, whose
+// conjugated outputs are F_cols^H (w (.) X), stored in place of the tile's
+// input.  X itself never reaches memory: the pass reads the row pass's
+// output and w and writes the adjoint's column half.
+template <int N, int E, int W>
+__global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>::MINB)
+    k_cols_wadj(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw,
+                const float *__restrict__ w, float *partials, int nx, int batch, int *status, int pf_dist) {
+    using Sh = ColShape<N, E, W>;
+    using Eng = typename Sh::Eng;
+    constexpr int R0 = Eng::R0;
+    constexpr int T = Sh::T;
+    constexpr int WARPS = Sh::THREADS / 32;
+    extern __shared__ __align__(128) unsigned char raw[];
+    float2 *tile = reinterpret_cast<float2 *>(raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(raw + Sh::BAR_OFF);
+    __shared__ int s_ok;
+    __shared__ float s_red[WARPS];
+
+    const int t = threadIdx.x;
+    const int c = t % W;
+    const int tt = t / W;
+    const int groups_x = nx / W;
+    const long long ntiles = (long long)groups_x * batch;
+    auto issue = [&](long long id) {  // thread 0: TMA loads of tile `id` (map over `out`, P = 1)
+        const int x = (int)(id % groups_x) * 2 * W, z0 = (int)(id / groups_x) * N;
+        mbar_expect_tx(bar, Sh::TILE_BYTES);
+#pragma unroll 1
+        for (int k = 0; k < N / Sh::BOXR; ++k) tma_load_3d(tile + k * Sh::BOXR * W, &map, x, 0, z0 + k * Sh::BOXR, bar);
+    };
+    auto prefetch = [&](long long id) {
+        const int x = (int)(id % groups_x) * 2 * W, z0 = (int)(id / groups_x) * N;
+#pragma unroll 1
+        for (int k = 0; k < N / Sh::BOXR; ++k) tma_prefetch_3d(&map, x, 0, z0 + k * Sh::BOXR);
+    };
+    auto load_v = [&](float2 (&v)[E]) {
+#pragma unroll
+        for (int bb = 0; bb < E / R0; ++bb) {
+            const int j = tt + bb * T;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) v[bb * R0 + r] = tile[(j + r * (N / R0)) * W + c];
+        }
+    };
+
+    if (t == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    long long id = blockIdx.x;
+    uint32_t phase = 0;
+    if (t == 0 && id < ntiles) {
+        issue(id);
+        for (int d = 1; d <= pf_dist; ++d)
+            if (id + (long long)d * gridDim.x < ntiles) prefetch(id + (long long)d * gridDim.x);
+    }
+    for (; id < ntiles; id += gridDim.x) {
+        if (t == 0) s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (t == 0) {
+                record_status(status, kStatusTimeout);
+                mbar_wait_bounded(bar, phase);  // give the copy in flight a last chance to land
+            }
+            return;
+        }
+        phase ^= 1;
+        const long long next = id + gridDim.x;
+        const long long b = id / groups_x;
+        const long long off = b * (long long)N * nx + (long long)(id % groups_x) * W;
+        float2 *dst = out + off;
+        const float *wt = w + off;
+
+        float part = 0.f;
+        float2 v[E];
+        load_v(v);
+        auto all_read = [] { __syncthreads(); };
+        auto fwd_store = [&](int i, int cc, float2 x) { tile[i * W + cc] = x; };
+        Eng::template run<FftPolicy, true>(v, tile, tw, tt, c, SyncBlock{}, all_read, fwd_store);
+        __syncthreads();  // X complete in the tile, natural order
+        // w (.) X, its power and the conjugate, element by element: each row
+        // of W adjacent w values is one coalesced run (offsets < N * nx)
+#pragma unroll 4
+        for (int k = t; k < N * W; k += Sh::THREADS) {
+            const int i = k / W, cc = k % W;
+            const float wv = __ldg(wt + (i * nx + cc));
+            const float2 x = tile[k];
+            part = fmaf(wv, fmaf(x.x, x.x, x.y * x.y), part);
+            tile[k] = make_float2(wv * x.x, -(wv * x.y));
+        }
+        __syncthreads();  // conj(w (.) X) complete in the tile
+        load_v(v);
+        auto after_reads = [&] {
+            __syncthreads();
+            if (t == 0 && next < ntiles) {
+                fence_proxy_async_smem();
+                issue(next);
+                const long long pf = next + (long long)pf_dist * gridDim.x;
+                if (pf_dist > 0 && pf < ntiles) prefetch(pf);
+            }
+        };
+        auto adj_store = [&](int i, int cc, float2 x) { dst[i * nx + cc] = make_float2(x.x, -x.y); };
+        // the same table, through a pointer the compiler cannot equate with
+        // `tw`: otherwise it keeps the first run's twiddle loads live for the
+        // second and spills
+        const float2 *tw2 = tw;
+        asm volatile("" : "+l"(tw2));
+        Eng::template run<FftPolicy, true>(v, tile, tw2, tt, c, SyncBlock{}, after_reads, adj_store);
+        // the tile's partial: warps, then thread 0 (s_red is next written a
+        // whole tile later, after several block barriers)
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) part += __shfl_xor_sync(0xffffffffu, part, m);
+        if ((t & 31) == 0) s_red[t >> 5] = part;
+        __syncthreads();
+        if (t == 0) {
+            float sum = 0.f;
+#pragma unroll
+            for (int k = 0; k < WARPS; ++k) sum += s_red[k];
+            partials[id] = sum;
+        }
+    }
+}
+
 // Movement-only twin: one tile of W columns whose dense staging buffer holds
 // integer tags exactly where the TMA copy would put the data.  map[i] = final
 // row of the element that started in row i of column 0.
@@ -174,12 +302,19 @@ namespace {
 struct ColEntry {
     ColVariant v;
     const void *movemap = nullptr;
+    const void *wadj = nullptr;  // the differentiation form's fused column half (N <= 2048)
 };
 constexpr int kWSlots = 4;  // W = 2, 4, 8, 16
 ColEntry g_cols[kMaxLog2 + 1][3][kWSlots];  // [log2n][E slot: default, 32, 64][W slot]
 std::once_flag g_cols_once;  // registry filled once, safe across host threads
 
 int w_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : w == 16 ? 3 : -1; }
+
+// the fused column half reduces per warp: whole warps only
+template <int N, int E, int W>
+struct THREADS_OK {
+    static constexpr bool value = ColShape<N, E, W>::THREADS % 32 == 0;
+};
 
 template <int N, int E, int W>
 void reg_col(int eslot) {
@@ -194,6 +329,7 @@ void reg_col(int eslot) {
     en.v.box_rows = Sh::BOXR;
     en.v.tw_size = Sched<N, E>::tw_size;
     en.movemap = (const void *)k_cols_movemap<N, E, W>;
+    if constexpr (N >= 32 && N <= 2048 && THREADS_OK<N, E, W>::value) en.wadj = (const void *)k_cols_wadj<N, E, W>;
 }
 
 template <int N, int E>
@@ -290,6 +426,26 @@ cudaError_t launch_cols(const ColVariant &v, const CUtensorMap &map, float2 *out
     void *args[] = {(void *)&m,     (void *)&out,   (void *)&tw,       (void *)&nx,     (void *)&batch,
                     (void *)&split, (void *)&conj_out, (void *)&status, (void *)&pf_dist};
     return cudaLaunchKernel(v.fn, dim3(grid), dim3(v.threads), args, v.smem, s);
+}
+
+bool cols_wadj_available(const ColVariant &v) {
+    const ColEntry *en = col_entry(ilog2(v.n), v.e, v.w);
+    return en && en->wadj;
+}
+
+cudaError_t launch_cols_wadj(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
+                             const float *w, float *partials, int nx, int batch, int *status, int grid, int pf_dist,
+                             cudaStream_t s) {
+    const ColEntry *en = col_entry(ilog2(v.n), v.e, v.w);
+    if (!en || !en->wadj) return cudaErrorInvalidValue;
+    if (v.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(en->wadj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (e != cudaSuccess) return e;
+    }
+    CUtensorMap m = map;
+    void *args[] = {(void *)&m,  (void *)&out,   (void *)&tw,     (void *)&w,      (void *)&partials,
+                    (void *)&nx, (void *)&batch, (void *)&status, (void *)&pf_dist};
+    return cudaLaunchKernel(en->wadj, dim3(grid), dim3(v.threads), args, v.smem, s);
 }
 
 cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s) {

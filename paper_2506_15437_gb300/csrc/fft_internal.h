@@ -189,6 +189,13 @@ cudaError_t launch_cols_stream(const ColVariant &v, const CUtensorMap &map, cons
 // Reorder-map debug launchers: write map[i] = output position of input i.
 cudaError_t launch_rows_movemap(int log2n, int *map, cudaStream_t s);
 cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s);
+// Differentiation form, fused column half (fft_cols.cu, P = 1, n <= 2048):
+// forward column transform, per-tile partials of w |X|^2, and F_cols^H (w (.) X)
+// stored in place; one partial per tile of v.w columns.
+bool cols_wadj_available(const ColVariant &v);
+cudaError_t launch_cols_wadj(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
+                             const float *w, float *partials, int nx, int batch, int *status, int grid, int pf_dist,
+                             cudaStream_t s);
 
 // Sets the calling thread's fft_last_error() value.
 void set_last_error(int code);
@@ -420,6 +427,10 @@ struct fft_plan_s {
     int tc_stream = 1;      // tensor-core columns of 4096 points: streaming radix-64 pass where allowed
     int tcg = 1;            // split-FP16 plans: 1 tcgen05/TMEM butterflies, 0 mma.sync
     int wp_parts = 0;
+    // the fused differentiation form's column map (over the caller's y)
+    CUtensorMap wadj_map;
+    const void *wadj_base = nullptr;
+    float2 *wadj_tw = nullptr;  // its column twiddles (plan creation)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional per-pass timing events
     gb300fft::Schedule sched;  // the schedule this plan was built with
     std::vector<void *> allocations;

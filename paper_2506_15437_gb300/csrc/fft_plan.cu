@@ -54,6 +54,25 @@ EncodeTiledFn get_encode_fn() {
 
 bool is_pow2(long long n) { return n >= 1 && (n & (n - 1)) == 0; }
 
+// The differentiation form with the loss and the adjoint's column half fused
+// into the forward's column pass: dense 2D FP32 forward plans whose column
+// pass runs without a pre-split and has a compiled fused variant.
+// Its tiles are the default widest ones (W adjacent columns, whole warps),
+// not the narrowed tiles small plans use for their column pass.
+const ColVariant *wadj_variant(fft_plan_s *p) {
+    if (!p || p->kind != 0 || p->prec != FFT_PREC_FP32 || p->dir != FFT_FORWARD) return nullptr;
+    if (p->any || p->fs.n1 > 0 || p->axes == 2 || p->rows.n < 2 || !p->rows.row || !p->cols.col) return nullptr;
+    // the whole column in one tile, up to 2048 points: at 4096 the fused
+    // column pass (two transforms per tile at 8 warps per SM) made the
+    // 2 x 4096^2 step slower than the unfused one
+    const int n = p->ny;
+    if (n > 2048 || !is_pow2(n)) return nullptr;
+    const int w = default_col_w(n, p->nx);
+    const ColVariant *v = col_variant(ilog2(n), preferred_col_e(n, w), w);
+    return v && p->nx % v->w == 0 && cols_wadj_available(*v) ? v : nullptr;
+}
+
+
 int fail(int code) {
     t_last_error = code;
     return code;
@@ -501,6 +520,14 @@ fft_plan_s *create_dense(int nx, int ny, int batch, int dir, int precision, cons
         else if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = FFT_ERR_CUDA;
     }
     p->wp_parts = p->num_sms * 4;
+    if (rc == FFT_OK) {
+        // the fused differentiation form's column twiddles, where it applies
+        if (const ColVariant *wv = wadj_variant(p)) {
+            p->wadj_tw = dev_alloc<float2>(p, wv->tw_size > 0 ? wv->tw_size : 1);
+            if (!p->wadj_tw) rc = FFT_ERR_ALLOC;
+            else if (wv->tw_size > 0 && build_twiddles(p->wadj_tw, wv->n, wv->e, 0) != cudaSuccess) rc = FFT_ERR_CUDA;
+        }
+    }
     if (rc == FFT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FFT_ERR_CUDA;
     if (rc != FFT_OK) {
         free_plan(p);
@@ -1235,6 +1262,63 @@ int fft_weighted_power(fft_plan_t p, const void *X, const void *w, void *partial
     if (launch_weighted_power(static_cast<const float2 *>(X), static_cast<const float *>(w), total,
                               static_cast<float *>(partials), p->wp_parts,
                               static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
+int fft_weighted_power_adjoint_parts(fft_plan_t p) {
+    if (!p) return FFT_ERR_INVALID_ARG;
+    const ColVariant *v = wadj_variant(p);
+    if (!v) return FFT_ERR_UNSUPPORTED;
+    const long long tiles = (long long)(p->nx / v->w) * p->batch;
+    return tiles > 0x7fffffffLL ? FFT_ERR_UNSUPPORTED : (int)tiles;
+}
+
+int fft_weighted_power_adjoint(fft_plan_t p, const void *x, const void *w, void *partials, void *y, void *stream) {
+    if (!p || !x || !w || !partials || !y || !aligned16(x) || !aligned16(y) || !aligned16(w) ||
+        (reinterpret_cast<uintptr_t>(partials) & 3))
+        return FFT_ERR_INVALID_ARG;
+    const ColVariant *v = wadj_variant(p);
+    if (!v || !p->wadj_tw) return FFT_ERR_UNSUPPORTED;
+    cudaSetDevice(p->device);
+    p->last_use_host = false;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float2 *yd = static_cast<float2 *>(y);
+    const long long nrows = (long long)p->ny * p->batch;
+    // forward rows, x -> y
+    const int rgrid = row_grid(*p->rows.row, nrows, p->num_sms, false, 1, p->row_persist > 0);
+    if (launch_rows(*p->rows.row, static_cast<const float2 *>(x), yd, p->rows.tw, p->twp, nrows, p->ny, 1, 0, 0,
+                    nullptr, 1.f, nullptr, rgrid, p->row_pf, 0, 0, 0, s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    // fused columns, in place on y
+    if (p->wadj_base != y) {
+        if (encode_col_map(&p->wadj_map, y, p->nx, (long long)p->ny * p->batch, 1, v->w, v->box_rows) != 0)
+            return FFT_ERR_CUDA;
+        p->wadj_base = y;
+    }
+    const long long tiles = (long long)(p->nx / v->w) * p->batch;
+    int grid = p->num_sms * col_ctas_per_sm(*v);
+    if (grid > tiles) grid = (int)tiles;
+    if (launch_cols_wadj(*v, p->wadj_map, yd, p->wadj_tw, static_cast<const float *>(w), static_cast<float *>(partials),
+                         p->nx, p->batch, p->status, grid, p->col_pf, s) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
+int fft_backward_rows_scaled(fft_plan_t p, const void *y, const void *scale_dev, float scale, void *grad_in,
+                             void *stream) {
+    if (!p || !y || !grad_in || !aligned16(y) || !aligned16(grad_in) ||
+        (scale_dev && (reinterpret_cast<uintptr_t>(scale_dev) & 3)))
+        return FFT_ERR_INVALID_ARG;
+    if (!wadj_variant(p)) return FFT_ERR_UNSUPPORTED;
+    cudaSetDevice(p->device);
+    p->last_use_host = false;
+    const long long nrows = (long long)p->ny * p->batch;
+    // F_rows^H = conj F_rows conj, times scale (and *scale_dev) on load
+    const int rgrid = row_grid(*p->rows.row, nrows, p->num_sms, true, 1, p->row_persist > 0);
+    if (launch_rows(*p->rows.row, static_cast<const float2 *>(y), static_cast<float2 *>(grad_in), p->rows.tw, p->twp,
+                    nrows, p->ny, 1, 1, 1, nullptr, scale, static_cast<const float *>(scale_dev), rgrid, p->row_pf, 0,
+                    0, 0, static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return FFT_ERR_CUDA;
     return FFT_OK;
 }

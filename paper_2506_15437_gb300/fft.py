@@ -131,6 +131,44 @@ class Plan:
                 "fft_weighted_power")
         return partials.double().sum()
 
+    def weighted_power_adjoint_parts(self) -> int:
+        """Partials of the fused differentiation form, or 0 where the plan
+        does not cover it (fft_weighted_power_adjoint_parts)."""
+        n = self._lib.fft_weighted_power_adjoint_parts(self._p)
+        return n if n > 0 else 0
+
+    def weighted_power_adjoint(self, x: torch.Tensor, w: torch.Tensor, y: torch.Tensor | None = None):
+        """(L, y): L = sum w*|F x|^2 as a float64 0-d tensor and y =
+        F_cols^H (w (.) F x), the adjoint's column half, in two passes
+        (fft_weighted_power_adjoint)."""
+        y = self._io(x, y)
+        _check_tensor(w, torch.float32, "w")
+        if w.numel() != self.numel:
+            raise ValueError("w has the wrong size")
+        parts = self.weighted_power_adjoint_parts()
+        if parts == 0:
+            raise N.FFTError(N.FFT_ERR_UNSUPPORTED, "fft_weighted_power_adjoint")
+        partials = torch.empty(parts, dtype=torch.float32, device=x.device)
+        N.check(self._lib.fft_weighted_power_adjoint(self._p, x.data_ptr(), w.data_ptr(), partials.data_ptr(),
+                                                     y.data_ptr(), _stream_handle(x.device)),
+                "fft_weighted_power_adjoint")
+        return partials.double().sum(), y
+
+    def backward_rows_scaled(self, y: torch.Tensor, scale_dev: torch.Tensor | None = None, scale: float = 1.0,
+                             out: torch.Tensor | None = None) -> torch.Tensor:
+        """scale * scale_dev * F_rows^H y (fft_backward_rows_scaled); scale_dev
+        a one-element float32 CUDA tensor read on the device, or None."""
+        out = self._io(y, out)
+        if scale_dev is not None:
+            _check_tensor(scale_dev, torch.float32, "scale_dev")
+            if scale_dev.numel() != 1:
+                raise ValueError("scale_dev must have one element")
+        N.check(self._lib.fft_backward_rows_scaled(self._p, y.data_ptr(),
+                                                   None if scale_dev is None else scale_dev.data_ptr(),
+                                                   ctypes.c_float(scale), out.data_ptr(), _stream_handle(y.device)),
+                "fft_backward_rows_scaled")
+        return out
+
     def set_pass_events(self, start=None, mid=None, end=None):
         """Record torch.cuda.Event objects around the row and column passes of
         every following execute/backward (None, None, None turns it off)."""
@@ -275,8 +313,12 @@ def fft1(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
 
 
 class WeightedPowerLoss(torch.autograd.Function):
-    """L = sum w * |FFT2(x)|^2 with a fused adjoint: dL/dx = 2 F^H (w (.) F x),
-    the weighting folded into the adjoint's first pass (fft_backward_weighted)."""
+    """L = sum w * |FFT2(x)|^2 with a fused adjoint: dL/dx = 2 F^H (w (.) F x).
+    Where the plan covers it, the forward's column pass also sums the loss
+    and runs the adjoint's column half (fft_weighted_power_adjoint), so the
+    backward is one scaled row pass (fft_backward_rows_scaled) and X = F x is
+    never stored; otherwise the forward stores X and the weighting is folded
+    into the adjoint's first pass (fft_backward_weighted_dev)."""
 
     @staticmethod
     def forward(ctx, x, w, precision: str = "fp32"):
@@ -284,17 +326,26 @@ class WeightedPowerLoss(torch.autograd.Function):
         w = w.contiguous()
         nx, ny, batch = _shape(x)
         plan = get_plan(nx, ny, batch, False, precision, x.device)
-        X = plan.execute(x)
         ctx.plan = plan
+        if plan.weighted_power_adjoint_parts() > 0:
+            L, y = plan.weighted_power_adjoint(x, w)
+            ctx.fused = True
+            ctx.save_for_backward(y)
+            return L.to(torch.float32)
+        X = plan.execute(x)
+        ctx.fused = False
         ctx.save_for_backward(X, w)
         return plan.weighted_power(X, w).to(torch.float32)
 
     @staticmethod
     def backward(ctx, gL):
-        X, w = ctx.saved_tensors
-        # the upstream gradient stays on the device: the adjoint's first pass
+        saved = ctx.saved_tensors
+        # the upstream gradient stays on the device: the backward's pass
         # reads it, so backward issues no host synchronisation
-        g = gL.detach().to(device=X.device, dtype=torch.float32).reshape(1).contiguous()
+        g = gL.detach().to(device=saved[0].device, dtype=torch.float32).reshape(1).contiguous()
+        if ctx.fused:
+            return ctx.plan.backward_rows_scaled(saved[0], g, 2.0), None, None
+        X, w = saved
         return ctx.plan.backward_weighted_dev(X, w, g, 2.0), None, None
 
 

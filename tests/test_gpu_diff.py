@@ -114,8 +114,10 @@ def test_backward_reads_the_upstream_gradient_on_the_device(g):
     finally:
         torch.cuda.set_sync_debug_mode(0)
     plan = g.get_plan(n, n, 2, False, "fp32", "cuda")
-    X = plan.execute(torch.from_numpy(x).cuda())
-    want = plan.backward_weighted(X, wd, 7.0)
+    # the loss runs the fused form here: its backward is the scaled row half
+    assert plan.weighted_power_adjoint_parts() > 0
+    _, y = plan.weighted_power_adjoint(torch.from_numpy(x).cuda(), wd)
+    want = plan.backward_rows_scaled(y, None, 7.0)
     torch.cuda.synchronize()
     assert torch.equal(torch.view_as_real(xd.grad), torch.view_as_real(want))
     gref, _ = ref_grad(x, w)
@@ -136,3 +138,90 @@ def test_backward_weighted_dev_rejects_bad_scale_pointer(g):
     rc = lib.fft_backward_weighted_dev(plan._p, X.data_ptr(), w.data_ptr(), s.data_ptr() + 2, 1.0, X.data_ptr(),
                                        torch.cuda.current_stream().cuda_stream)
     assert rc == N.FFT_ERR_INVALID_ARG
+
+
+# The fused form: fft_weighted_power_adjoint (forward rows, then one column
+# pass that sums the loss and runs the adjoint's column half) and
+# fft_backward_rows_scaled (the adjoint's row half).
+FUSED_SHAPES = [(64, 64, 1), (256, 1024, 3), (1024, 256, 2), (2048, 2048, 1), (32, 4096, 1), (2048, 64, 2)]
+
+
+@pytest.mark.parametrize("ny,nx,b", FUSED_SHAPES, ids=[f"{b}x{ny}x{nx}" for ny, nx, b in FUSED_SHAPES])
+def test_fused_column_half_against_fp64(g, ny, nx, b):
+    """y = F_cols^H (w (.) F x) against the FP64 oracle (the forward 2D
+    transform, then the inverse-sign 1D transform down every column of the
+    weighted product), the loss against sum w |F x|^2, and the full gradient
+    2 F_rows^H y against 2 F^H (w (.) F x)."""
+    x = synth.uniform_complex((b, ny, nx), seed=ny + 3 * nx + b)
+    w = synth.mask((b, ny, nx), seed=ny + nx)
+    plan = g.Plan(nx, ny, b)
+    assert plan.weighted_power_adjoint_parts() > 0
+    xd = torch.from_numpy(x).cuda()
+    wd = torch.from_numpy(w).cuda()
+    L, y = plan.weighted_power_adjoint(xd, wd)
+    G = plan.backward_rows_scaled(y, None, 2.0)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    X = oracle.fft2d(x, dir=-1, threads=ORACLE_THREADS)
+    wx = w * X
+    yref = np.swapaxes(oracle.fft1d_batch(np.ascontiguousarray(np.swapaxes(wx, -1, -2)), dir=1,
+                                          threads=ORACLE_THREADS), -1, -2)
+    n = nx * ny
+    for k in range(b):
+        assert rel_l2(y[k].cpu().numpy(), yref[k]) <= tol_fp32(n), k
+    Lref = float(np.sum(w * np.abs(X) ** 2))
+    assert abs(L.item() - Lref) / Lref < 1e-6
+    gref, _ = ref_grad(x, w)
+    for k in range(b):
+        assert rel_l2(G[k].cpu().numpy(), gref[k]) <= 2 * tol_fp32(n), k
+    plan.close()
+
+
+def test_fused_and_unfused_forms_agree(g):
+    """The same loss and gradient from both forms; in place (y over x) too."""
+    n, b = 512, 2
+    x = synth.uniform_complex((b, n, n), seed=41)
+    w = synth.mask((b, n, n), seed=42)
+    plan = g.Plan(n, n, b)
+    xd = torch.from_numpy(x).cuda()
+    wd = torch.from_numpy(w).cuda()
+    one = torch.ones(1, dtype=torch.float32, device="cuda")
+    L1, y = plan.weighted_power_adjoint(xd, wd)
+    G1 = plan.backward_rows_scaled(y, one, 2.0)
+    X = plan.execute(xd)
+    L2 = plan.weighted_power(X, wd)
+    G2 = plan.backward_weighted_dev(X, wd, one, 2.0)
+    torch.cuda.synchronize()
+    assert abs(L1.item() - L2.item()) / L2.item() < 1e-6
+    assert rel_l2(G1.cpu().numpy(), G2.cpu().numpy()) <= 2 * tol_fp32(n * n)
+    d = xd.clone()
+    L3, y3 = plan.weighted_power_adjoint(d, wd, d)
+    assert y3.data_ptr() == d.data_ptr()
+    assert L3.item() == L1.item() and torch.equal(torch.view_as_real(d), torch.view_as_real(y))
+    G3 = plan.backward_rows_scaled(d, one, 2.0, out=d)
+    assert torch.equal(torch.view_as_real(G3), torch.view_as_real(G1))
+    plan.close()
+
+
+def test_unfused_plans_keep_the_unfused_loss(g):
+    """Inverse plans and columns longer than 2048 have no fused form: both
+    calls report FFT_ERR_UNSUPPORTED, and the loss runs the unfused path
+    with the same gradient bound."""
+    from paper_2506_15437_gb300 import _native as N
+    inv = g.Plan(64, 64, 1, inverse=True)
+    assert inv.weighted_power_adjoint_parts() == 0
+    assert inv._lib.fft_weighted_power_adjoint_parts(inv._p) == N.FFT_ERR_UNSUPPORTED
+    z = torch.zeros(64 * 64, dtype=torch.complex64, device="cuda")
+    assert inv._lib.fft_backward_rows_scaled(inv._p, z.data_ptr(), None, 1.0, z.data_ptr(), None) == \
+        N.FFT_ERR_UNSUPPORTED
+    inv.close()
+    assert g.get_plan(16, 4096, 1, False, "fp32", "cuda").weighted_power_adjoint_parts() == 0
+    ny, nx = 8192, 16
+    long = g.get_plan(nx, ny, 1, False, "fp32", "cuda")
+    assert long.weighted_power_adjoint_parts() == 0
+    x = synth.uniform_complex((ny, nx), seed=51)
+    w = synth.mask((ny, nx), seed=52)
+    xd = torch.from_numpy(x).cuda().requires_grad_(True)
+    g.weighted_power_loss(xd, torch.from_numpy(w).cuda()).backward()
+    gref, _ = ref_grad(x, w)
+    assert rel_l2(xd.grad.cpu().numpy(), gref) <= 2 * tol_fp32(nx * ny)
