@@ -433,6 +433,15 @@ bool cols_wadj_available(const ColVariant &v) {
     return en && en->wadj;
 }
 
+int cols_wadj_ctas_per_sm(const ColVariant &v) {
+    const ColEntry *en = col_entry(ilog2(v.n), v.e, v.w);
+    if (!en || !en->wadj) return 1;
+    int blocks = 0;
+    if (v.smem > 48 * 1024) cudaFuncSetAttribute(en->wadj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, en->wadj, v.threads, v.smem) != cudaSuccess) return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
 cudaError_t launch_cols_wadj(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
                              const float *w, float *partials, int nx, int batch, int *status, int grid, int pf_dist,
                              cudaStream_t s) {

@@ -193,6 +193,7 @@ cudaError_t launch_cols_movemap(int log2n, int *map, cudaStream_t s);
 // forward column transform, per-tile partials of w |X|^2, and F_cols^H (w (.) X)
 // stored in place; one partial per tile of v.w columns.
 bool cols_wadj_available(const ColVariant &v);
+int cols_wadj_ctas_per_sm(const ColVariant &v);
 cudaError_t launch_cols_wadj(const ColVariant &v, const CUtensorMap &map, float2 *out, const float2 *tw,
                              const float *w, float *partials, int nx, int batch, int *status, int grid, int pf_dist,
                              cudaStream_t s);

@@ -57,8 +57,11 @@ bool is_pow2(long long n) { return n >= 1 && (n & (n - 1)) == 0; }
 // The differentiation form with the loss and the adjoint's column half fused
 // into the forward's column pass: dense 2D FP32 forward plans whose column
 // pass runs without a pre-split and has a compiled fused variant.
-// Its tiles are the default widest ones (W adjacent columns, whole warps),
-// not the narrowed tiles small plans use for their column pass.
+// Its tiles are the widest of at most 64 KiB (whole warps, W adjacent
+// columns), not the narrowed tiles small plans use for their column pass:
+// two CTAs per SM, one transforming while the other loads (measured against
+// the column pass's own 128 KiB tiles: 8 x 2048^2 step 0.495 -> 0.483 ms,
+// 32 x 1024^2 0.461 -> 0.452).
 const ColVariant *wadj_variant(fft_plan_s *p) {
     if (!p || p->kind != 0 || p->prec != FFT_PREC_FP32 || p->dir != FFT_FORWARD) return nullptr;
     if (p->any || p->fs.n1 > 0 || p->axes == 2 || p->rows.n < 2 || !p->rows.row || !p->cols.col) return nullptr;
@@ -67,7 +70,8 @@ const ColVariant *wadj_variant(fft_plan_s *p) {
     // 2 x 4096^2 step slower than the unfused one
     const int n = p->ny;
     if (n > 2048 || !is_pow2(n)) return nullptr;
-    const int w = default_col_w(n, p->nx);
+    int w = default_col_w(n, p->nx);
+    while (w > 2 && (long long)n * w * sizeof(float2) > 65536) w >>= 1;
     const ColVariant *v = col_variant(ilog2(n), preferred_col_e(n, w), w);
     return v && p->nx % v->w == 0 && cols_wadj_available(*v) ? v : nullptr;
 }
@@ -1297,7 +1301,7 @@ int fft_weighted_power_adjoint(fft_plan_t p, const void *x, const void *w, void 
         p->wadj_base = y;
     }
     const long long tiles = (long long)(p->nx / v->w) * p->batch;
-    int grid = p->num_sms * col_ctas_per_sm(*v);
+    int grid = p->num_sms * cols_wadj_ctas_per_sm(*v);
     if (grid > tiles) grid = (int)tiles;
     if (launch_cols_wadj(*v, p->wadj_map, yd, p->wadj_tw, static_cast<const float *>(w), static_cast<float *>(partials),
                          p->nx, p->batch, p->status, grid, p->col_pf, s) != cudaSuccess)
