@@ -425,6 +425,12 @@ int fft_debug_tc_layout(int n, int kind, long long *info);
  * FFT_ERR_INVALID_ARG for NULL pointers or r < 1.  Host only. */
 int fft_debug_root(int m, int r, float *c, float *s);
 
+/* The library's CUDA runtime keeps its own per-thread last error (it is
+ * linked statically): the text of the last CUDA error this thread met inside
+ * the library, without clearing it ("no error" if none).  A call that
+ * returned FFT_ERR_CUDA has left its cause here.  Never NULL. */
+const char *fft_debug_last_cuda_error(void);
+
 /* Library version string. */
 const char *fft_version(void);
 

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("fft_debug_tc_layout", _I, [_I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     ("fft_debug_mixed_plan", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("fft_debug_root", _I, [_I, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    ("fft_debug_last_cuda_error", ctypes.c_char_p, []),
     ("fft_version", ctypes.c_char_p, []),
 ]
 

@@ -430,9 +430,15 @@ const void *mixed_fn(bool cols, bool fs) {
                 : fs ? (const void *)k_mixed<false, true> : (const void *)k_mixed<false, false>;
 }
 
+// One kernel serves every mixed length, each plan with its own shared
+// memory size, so the kernel's dynamic shared-memory limit is raised to the
+// largest any plan may ask for, the same value from every plan: a
+// plan-sized limit would let a plan created later (or concurrently, on
+// another thread) lower it below what an earlier plan launches with.
 bool smem_ok(const void *fn, size_t smem) {
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                                cudaSuccess)
+    if (smem > kMixedMaxSmem) return false;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedMaxSmem) != cudaSuccess)
         return false;
     return true;
 }
@@ -714,3 +720,5 @@ extern "C" int fft_debug_root(int m, int r, float *c, float *s) {
     *s = (float)gb300fft::sin_2pi(m, r);
     return FFT_OK;
 }
+
+extern "C" const char *fft_debug_last_cuda_error(void) { return cudaGetErrorString(cudaPeekAtLastError()); }

@@ -294,3 +294,22 @@ def test_bench_batches_full_size_sampled(g, n, batch):
     assert rt <= 2 * tol_any(n, 1), rt
     for p in (plan, inv):
         p.close()
+
+
+@pytest.mark.parametrize("first", [1000, 4095])
+def test_mixed_plans_with_different_shared_memory_coexist(g, first):
+    """Two mixed-radix plans whose CTAs need different amounts of dynamic
+    shared memory above 48 KiB from the same kernel (1000-point rows four to
+    a CTA, one 4095-point row per CTA), created one after the other: the
+    later plan must not leave the kernel unable to launch the earlier one's
+    CTAs (it did when each plan set the kernel's limit to its own size)."""
+    shapes = {1000: 8, 4095: 2}
+    order = [first, 4095 if first == 1000 else 1000]
+    plans = {n: g.Plan(n, 1, shapes[n]) for n in order}
+    for n in order + order:
+        x = synth.uniform_complex((shapes[n], n), seed=n)
+        got = plans[n].execute(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert plans[n].status() == 0
+        assert worst_rel_l2(got, oracle.fft1d_any(x, threads=ORACLE_THREADS), n) <= tol_any(n, 1), n
+    for p in plans.values():
+        p.close()
