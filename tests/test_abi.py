@@ -90,6 +90,17 @@ def test_null_plan_calls(lib):
     assert lib.fft_plan_status(None, None) == -2
     off = ctypes.c_longlong(0)
     assert lib.fft_ragged_offset(None, 0, ctypes.byref(off)) < 0
+    # the fused differentiation form: a NULL plan is an argument error
+    assert lib.fft_weighted_power_adjoint_parts(None) == -2
+    assert lib.fft_weighted_power_adjoint(None, None, None, None, None, None) == -2
+    assert lib.fft_backward_rows_scaled(None, None, None, 1.0, None, None) == -2
+
+
+def test_last_cuda_error_text(lib):
+    """A readable string whatever state the runtime is in (here, without
+    a GPU, whatever the runtime reports for that)."""
+    t = lib.fft_debug_last_cuda_error()
+    assert isinstance(t, bytes) and len(t) > 0
 
 
 def test_ragged_rejects_out_of_range_sizes(lib):
