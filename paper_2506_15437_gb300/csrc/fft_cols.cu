@@ -138,12 +138,13 @@ __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>:
 
 // Differentiation form, column half (P = 1).  For L = sum w |F x|^2 the
 // gradient is 2 F^H (w (.) X) with X = F x, and F^H = F_rows^H F_cols^H.
-// Each tile: the forward column transform X, in registers; the tile's loss
-// partial sum of w |X|^2 (float, one per tile); conj(w (.) X) written into
-// the tile in natural order; the same forward engine over it, whose
-// conjugated outputs are F_cols^H (w (.) X), stored in place of the tile's
-// input.  X itself never reaches memory: the pass reads the row pass's
-// output and w and writes the adjoint's column half.
+// Each tile: the forward column transform, its outputs X written back into
+// the tile in natural order; one sweep over the tile that adds the tile's
+// loss partial sum of w |X|^2 (float, one per tile) and replaces X by
+// conj(w (.) X); the same forward engine over that, whose conjugated outputs
+// are F_cols^H (w (.) X), stored in place of the tile's input.  X itself
+// never reaches HBM: the pass reads the row pass's output and w and writes
+// the adjoint's column half.
 template <int N, int E, int W>
 __global__ void __launch_bounds__(ColShape<N, E, W>::THREADS, ColShape<N, E, W>::MINB)
     k_cols_wadj(const __grid_constant__ CUtensorMap map, float2 *out, const float2 *__restrict__ tw,
