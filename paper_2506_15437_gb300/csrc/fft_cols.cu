@@ -391,11 +391,14 @@ int preferred_col_e(int n, int w) {
     return default_col_e(n);
 }
 
-// Widest tile that keeps the staged tile within 128 KiB and the row length:
-// rows of at least 32 bytes (W >= 4) make whole DRAM sectors, which the TMA
-// moves far faster than 16-byte rows.
+// Widest tile that keeps the staged tile within 128 KiB (columns of 4096
+// points and more) or 64 KiB (shorter columns: two CTAs per SM, one
+// transforming while the other loads; measured against 128 KiB tiles,
+// 4 x 2048^2 0.136 -> 0.127 ms, 16 x 1024^2 0.124 -> 0.119) and the row
+// length: rows of at least 32 bytes (W >= 4) make whole DRAM sectors, which
+// the TMA moves far faster than 16-byte rows.
 int default_col_w(int n, int nx) {
-    int w = 16384 / n;
+    int w = (n >= 4096 ? 16384 : 8192) / n;
     if (w > 16) w = 16;
     if (w < 2) w = 2;
     while (w > nx) w >>= 1;
