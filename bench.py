@@ -491,8 +491,10 @@ def ragged_form(torch, g, steps, dev):
 
 def ragged_algorithmic_bytes(nx, ny, fused_max=8192):
     """One read and one write of complex64 per point per HBM pass: instances
-    of at most `fused_max` points run rows and columns in one CTA (one pass,
-    16 B per point), larger ones two passes (32 B per point)."""
+    of at most `fused_max` points fit one CTA's shared memory, so they are
+    charged one pass (16 B per point), larger ones two passes (32 B per
+    point).  The kernel fuses only instances up to its 4096-element work
+    item, so for those between 4096 and 8192 points this is a lower bound."""
     total = 0
     for a, b in zip(nx, ny):
         n = int(a) * int(b)

@@ -295,14 +295,14 @@ int fft_execute_ragged_loop(fft_plan_t p, const void *in, void *out, void *strea
  * later for lack of it).  The paper has no counterpart; it is an addition of
  * this library.
  *   count    1..1024 instances; nx[i], ny[i] powers of two in 32..1024 (host
- *            arrays, read during the call); at most 65536 work items (one item
- *            is 8192 elements of one pass; a 512 x 512 instance takes 64).
+ *            arrays, read during the call); at most 131072 work items (one
+ *            item is 4096 elements of one pass; a 512 x 512 instance takes 128).
  *            Larger requests return FFT_ERR_INVALID_SIZE without launching.
  *   dir      FFT_FORWARD or FFT_INVERSE.
  *   in, out  caller-owned device buffers of the packed batch (may be equal).
  *   status   optional caller-owned device int: a kernel that times out on
  *            its bounded wait writes FFT_ERR_TIMEOUT there (NULL: not reported).
- * It allocates nothing.  Its scratch is one fixed array of about 1.1 MiB
+ * It allocates nothing.  Its scratch is one fixed array of about 2.1 MiB
  * inside the library, present on every GPU that loads the library until the
  * process exits.  The first call on each device looks up that array's address
  * and fills its twiddle tables (a short set-up, with the device current, that

@@ -4,11 +4,13 @@
 // The paper's 2D transform (Section 5) runs row FFTs, then column FFTs, with
 // the rows spread evenly over cores (it assumes an even decomposition).  A
 // ragged batch has no even decomposition, so the work is cut into items of
-// 8192 complex elements (64 KiB), executed by a 512-thread CTA each:
-//   * fused item  -- a whole instance with nx*ny <= 8192: its rows, then (same
+// 4096 complex elements (32 KiB), executed by a 256-thread CTA each (four per
+// SM; items of 8192 elements at two 512-thread CTAs per SM measured 2 %
+// slower on the 512-instance batch):
+//   * fused item  -- a whole instance with nx*ny <= 4096: its rows, then (same
 //     CTA, through L2) its columns;
-//   * row item    -- 8192/nx consecutive rows of a larger instance;
-//   * column item -- 8192/ny adjacent columns of a larger instance; it may
+//   * row item    -- 4096/nx consecutive rows of a larger instance;
+//   * column item -- 4096/ny adjacent columns of a larger instance; it may
 //     start only when every row item of its instance has finished, which a
 //     per-instance counter records (release: __threadfence + atomicAdd;
 //     acquire: ld.acquire polled with a bounded wait).
@@ -35,8 +37,9 @@
 
 namespace gb300fft {
 
-constexpr int kRagThreads = 512;
-constexpr int kRagItem = 8192;  // complex elements per work item
+constexpr int kRagThreads = 256;
+constexpr int kRagItem = 4096;  // complex elements per work item
+constexpr int kRagCtasPerSm = 4;
 constexpr int kRagE = 16;
 
 enum : int { kItemFused = 0, kItemRows = 1, kItemCols = 2 };
@@ -162,7 +165,7 @@ __device__ __noinline__ void fused_item(const float2 *twx, const float2 *twy, fl
     rag_cols<NY, NX>(out, NX, 0, twy, so, smem);
 }
 
-__global__ void __launch_bounds__(kRagThreads, 2) k_ragged(const RagArgs a) {
+__global__ void __launch_bounds__(kRagThreads, kRagCtasPerSm) k_ragged(const RagArgs a) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ int s_item;
     __shared__ int s_ok;
@@ -220,23 +223,19 @@ __global__ void __launch_bounds__(kRagThreads, 2) k_ragged(const RagArgs a) {
                 default: dispatch_cols<10>(a.tw.p[10], a.so, out, nx, item.z, smem); break;
             }
         } else {
-            switch (lx * 16 + ly) {  // lx + ly <= 13, both >= 5
+            switch (lx * 16 + ly) {  // lx + ly <= 12, both >= 5
                 case 5 * 16 + 5: fused_item<5, 5>(a.tw.p[5], a.tw.p[5], a.si, a.so, in, out, smem); break;
                 case 5 * 16 + 6: fused_item<5, 6>(a.tw.p[5], a.tw.p[6], a.si, a.so, in, out, smem); break;
                 case 5 * 16 + 7: fused_item<5, 7>(a.tw.p[5], a.tw.p[7], a.si, a.so, in, out, smem); break;
-                case 5 * 16 + 8: fused_item<5, 8>(a.tw.p[5], a.tw.p[8], a.si, a.so, in, out, smem); break;
                 case 6 * 16 + 5: fused_item<6, 5>(a.tw.p[6], a.tw.p[5], a.si, a.so, in, out, smem); break;
                 case 6 * 16 + 6: fused_item<6, 6>(a.tw.p[6], a.tw.p[6], a.si, a.so, in, out, smem); break;
-                case 6 * 16 + 7: fused_item<6, 7>(a.tw.p[6], a.tw.p[7], a.si, a.so, in, out, smem); break;
-                case 7 * 16 + 5: fused_item<7, 5>(a.tw.p[7], a.tw.p[5], a.si, a.so, in, out, smem); break;
-                case 7 * 16 + 6: fused_item<7, 6>(a.tw.p[7], a.tw.p[6], a.si, a.so, in, out, smem); break;
-                default: fused_item<8, 5>(a.tw.p[8], a.tw.p[5], a.si, a.so, in, out, smem); break;
+                default: fused_item<7, 5>(a.tw.p[7], a.tw.p[5], a.si, a.so, in, out, smem); break;
             }
         }
     }
 }
 
-// Shared memory of the largest item: 8192/n rows (or W columns) of padded
+// Shared memory of the largest item: 4096/n rows (or W columns) of padded
 // length-n exchange buffers.
 constexpr size_t kRagSmem = sizeof(float2) * (size_t)(kRagItem + (kRagItem >> 4));
 
@@ -646,7 +645,7 @@ namespace gb300fft {
 // kNoAllocBytes until the process exits.
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxCount = 1024;   // instances per call
-constexpr int kNoAllocMaxItems = 65536;  // work items per call
+constexpr int kNoAllocMaxItems = 131072;  // work items per call
 constexpr size_t kNoAllocTwOffset = 0;   // twiddle tables, 4096 float2 (filled once per device)
 constexpr size_t kNoAllocTwElems = 4096;
 constexpr size_t kNoAllocItemsOffset = kNoAllocTwOffset + kNoAllocTwElems * sizeof(float2);

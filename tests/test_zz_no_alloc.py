@@ -116,6 +116,6 @@ def test_noalloc_rejects_requests_beyond_its_fixed_scratch(lib):
     x = torch.zeros(1024 * 1024 * 8, dtype=torch.complex64, device="cuda")
     rc, _ = noalloc(lib, [32] * 1025, [32] * 1025, x)
     assert rc == -1  # FFT_ERR_INVALID_SIZE: more instances than the array holds
-    big = [1024] * 300  # 300 instances of 1024 x 1024 need 76800 work items
+    big = [1024] * 300  # 300 instances of 1024 x 1024 need 153600 work items
     rc, _ = noalloc(lib, big, big, x)
     assert rc == -1
