@@ -26,7 +26,8 @@
  * graph.  A plan must not be used on two streams at the same time.
  * Different plans may be created, used and destroyed from several host
  * threads at once (the library's kernel tables are filled once, under
- * std::call_once).
+ * std::call_once, and each kernel's dynamic shared-memory limit is one fixed
+ * value whichever plan sets it).
  *
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream).
