@@ -720,5 +720,3 @@ extern "C" int fft_debug_root(int m, int r, float *c, float *s) {
     *s = (float)gb300fft::sin_2pi(m, r);
     return FFT_OK;
 }
-
-extern "C" const char *fft_debug_last_cuda_error(void) { return cudaGetErrorString(cudaPeekAtLastError()); }

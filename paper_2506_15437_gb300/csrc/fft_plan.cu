@@ -1585,6 +1585,10 @@ int fft_debug_row_variant(int n, int e, int split, int *info) {
     return FFT_OK;
 }
 
+// The library links the CUDA runtime statically, so its last error is not
+// the caller's runtime's: this reads it (without clearing it).
+const char *fft_debug_last_cuda_error(void) { return cudaGetErrorString(cudaPeekAtLastError()); }
+
 int fft_debug_mixed_plan(int n, int *radices, int *n1, int *n2) {
     if (!radices || !n1 || !n2) return FFT_ERR_INVALID_ARG;
     *n1 = *n2 = 0;
